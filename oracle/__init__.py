@@ -1,0 +1,25 @@
+"""Plain FP64 CPU oracle for the GD-lambda-AMG hot path (arXiv 2004.08146).
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, obviously-correct
+restatement of what the GPU library computes, written from the paper in
+numpy float64/complex128.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  The
+CUDA product path never imports, links or executes anything in here, and this
+package imports nothing from the product package.
+
+Modules
+-------
+dirac   Wilson-clover operator D, Gamma5, Q = Gamma5 D (Sec. 2, Eq. 2.4, 2.5, 2.7)
+mg      aggregation interpolation P, restriction P^H, Galerkin coarse operator
+        D_c = P^H D P, SAP smoother, GMRES/FGMRES and the two-level cycle
+        E_2g (Sec. 2, Eq. 2.8-2.11, Prop. 1)
+gd      generalized Davidson with harmonic Ritz extraction, thick restart,
+        locking and interpolation updates (Sec. 3, Algorithm 1, Algorithm 2,
+        Theorem 1, Eq. 3.4-3.6)
+grad    Hellmann-Feynman eigenvalue gradients dlambda/dU (derivative of the
+        operator of Eq. 2.4 plus the clover term) -- parity unpinned only for
+        the clover-force convention, see the module header.
+
+Every function cites the passage it restates.  Readings taken where the paper
+is silent are stated in the function docstrings.
+"""

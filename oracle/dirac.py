@@ -1,0 +1,232 @@
+"""Wilson-clover Dirac operator D, Gamma5 and Q = Gamma5 D in plain FP64 numpy.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): the oracle the GPU
+library is checked against.
+
+Conventions (Sec. 2 of the paper, with the readings it leaves open):
+
+* Lattice ``dims = (L0, L1, L2, L3)``; direction mu = 0 is time, the site
+  index is lexicographic with mu = 3 fastest.  Fields are numpy arrays with
+  the four lattice axes first:
+  spinor ``psi[L0, L1, L2, L3, 4 spins, 3 colours]`` (complex128; the
+  operators also accept a leading batch axis),
+  links ``U[L0, L1, L2, L3, 4 mu, 3, 3]`` with ``U[..., mu, :, :] = U_mu(x)``.
+* Lattice spacing a = 1 (Eq. 2.5 writes a; Table 1 quotes a*m0).
+* gamma matrices: the paper fixes only the Clifford relations (Eq. 2.3),
+  gamma5 = gamma0 gamma1 gamma2 gamma3 (Eq. 2.4) and the representation with
+  gamma5 = diag(I2, -I2) (Sec. 2, below Eq. 2.5).  Reading taken: the chiral
+  basis gamma0 = -[[0, I2], [I2, 0]], gamma_k = [[0, -i sigma_k], [i sigma_k, 0]]
+  (k = 1, 2, 3; sigma_k the Pauli matrices).
+* Boundary: the paper says periodic (Sec. 2, below Eq. 2.5); the workloads
+  use antiperiodic time.  A hop that crosses the time boundary picks up a
+  factor -1 (both directions) when ``antiperiodic_t`` is set; links are not
+  modified, so the clover term never sees the phase.
+* Clover (Sec. 4, "clover improved ... block diagonal term with 6x6 diagonal
+  blocks"; Sheikholeslami-Wohlert).  Reading taken:
+  D += c_sw * (i/4) * sum_{mu,nu} sigma_{mu nu} (x) F_{mu nu}(x),
+  sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu],
+  F_{mu nu} = (1/8) (Q_{mu nu} - Q_{mu nu}^H) with Q_{mu nu}(x) the sum of the
+  four plaquette leaves in the (mu, nu) plane that start and end at x.
+  No trace is subtracted from F.
+"""
+import numpy as np
+
+# ---------------------------------------------------------------- gamma basis
+_I2 = np.eye(2, dtype=np.complex128)
+_Z2 = np.zeros((2, 2), dtype=np.complex128)
+_PAULI = (
+    np.array([[0, 1], [1, 0]], dtype=np.complex128),
+    np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+    np.array([[1, 0], [0, -1]], dtype=np.complex128),
+)
+
+
+def gamma_matrices():
+    """The four Hermitian gamma matrices (Eq. 2.3) and gamma5 (Eq. 2.4).
+
+    Returns ``(g, g5)`` with ``g`` of shape (4, 4, 4): g[mu] = gamma_mu, and
+    g5 = g[0] g[1] g[2] g[3], which in this basis is diag(1, 1, -1, -1).
+    """
+    g = np.empty((4, 4, 4), dtype=np.complex128)
+    g[0] = -np.block([[_Z2, _I2], [_I2, _Z2]])
+    for k in range(3):
+        g[k + 1] = np.block([[_Z2, -1j * _PAULI[k]], [1j * _PAULI[k], _Z2]])
+    g5 = g[0] @ g[1] @ g[2] @ g[3]
+    return g, g5
+
+
+GAMMA, GAMMA5 = gamma_matrices()
+
+
+def sigma_munu(mu, nu):
+    """sigma_{mu nu} = (i/2) [gamma_mu, gamma_nu] (clover term, reading above)."""
+    return 0.5j * (GAMMA[mu] @ GAMMA[nu] - GAMMA[nu] @ GAMMA[mu])
+
+
+# ---------------------------------------------------------------- geometry
+def volume(dims):
+    return int(np.prod(dims))
+
+
+def shift_field(f, mu, sign):
+    """f(x + sign * mu_hat) with periodic wrap (no boundary phase)."""
+    return np.roll(f, -sign, axis=mu)
+
+
+def hop_spinor(psi, mu, sign, antiperiodic_t):
+    """psi(x + sign*mu_hat) including the fermion boundary phase of the time
+    direction (reading: -1 on hops across t = L0-1 <-> 0 when antiperiodic).
+    ``psi`` has shape (..., L0, L1, L2, L3, 4, 3)."""
+    out = np.roll(psi, -sign, axis=mu - 6)
+    if mu == 0 and antiperiodic_t:
+        L0 = psi.shape[-6]
+        edge = (Ellipsis, L0 - 1 if sign > 0 else 0) + (slice(None),) * 5
+        out[edge] *= -1.0   # x at the last (first) time slice reads across the boundary
+    return out
+
+
+def _dag(M):
+    return np.conj(np.swapaxes(M, -1, -2))
+
+
+def _cmul(U, psi):
+    """Colour matrix (..., 3, 3) times spinor (..., 4, 3) on the colour index."""
+    return np.einsum('...ab,...sb->...sa', U, psi)
+
+
+def _smul(G, psi):
+    """Spin matrix (4, 4) times spinor (..., 4, 3) on the spin index."""
+    return np.einsum('st,...tc->...sc', G, psi)
+
+
+# ---------------------------------------------------------------- clover
+def plaquette_leaves(U, mu, nu):
+    """Q_{mu nu}(x): sum of the four plaquette leaves in the (mu, nu) plane
+    starting and ending at x, all with the same orientation (clover term)."""
+    Umu = U[..., mu, :, :]
+    Unu = U[..., nu, :, :]
+    S = shift_field
+    Umu_m = S(Umu, mu, -1)            # U_mu(x - mu)
+    Unu_m = S(Unu, nu, -1)            # U_nu(x - nu)
+    leaf1 = Umu @ S(Unu, mu, +1) @ _dag(S(Umu, nu, +1)) @ _dag(Unu)
+    leaf2 = Unu @ _dag(S(S(Umu, nu, +1), mu, -1)) @ _dag(S(Unu, mu, -1)) @ Umu_m
+    leaf3 = _dag(Umu_m) @ _dag(S(S(Unu, mu, -1), nu, -1)) @ S(S(Umu, mu, -1), nu, -1) @ Unu_m
+    leaf4 = _dag(Unu_m) @ S(Umu, nu, -1) @ S(S(Unu, mu, +1), nu, -1) @ _dag(Umu)
+    return leaf1 + leaf2 + leaf3 + leaf4
+
+
+def field_strength(U, mu, nu):
+    """F_{mu nu}(x) = (Q_{mu nu} - Q_{mu nu}^H) / 8 (clover reading, module header)."""
+    Q = plaquette_leaves(U, mu, nu)
+    return (Q - _dag(Q)) / 8.0
+
+
+def clover_field(U, csw):
+    """Site-diagonal clover matrices as full 12x12 blocks, index s*3 + c.
+
+    C(x) = c_sw * (i/4) * sum_{mu != nu} sigma_{mu nu} (x) F_{mu nu}(x)
+         = c_sw * (i/2) * sum_{mu < nu} sigma_{mu nu} (x) F_{mu nu}(x).
+    Returns an array of shape dims + (12, 12).
+    """
+    dims = U.shape[:4]
+    C = np.zeros(dims + (12, 12), dtype=np.complex128)
+    if csw == 0.0:
+        return C
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            F = field_strength(U, mu, nu)
+            C += np.einsum('st,...ab->...satb', sigma_munu(mu, nu), F).reshape(dims + (12, 12))
+    return C * (csw * 0.5j)
+
+
+# ---------------------------------------------------------------- operators
+class WilsonClover:
+    """The operator D of Eq. 2.5 (a = 1) plus the clover term.
+
+    (D psi)(x) = (m0 + 4) psi(x) + C(x) psi(x)
+                 - 1/2 sum_mu (I4 - gamma_mu) (x) U_mu(x) psi(x + mu)
+                 - 1/2 sum_mu (I4 + gamma_mu) (x) U_mu(x - mu)^H psi(x - mu)
+    """
+
+    def __init__(self, U, m0, csw, antiperiodic_t=True):
+        self.U = np.asarray(U, dtype=np.complex128)
+        self.dims = tuple(self.U.shape[:4])
+        self.m0 = float(m0)
+        self.csw = float(csw)
+        self.antiperiodic_t = bool(antiperiodic_t)
+        self.C = clover_field(self.U, self.csw)
+        self.Ub = [shift_field(self.U[..., mu, :, :], mu, -1) for mu in range(4)]  # U_mu(x-mu)
+        self.n = volume(self.dims) * 12
+
+    # ---- pieces of Eq. 2.5
+    def diag(self, psi):
+        """(m0 + 4) psi + C psi: the site-diagonal part."""
+        Cpsi = np.einsum('...ij,...j->...i', self.C,
+                         psi.reshape(psi.shape[:-2] + (12,))).reshape(psi.shape)
+        return (self.m0 + 4.0) * psi + Cpsi
+
+    def hop(self, psi, mu, sign):
+        """The hop term of direction sign*mu of Eq. 2.5 (including -1/2):
+        sign=+1: -1/2 (I - gamma_mu) (x) U_mu(x) psi(x + mu)
+        sign=-1: -1/2 (I + gamma_mu) (x) U_mu(x - mu)^H psi(x - mu)."""
+        nb = hop_spinor(psi, mu, sign, self.antiperiodic_t)
+        if sign > 0:
+            Up = _cmul(self.U[..., mu, :, :], nb)
+            return -0.5 * (Up - _smul(GAMMA[mu], Up))
+        Up = _cmul(_dag(self.Ub[mu]), nb)
+        return -0.5 * (Up + _smul(GAMMA[mu], Up))
+
+    def D(self, psi):
+        out = self.diag(psi)
+        for mu in range(4):
+            out = out + self.hop(psi, mu, +1) + self.hop(psi, mu, -1)
+        return out
+
+    @staticmethod
+    def g5(psi):
+        """Gamma5 = I (x) gamma5 (x) I3 (Sec. 2, above Eq. 2.7)."""
+        return _smul(GAMMA5, psi)
+
+    def Q(self, psi):
+        """Q = Gamma5 D (Sec. 2, definition of the Hermitian Wilson-Dirac operator)."""
+        return self.g5(self.D(psi))
+
+    def Q_shift(self, psi, tau):
+        """(Q - tau I) psi: the shifted operator of Eq. 1.1 / Eq. 3.6."""
+        return self.Q(psi) - tau * psi
+
+    def D_g5shift(self, psi, tau):
+        """(D - tau Gamma5) psi: the Gamma5-preconditioned operator of Eq. 3.7."""
+        return self.D(psi) - tau * self.g5(psi)
+
+    # ---- flat views, [site][spin][colour] order
+    def shape_field(self, v):
+        return np.asarray(v, dtype=np.complex128).reshape(self.dims + (4, 3))
+
+    def dense(self, which='Q', tau=0.0, chunk=384):
+        """Dense matrix of Q - tau, D - tau*Gamma5 or D by applying the operator
+        to every unit vector (brute force, small lattices only)."""
+        n = self.n
+        M = np.empty((n, n), dtype=np.complex128)
+        for j0 in range(0, n, chunk):
+            j1 = min(n, j0 + chunk)
+            E = np.zeros((j1 - j0, n), dtype=np.complex128)
+            E[np.arange(j1 - j0), np.arange(j0, j1)] = 1.0
+            psi = E.reshape((j1 - j0,) + self.dims + (4, 3))
+            if which == 'Q':
+                col = self.Q_shift(psi, tau)
+            elif which == 'Dg5':
+                col = self.D_g5shift(psi, tau)
+            else:
+                col = self.D(psi)
+            M[:, j0:j1] = col.reshape(j1 - j0, n).T
+        return M
+
+
+def clover_blocks(C):
+    """The two 6x6 chirality blocks of each 12x12 clover matrix: block 0 is
+    spins {0, 1} (gamma5 = +1), block 1 spins {2, 3}.  Returns (..., 2, 6, 6)."""
+    out = np.empty(C.shape[:-2] + (2, 6, 6), dtype=np.complex128)
+    out[..., 0, :, :] = C[..., :6, :6]
+    out[..., 1, :, :] = C[..., 6:, 6:]
+    return out
