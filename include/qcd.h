@@ -1,0 +1,210 @@
+/*
+ * libqcd -- GB300 (sm_103a) hot path of the GD-lambda-AMG eigensolver for the
+ * Hermitian Wilson-clover operator Q = Gamma5 D (Frommer, Kahl, Knechtli,
+ * Rottmann, Strebel, Zwaan, arXiv 2004.08146).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Lattice dims = {L0, L1, L2, L3}; mu = 0 is time; the site index is
+ *    lexicographic, site = ((x0*L1 + x1)*L2 + x2)*L3 + x3 (Sec. 2: N_t x N_s^3).
+ *  - Gauge links U: [site][mu][row][col], complex128 stored as interleaved
+ *    (re, im) doubles, HOST memory, copied in by qcd_set_gauge.
+ *  - Fine spinor fields: [site][spin 4][colour 3] complex; complex128 for the
+ *    FP64 entry points, complex64 where an entry point says so.  They are
+ *    DEVICE pointers owned by the caller and used on the context's stream.
+ *  - gamma matrices: chiral basis with gamma5 = diag(1, 1, -1, -1) (Sec. 2);
+ *    gamma0 = -[[0, I],[I, 0]], gamma_k = [[0, -i sigma_k],[i sigma_k, 0]].
+ *  - D = (m0 + 4) + clover - 1/2 sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu)
+ *        + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu)]  (Eq. 2.5, a = 1), clover
+ *    c_sw (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu}, F = (Q_{mu nu} - h.c.)/8.
+ *  - Every call returns 0 (QCD_OK) or one of the QCD_E* codes below; no
+ *    exception crosses the ABI; qcd_last_error() gives a message.
+ *  - Calls on one context are not thread safe; use one context per stream.
+ */
+#ifndef QCD_H
+#define QCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QCD_OK        0
+#define QCD_EINVAL    1   /* bad argument, size or aliasing */
+#define QCD_ENOMEM    2   /* device allocation failed */
+#define QCD_ENOTSETUP 3   /* gauge field or multigrid hierarchy missing */
+#define QCD_ENOCONV   4   /* iteration cap reached; outputs hold the best iterate */
+#define QCD_ETIMEOUT  5   /* a device-side wait hit its iteration limit */
+#define QCD_ECUDA     6   /* a CUDA runtime call failed */
+
+/* Operators for qcd_apply */
+#define QCD_OP_D   0      /* out = (D - tau Gamma5) in   (Eq. 3.7; tau = 0 gives D) */
+#define QCD_OP_Q   1      /* out = (Q - tau) in          (Eq. 3.6) */
+
+/* Precisions */
+#define QCD_FP64   0      /* complex128 fields, FP64 arithmetic */
+#define QCD_FP32   1      /* complex64 fields, FP32 arithmetic */
+#define QCD_MIXED  1      /* solver mode: FP32 inner solves, FP64 outer */
+
+/* Smoothers */
+#define QCD_SMOOTHER_SAP   0
+#define QCD_SMOOTHER_GMRES 1
+
+typedef struct qcd_ctx qcd_ctx;
+
+/* Parameters; defaults (qcd_default_params) are Table 2 of the paper. */
+typedef struct qcd_params {
+    int    antiperiodic_t;   /* 1: hops across the time boundary get -1 (default 1) */
+    int    precision;        /* QCD_FP64 or QCD_MIXED for solves and eigs (default MIXED) */
+    int    correction_form;  /* QCD_OP_D: (D - theta G5) t = G5 r (Eq. 3.7, default);
+                                QCD_OP_Q: (Q - theta) t = r (Eq. 3.6) */
+    int    use_mg;           /* 0: plain GMRES inner solve; 1: FGMRES + two-level MG */
+    int    setup_iters;      /* adaptive setup iterations (Table 2: 6) */
+    int    smoother;         /* QCD_SMOOTHER_SAP (default) or QCD_SMOOTHER_GMRES */
+    int    nu;               /* post-smoothing steps (Table 2: 4) */
+    int    sap_block[4];     /* SAP block extents (default 2,2,2,2) */
+    int    sap_block_iters;  /* GMRES steps per SAP block solve (Sec. 4: 10) */
+    double sap_block_tol;    /* block residual reduction (Sec. 4: 1e-1) */
+    int    gmres_smooth_iters; /* GMRES smoother steps per smoothing step (4) */
+    double inner_tol;        /* FGMRES relative residual (Table 2: 1e-1) */
+    int    inner_maxiter;    /* FGMRES iterations (Table 2: 5) */
+    double coarse_tol;       /* coarse GMRES reduction (Table 2: 5e-1) */
+    int    coarse_maxiter;   /* coarse GMRES iteration cap (default 100) */
+    int    plain_maxiter;    /* plain GMRES inner iterations without MG (default 20) */
+    int    m_min;            /* Table 2: 30 */
+    int    m_max;            /* Table 2: 50 */
+    int    block;            /* targets per outer iteration (>= 1; default 2) */
+    int    n_init;           /* random start vectors when use_mg = 0 (default 8) */
+    int    update_every;     /* interpolation rebuild every k locks (default 1) */
+    int    max_outer;        /* outer iteration cap (default 100000) */
+    unsigned long long seed; /* counter-based RNG seed for setup / start vectors */
+    int    verbose;          /* 1: per-lock progress on stderr */
+} qcd_params;
+
+typedef struct qcd_solve_info {
+    int    iterations;       /* FGMRES / GMRES iterations (summed over refinements) */
+    int    refinements;      /* FP64 refinement steps (mixed precision) */
+    double residual;         /* final ||b - (Q - tau) x|| / ||b|| in FP64 */
+    double seconds;          /* wall time of the call */
+} qcd_solve_info;
+
+typedef struct qcd_eig_info {
+    int    outer;            /* outer (Davidson) iterations */
+    int    inner;            /* inner FGMRES/GMRES iterations, all targets */
+    int    locked;           /* pairs locked (>= k when converged) */
+    int    updates;          /* interpolation rebuilds */
+    int    converged;        /* 1 when all k pairs met tol */
+    double max_residual;     /* max ||Q v - lambda v|| over the returned pairs */
+    double seconds;          /* wall time of the call */
+} qcd_eig_info;
+
+/* Fill *p with the defaults above. */
+void qcd_default_params(qcd_params* p);
+
+/* Create a context bound to a CUDA stream (cudaStream_t; NULL = legacy
+ * default stream) on the current device.  *ctx is owned by the caller and
+ * released by qcd_destroy.  EINVAL on a NULL ctx or p. */
+int qcd_create(qcd_ctx** ctx, const qcd_params* p, void* cuda_stream);
+int qcd_destroy(qcd_ctx* ctx);
+const char* qcd_last_error(qcd_ctx* ctx);
+
+/* Change parameters after creation (solver knobs only; the multigrid
+ * hierarchy is rebuilt by the next qcd_mg_setup). */
+int qcd_set_params(qcd_ctx* ctx, const qcd_params* p);
+
+/* Load the gauge field (Sec. 2, Eq. 2.5): U is a HOST array of
+ * dims[0]*dims[1]*dims[2]*dims[3]*4*9 complex128 in [site][mu][row][col]
+ * order; the library copies it, builds the clover term on the device and
+ * keeps FP64 and FP32 copies.  m0 and csw as in Eq. 2.5 / Table 1.  Every
+ * extent must be >= 2; a previous hierarchy is dropped.  EINVAL on bad dims. */
+int qcd_set_gauge(qcd_ctx* ctx, const double* U, const int dims[4], double m0, double csw);
+
+/* out = (Q - tau) in  (Eq. 1.1 with A = Q; Eq. 3.6).  in/out: device
+ * complex128 fields of 12 * V elements; in == out returns EINVAL. */
+int qcd_apply_Q(qcd_ctx* ctx, const void* in, void* out, double tau);
+
+/* Multi-right-hand-side operator apply (Eq. 2.5 / 3.6 / 3.7): for
+ * j < nrhs, out_j = op(tau[j]) in_j where op is QCD_OP_D (D - tau Gamma5) or
+ * QCD_OP_Q (Q - tau).  in/out are device arrays of nrhs consecutive fields
+ * (complex128 for QCD_FP64, complex64 for QCD_FP32); tau is a HOST array
+ * of nrhs doubles; 1 <= nrhs <= 64; in and out must not overlap. */
+int qcd_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* in, void* out,
+              const double* tau);
+
+/* Multigrid setup (Sec. 2 "Algebraic multigrid methods", Table 2): draw Nv
+ * seeded random test vectors, run params.setup_iters adaptive setup
+ * iterations and build the chirality-split aggregation P over blocks of
+ * extent block[4] (each must divide the lattice) and the Galerkin coarse
+ * operator D_c = P^H D P (Eq. 2.8, 2.9).  Requires qcd_set_gauge. */
+int qcd_mg_setup(qcd_ctx* ctx, int Nv, const int block[4]);
+
+/* Rebuild P and D_c from nvec given fine vectors (Sec. 3, "Local coherence";
+ * Algorithm 2 interpolation update).  V: DEVICE array of nvec consecutive
+ * complex128 fields.  Without a prior qcd_mg_setup, block = params.sap_block
+ * is used for the aggregates.  1 <= nvec <= 32. */
+int qcd_mg_update_from_eigvecs(qcd_ctx* ctx, const void* V, int nvec);
+
+/* Solve (Q - tau) x = b to ||b - (Q - tau) x|| <= tol ||b|| (Eq. 1.1):
+ * FGMRES preconditioned by the two-level cycle on the Gamma5 form (Eq. 3.7),
+ * FP32 inner solves wrapped by FP64 iterative refinement in QCD_MIXED mode.
+ * b, x: device complex128 fields; x is the output (its input is ignored).
+ * ENOCONV leaves the best iterate in x and its residual in info. */
+int qcd_shifted_solve(qcd_ctx* ctx, const void* b, void* x, double tau, double tol,
+                      qcd_solve_info* info);
+
+/* Batched form: nrhs systems with distinct shifts tau[j] (HOST array) solved
+ * together, b[j], x[j] device complex128 fields; 1 <= nrhs <= 64. */
+int qcd_shifted_solve_batched(qcd_ctx* ctx, int nrhs, const void* const* b, void* const* x,
+                              const double* tau, double tol, qcd_solve_info* info);
+
+/* GD-lambda-AMG (Algorithm 2): the k eigenpairs of Q of smallest |lambda| to
+ * ||Q v - lambda v|| <= tol (||v|| = 1).  lambda: HOST array of k doubles,
+ * ascending |lambda| (ties ascending lambda); V: DEVICE array of k
+ * consecutive complex128 fields (may be NULL).  Uses the hierarchy from
+ * qcd_mg_setup when params.use_mg = 1 (ENOTSETUP otherwise). */
+int qcd_eigs(qcd_ctx* ctx, int k, double tol, double* lambda, void* V, qcd_eig_info* info);
+
+/* ---------------------------------------------------------------------
+ * Component entry points (the pieces of the hot path, for tests and for
+ * callers that build their own solvers).  Coarse vectors are
+ * [coarse site][chirality][i < Nv] complex; prec selects complex128 or
+ * complex64 buffers; all pointers are DEVICE pointers unless stated.
+ * ------------------------------------------------------------------- */
+
+/* Sizes of the current hierarchy: out[0] = coarse sites, out[1] = Nv,
+ * out[2..5] = coarse dims, out[6] = block sites. */
+int qcd_mg_info(qcd_ctx* ctx, int out[8]);
+
+/* x_c = P^H r (Eq. 2.8, R = P^H) for nrhs fields. */
+int qcd_mg_restrict(qcd_ctx* ctx, int prec, int nrhs, const void* r, void* xc);
+
+/* x = P x_c for nrhs coarse vectors (overwrites x). */
+int qcd_mg_prolong(qcd_ctx* ctx, int prec, int nrhs, const void* xc, void* x);
+
+/* y_j = (D_c - tau_j Gamma5^c) x_j (op QCD_OP_D) or (Gamma5^c D_c - tau_j) x_j
+ * (op QCD_OP_Q), coarse stencil of Eq. 2.8 / 2.9; tau HOST array. */
+int qcd_coarse_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* x, void* y,
+                     const double* tau);
+
+/* Copy P (HOST complex128 [coarse site][chi][i][block site][spin 2][colour 3])
+ * and the coarse stencil (HOST complex128 [coarse site][9][row][col];
+ * direction 0 = self, 1+mu = +mu, 5+mu = -mu) out of the library. */
+int qcd_mg_get_P(qcd_ctx* ctx, double* P_host);
+int qcd_mg_get_coarse(qcd_ctx* ctx, double* A_host);
+
+/* `sweeps` SAP sweeps (Eq. 2.10; colour 0 blocks, then colour 1) on
+ * op(tau) x = b with GMRES block solves of params.sap_block_iters steps to
+ * params.sap_block_tol (block_tol < 0 forces exactly sap_block_iters
+ * steps); x is updated in place.  nrhs fields, tau HOST array. */
+int qcd_sap(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x,
+            const double* tau, int sweeps, double block_tol);
+
+/* One two-level cycle x = M b (Eq. 2.8 with post-smoothing only) on op(tau). */
+int qcd_mg_cycle(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x,
+                 const double* tau);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QCD_H */

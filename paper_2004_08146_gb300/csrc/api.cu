@@ -1,0 +1,1191 @@
+// libqcd C ABI and host-side control: context, gauge upload, operator
+// applies, the multigrid hierarchy (setup and interpolation updates),
+// batched (F)GMRES, the two-level cycle, shifted solves with FP64 iterative
+// refinement and the GD-lambda-AMG outer iteration (Algorithm 2).  The host
+// only reads back scalars (dot products, norms, harmonic Ritz values) to take
+// control decisions; every vector operation runs in the kernels of the other
+// translation units.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <numeric>
+#include <stdexcept>
+
+#include "internal.h"
+
+using namespace qcd;
+
+namespace {
+
+struct QcdError : std::runtime_error {
+    int code;
+    QcdError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            throw QcdError(QCD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+void check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw QcdError(QCD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+using cd = std::complex<double>;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct qcd_ctx {
+    qcd_params p{};
+    cudaStream_t st = nullptr;
+    std::string err;
+    bool have_gauge = false;
+    FineOp f;
+    Coarse c;
+    SapPlan sap;
+    bool have_sap = false;
+    std::map<std::string, DevBuf> ws;
+    double2* pinned = nullptr;   // host staging for small read-backs
+    size_t pinned_n = 0;
+    double2* test_vectors = nullptr;  // FP64 setup vectors [nv][V*12]
+    int n_test = 0;
+
+    ~qcd_ctx() { release(); }
+
+    void release() {
+        for (auto& kv : ws) if (kv.second.p) cudaFree(kv.second.p);
+        ws.clear();
+        auto fr = [](void* q) { if (q) cudaFree(q); };
+        fr(f.U64); fr(f.U32); fr(f.A64); fr(f.A32);
+        f.U64 = nullptr; f.U32 = nullptr; f.A64 = nullptr; f.A32 = nullptr;
+        drop_mg();
+        fr(sap.blocks_of_colour[0]); fr(sap.blocks_of_colour[1]);
+        sap.blocks_of_colour[0] = sap.blocks_of_colour[1] = nullptr;
+        have_sap = false;
+        if (pinned) cudaFreeHost(pinned);
+        pinned = nullptr;
+        pinned_n = 0;
+    }
+    void drop_mg() {
+        auto fr = [](void* q) { if (q) cudaFree(q); };
+        fr(c.P64); fr(c.P32); fr(c.A64); fr(c.A32); fr(test_vectors);
+        c.P64 = nullptr; c.P32 = nullptr; c.A64 = nullptr; c.A32 = nullptr;
+        test_vectors = nullptr;
+        n_test = 0;
+        c.ready = false;
+    }
+
+    void* buf(const std::string& name, size_t bytes) {
+        DevBuf& b = ws[name];
+        if (b.bytes < bytes) {
+            if (b.p) CK(cudaFree(b.p));
+            b.p = nullptr;
+            b.bytes = 0;
+            if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                throw QcdError(QCD_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes for " + name);
+            }
+            b.bytes = bytes;
+        }
+        return b.p;
+    }
+    double2* host(size_t n) {
+        if (pinned_n < n) {
+            if (pinned) CK(cudaFreeHost(pinned));
+            pinned = nullptr;
+            CK(cudaMallocHost((void**)&pinned, n * sizeof(double2)));
+            pinned_n = n;
+        }
+        return pinned;
+    }
+    // copy n complex values from the device and wait
+    const double2* fetch(const double2* d, size_t n) {
+        double2* h = host(n);
+        CK(cudaMemcpyAsync(h, d, n * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return h;
+    }
+    size_t nfine() const { return (size_t)f.g.V * 12; }
+};
+
+namespace {
+
+size_t esz(int prec) { return prec == QCD_FP64 ? sizeof(double2) : sizeof(float2); }
+
+void validate_params(const qcd_params& p) {
+    if (p.m_min < 1 || p.m_max < p.m_min + 1 || p.m_max > 64)
+        throw QcdError(QCD_EINVAL, "need 1 <= m_min < m_max <= 64");
+    if (p.block < 1 || p.block > 16) throw QcdError(QCD_EINVAL, "block must be in [1, 16]");
+    if (p.nu < 0 || p.sap_block_iters < 1 || p.sap_block_iters > 32) throw QcdError(QCD_EINVAL, "bad smoother params");
+    if (p.inner_maxiter < 1 || p.inner_maxiter > 64 || p.coarse_maxiter < 1 || p.coarse_maxiter > 200 ||
+        p.plain_maxiter < 1 || p.plain_maxiter > 200)
+        throw QcdError(QCD_EINVAL, "bad iteration caps");
+    if (p.precision != QCD_FP64 && p.precision != QCD_MIXED) throw QcdError(QCD_EINVAL, "bad precision");
+    if (p.correction_form != QCD_OP_D && p.correction_form != QCD_OP_Q) throw QcdError(QCD_EINVAL, "bad correction_form");
+}
+
+// ------------------------------------------------------------------ linear operators
+using OpFn = std::function<void(const void* in, void* out)>;
+
+struct GmresResult {
+    std::vector<int> iters;
+    std::vector<double> resest;   // relative residual estimates
+};
+
+// Batched (F)GMRES from a zero initial guess: nrhs independent systems of
+// length n in precision prec; Arnoldi by classical Gram-Schmidt applied
+// twice; complex Givens rotations; system j stops at |g_{k+1}| <= tol ||b_j||.
+// With a preconditioner M this is flexible GMRES (right preconditioning).
+GmresResult gmres_batched(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn& A, const OpFn* M,
+                          const void* b, void* x, double tol, int maxit, const std::string& tag) {
+    cudaStream_t st = ctx->st;
+    const size_t vs = n * nrhs;                 // one "vector set" (all rhs)
+    const size_t eb = esz(prec);
+    char* Vk = (char*)ctx->buf(tag + ".V", (size_t)(maxit + 1) * vs * eb);
+    char* Zk = M ? (char*)ctx->buf(tag + ".Z", (size_t)maxit * vs * eb) : nullptr;
+    void* w = ctx->buf(tag + ".w", vs * eb);
+    double2* dd = (double2*)ctx->buf(tag + ".dots", (size_t)(2 * (maxit + 2) + 2) * nrhs * sizeof(double2));
+    double2* part = (double2*)ctx->buf(tag + ".part", (size_t)(maxit + 2) * nrhs * 64 * sizeof(double2));
+    double2* coef = (double2*)ctx->buf(tag + ".coef", (size_t)(maxit + 1) * nrhs * sizeof(double2));
+    double2* h1 = dd;
+    double2* h2 = dd + (size_t)(maxit + 1) * nrhs;
+    double2* nr = dd + (size_t)2 * (maxit + 1) * nrhs;
+
+    GmresResult out;
+    out.iters.assign(nrhs, 0);
+    out.resest.assign(nrhs, 1.0);
+    // beta_j = ||b_j||
+    blas_multidot(prec, b, 1, vs, b, nrhs, n, nr, part, st);
+    const double2* hb = ctx->fetch(nr, nrhs);
+    std::vector<double> beta(nrhs);
+    std::vector<double2> scl(nrhs);
+    for (int j = 0; j < nrhs; ++j) {
+        beta[j] = std::sqrt(std::max(hb[j].x, 0.0));
+        scl[j] = make_double2(beta[j] > 0 ? 1.0 / beta[j] : 0.0, 0.0);
+    }
+    blas_zero(prec, x, vs, st);
+    CK(cudaMemcpyAsync(coef, scl.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
+    blas_scale_dev(prec, b, Vk, coef, nrhs, n, false, false, st);
+    std::vector<std::vector<cd>> H(nrhs, std::vector<cd>((size_t)(maxit + 1) * maxit, 0.0));
+    std::vector<std::vector<double>> cs(nrhs, std::vector<double>(maxit, 0.0));
+    std::vector<std::vector<cd>> sn(nrhs, std::vector<cd>(maxit, 0.0));
+    std::vector<std::vector<cd>> g(nrhs, std::vector<cd>(maxit + 1, 0.0));
+    std::vector<char> active(nrhs, 0);
+    int nactive = 0;
+    for (int j = 0; j < nrhs; ++j) {
+        g[j][0] = beta[j];
+        active[j] = beta[j] > 0;
+        nactive += active[j];
+    }
+    int steps = 0;
+    for (int it = 0; it < maxit && nactive > 0; ++it) {
+        void* vj = Vk + (size_t)it * vs * eb;
+        if (M) {
+            void* zj = Zk + (size_t)it * vs * eb;
+            (*M)(vj, zj);
+            A(zj, w);
+        } else {
+            A(vj, w);
+        }
+        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h1, part, st);
+        blas_multiaxpy(prec, Vk, it + 1, vs, h1, -1.0, w, nrhs, n, st);
+        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h2, part, st);
+        blas_multiaxpy(prec, Vk, it + 1, vs, h2, -1.0, w, nrhs, n, st);
+        blas_multidot(prec, w, 1, vs, w, nrhs, n, nr, part, st);
+        check_launch("gmres iteration");
+        const double2* hh = ctx->fetch(dd, (size_t)(2 * (maxit + 1) + 1) * nrhs);
+        const double2* hh1 = hh;
+        const double2* hh2 = hh + (size_t)(maxit + 1) * nrhs;
+        const double2* hnr = hh + (size_t)2 * (maxit + 1) * nrhs;
+        for (int j = 0; j < nrhs; ++j) {
+            double hn = std::sqrt(std::max(hnr[j].x, 0.0));
+            scl[j] = make_double2(hn > 0 ? 1.0 / hn : 0.0, 0.0);
+            if (!active[j]) continue;
+            auto& Hj = H[j];
+            for (int i = 0; i <= it; ++i)
+                Hj[(size_t)i * maxit + it] = cd(hh1[i * nrhs + j].x + hh2[i * nrhs + j].x,
+                                                hh1[i * nrhs + j].y + hh2[i * nrhs + j].y);
+            Hj[(size_t)(it + 1) * maxit + it] = hn;
+            for (int i = 0; i < it; ++i) {
+                cd a = Hj[(size_t)i * maxit + it], c = Hj[(size_t)(i + 1) * maxit + it];
+                Hj[(size_t)i * maxit + it] = cs[j][i] * a + sn[j][i] * c;
+                Hj[(size_t)(i + 1) * maxit + it] = -std::conj(sn[j][i]) * a + cs[j][i] * c;
+            }
+            cd a = Hj[(size_t)it * maxit + it], c = Hj[(size_t)(it + 1) * maxit + it];
+            double aa = std::abs(a), rr = std::sqrt(aa * aa + std::norm(c));
+            if (aa > 0) {
+                cs[j][it] = aa / rr;
+                sn[j][it] = (a / aa) * std::conj(c) / rr;
+            } else {
+                cs[j][it] = 0.0;
+                sn[j][it] = 1.0;
+            }
+            Hj[(size_t)it * maxit + it] = cs[j][it] * a + sn[j][it] * c;
+            Hj[(size_t)(it + 1) * maxit + it] = 0.0;
+            g[j][it + 1] = -std::conj(sn[j][it]) * g[j][it];
+            g[j][it] = cs[j][it] * g[j][it];
+            out.iters[j] = it + 1;
+            out.resest[j] = beta[j] > 0 ? std::abs(g[j][it + 1]) / beta[j] : 0.0;
+            if (std::abs(g[j][it + 1]) <= tol * beta[j]) {
+                active[j] = 0;
+                --nactive;
+            }
+        }
+        steps = it + 1;
+        if (nactive == 0 || it + 1 == maxit) break;
+        CK(cudaMemcpyAsync(coef, scl.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
+        blas_scale_dev(prec, w, Vk + (size_t)(it + 1) * vs * eb, coef, nrhs, n, false, false, st);
+    }
+    // x_j = sum_i y_ji (Z or V)_i
+    if (steps > 0) {
+        std::vector<double2> cf((size_t)steps * nrhs, make_double2(0, 0));
+        for (int j = 0; j < nrhs; ++j) {
+            int k = out.iters[j];
+            std::vector<cd> y(k, 0.0);
+            for (int i = k - 1; i >= 0; --i) {
+                cd s = g[j][i];
+                for (int l = i + 1; l < k; ++l) s -= H[j][(size_t)i * maxit + l] * y[l];
+                cd d = H[j][(size_t)i * maxit + i];
+                y[i] = std::abs(d) > 0 ? s / d : 0.0;
+            }
+            for (int i = 0; i < k; ++i) cf[(size_t)i * nrhs + j] = make_double2(y[i].real(), y[i].imag());
+        }
+        CK(cudaMemcpyAsync(coef, cf.data(), cf.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+        blas_multiaxpy(prec, M ? (const void*)Zk : (const void*)Vk, steps, vs, coef, 1.0, x, nrhs, n, st);
+        check_launch("gmres update");
+        CK(cudaStreamSynchronize(st));   // coef and scl live on the host stack
+    }
+    return out;
+}
+
+// ------------------------------------------------------------------ hierarchy pieces
+void require_gauge(qcd_ctx* ctx) {
+    if (!ctx->have_gauge) throw QcdError(QCD_ENOTSETUP, "no gauge field: call qcd_set_gauge first");
+}
+void require_mg(qcd_ctx* ctx) {
+    require_gauge(ctx);
+    if (!ctx->c.ready) throw QcdError(QCD_ENOTSETUP, "no multigrid hierarchy: call qcd_mg_setup first");
+}
+
+Blocking make_blocking(const Geom& g, const int b[4]) {
+    Blocking B;
+    B.bs = 1;
+    B.nb = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (b[mu] < 1 || g.L[mu] % b[mu]) throw QcdError(QCD_EINVAL, "block extents must divide the lattice");
+        B.b[mu] = b[mu];
+        B.cd[mu] = g.L[mu] / b[mu];
+        B.bs *= b[mu];
+        B.nb *= B.cd[mu];
+    }
+    return B;
+}
+
+void ensure_sap(qcd_ctx* ctx) {
+    if (ctx->have_sap) return;
+    Blocking B = make_blocking(ctx->f.g, ctx->p.sap_block);
+    for (int mu = 0; mu < 4; ++mu)
+        if (B.cd[mu] % 2) throw QcdError(QCD_EINVAL, "SAP needs an even number of blocks in every direction");
+    if (B.bs & (B.bs - 1) || B.bs > 1024) throw QcdError(QCD_EINVAL, "SAP block sites must be a power of two <= 1024");
+    std::vector<int> lists[2];
+    for (int b = 0; b < B.nb; ++b) {
+        int t = b, c3 = t % B.cd[3]; t /= B.cd[3];
+        int c2 = t % B.cd[2]; t /= B.cd[2];
+        int c1 = t % B.cd[1], c0 = t / B.cd[1];
+        lists[(c0 + c1 + c2 + c3) % 2].push_back(b);
+    }
+    for (int c = 0; c < 2; ++c) {
+        CK(cudaMalloc(&ctx->sap.blocks_of_colour[c], lists[c].size() * sizeof(int)));
+        CK(cudaMemcpy(ctx->sap.blocks_of_colour[c], lists[c].data(), lists[c].size() * sizeof(int), cudaMemcpyHostToDevice));
+        ctx->sap.ncol[c] = (int)lists[c].size();
+    }
+    ctx->sap.B = B;
+    ctx->have_sap = true;
+}
+
+// nu SAP sweeps (Eq. 2.10) on op(tau) x = b, x updated in place
+void sap_smooth(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau, int sweeps,
+                double tol) {
+    ensure_sap(ctx);
+    const size_t n = ctx->nfine();
+    void* r = ctx->buf("sap.r", n * nrhs * esz(prec));
+    void* scr = ctx->buf("sap.scratch", sap_scratch_bytes(ctx->sap, prec, nrhs, ctx->p.sap_block_iters));
+    for (int s = 0; s < sweeps; ++s) {
+        for (int colour = 0; colour < 2; ++colour) {
+            residual_op(ctx->f, prec, op, nrhs, b, x, r, tau, ctx->st);
+            sap_blocks(ctx->f, ctx->sap, colour, prec, op, nrhs, r, x, tau, ctx->p.sap_block_iters, tol, scr, ctx->st);
+        }
+    }
+    check_launch("sap");
+}
+
+void smooth(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau) {
+    if (ctx->p.nu <= 0) return;
+    if (ctx->p.smoother == QCD_SMOOTHER_SAP) {
+        sap_smooth(ctx, prec, op, nrhs, b, x, tau, ctx->p.nu, ctx->p.sap_block_tol);
+        return;
+    }
+    const size_t n = ctx->nfine();
+    void* r = ctx->buf("gsm.r", n * nrhs * esz(prec));
+    void* e = ctx->buf("gsm.e", n * nrhs * esz(prec));
+    std::vector<double> tv(tau, tau + nrhs);
+    OpFn A = [ctx, prec, op, nrhs, tv](const void* in, void* out) {
+        apply_op(ctx->f, prec, op, nrhs, in, out, tv.data(), ctx->st);
+    };
+    for (int s = 0; s < ctx->p.nu; ++s) {
+        residual_op(ctx->f, prec, op, nrhs, b, x, r, tau, ctx->st);
+        gmres_batched(ctx, prec, n, nrhs, A, nullptr, r, e, 0.0, ctx->p.gmres_smooth_iters, "gsm");
+        blas_axpby(prec, make_double2(1, 0), e, make_double2(1, 0), x, n * nrhs, ctx->st);
+    }
+}
+
+// two-level cycle x = M b (Eq. 2.8, post-smoothing only)
+void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau) {
+    const Coarse& c = ctx->c;
+    const size_t nco = (size_t)c.gc.V * c.nc;
+    void* rc = ctx->buf("cyc.rc", nco * nrhs * esz(prec));
+    void* xc = ctx->buf("cyc.xc", nco * nrhs * esz(prec));
+    mg_restrict(ctx->f, c, prec, nrhs, b, rc, ctx->st);
+    std::vector<double> tv(tau, tau + nrhs);
+    OpFn Ac = [ctx, prec, op, nrhs, tv](const void* in, void* out) {
+        coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st);
+    };
+    gmres_batched(ctx, prec, nco, nrhs, Ac, nullptr, rc, xc, ctx->p.coarse_tol, ctx->p.coarse_maxiter, "coarse");
+    mg_prolong(ctx->f, c, prec, nrhs, xc, x, false, ctx->st);
+    smooth(ctx, prec, op, nrhs, b, x, tau);
+    check_launch("mg cycle");
+}
+
+void normalize_set(qcd_ctx* ctx, double2* X, int nvec, size_t n) {
+    double2* nr = (double2*)ctx->buf("nrm.d", nvec * sizeof(double2));
+    double2* part = (double2*)ctx->buf("nrm.part", (size_t)nvec * 64 * sizeof(double2));
+    blas_multidot(QCD_FP64, X, 1, (size_t)nvec * n, X, nvec, n, nr, part, ctx->st);
+    const double2* h = ctx->fetch(nr, nvec);
+    std::vector<double2> s(nvec);
+    for (int i = 0; i < nvec; ++i) s[i] = make_double2(h[i].x > 0 ? 1.0 / std::sqrt(h[i].x) : 0.0, 0.0);
+    double2* sd = (double2*)ctx->buf("nrm.s", nvec * sizeof(double2));
+    CK(cudaMemcpyAsync(sd, s.data(), nvec * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+    blas_scale_dev(QCD_FP64, X, X, sd, nvec, n, false, false, ctx->st);
+    CK(cudaStreamSynchronize(ctx->st));
+}
+
+void build_from_vectors(qcd_ctx* ctx, const double2* V, int nvec, const int block[4]) {
+    Coarse& c = ctx->c;
+    Blocking B = make_blocking(ctx->f.g, block);
+    if (nvec < 1 || nvec > 32) throw QcdError(QCD_EINVAL, "need 1 <= Nv <= 32");
+    if (B.bs * 6 < nvec) throw QcdError(QCD_EINVAL, "aggregate smaller than Nv");
+    bool realloc = !c.P64 || c.nv != nvec || memcmp(c.B.b, B.b, sizeof(B.b)) != 0;
+    if (realloc) {
+        auto fr = [](void* q) { if (q) cudaFree(q); };
+        fr(c.P64); fr(c.P32); fr(c.A64); fr(c.A32);
+        c.P64 = nullptr; c.P32 = nullptr; c.A64 = nullptr; c.A32 = nullptr;
+        c.B = B;
+        c.nv = nvec;
+        c.nc = 2 * nvec;
+        for (int mu = 0; mu < 4; ++mu) c.gc.L[mu] = B.cd[mu];
+        c.gc.V = B.nb;
+        c.gc.antiperiodic = 0;
+        size_t np = (size_t)B.nb * 2 * nvec * B.bs * 6;
+        size_t na = (size_t)B.nb * 9 * c.nc * c.nc;
+        CK(cudaMalloc(&c.P64, np * sizeof(double2)));
+        CK(cudaMalloc(&c.P32, np * sizeof(float2)));
+        CK(cudaMalloc(&c.A64, na * sizeof(double2)));
+        CK(cudaMalloc(&c.A32, na * sizeof(float2)));
+    }
+    mg_build_P(ctx->f, c, V, nvec, ctx->st);
+    mg_build_coarse(ctx->f, c, ctx->st);
+    check_launch("mg build");
+    c.ready = true;
+}
+
+void mg_setup_impl(qcd_ctx* ctx, int Nv, const int block[4]) {
+    require_gauge(ctx);
+    const size_t n = ctx->nfine();
+    const int prec = ctx->p.precision == QCD_FP64 ? QCD_FP64 : QCD_FP32;
+    if (ctx->test_vectors) CK(cudaFree(ctx->test_vectors));
+    ctx->test_vectors = nullptr;
+    CK(cudaMalloc(&ctx->test_vectors, (size_t)Nv * n * sizeof(double2)));
+    ctx->n_test = Nv;
+    double2* W = ctx->test_vectors;
+    blas_gaussian(W, (size_t)Nv * n, ctx->p.seed, 0x5e7000000000ull, ctx->st);
+    std::vector<double> zero_tau(Nv, 0.0);
+    void* wp = ctx->buf("setup.w", (size_t)Nv * n * esz(prec));
+    void* bp = ctx->buf("setup.b", (size_t)Nv * n * esz(prec));
+    void* xp = ctx->buf("setup.x", (size_t)Nv * n * esz(prec));
+    // iteration 1: smooth D x = 0 starting from the random vectors
+    blas_convert(QCD_FP64, W, prec, wp, (size_t)Nv * n, ctx->st);
+    blas_zero(prec, bp, (size_t)Nv * n, ctx->st);
+    smooth(ctx, prec, QCD_OP_D, Nv, bp, wp, zero_tau.data());
+    blas_convert(prec, wp, QCD_FP64, W, (size_t)Nv * n, ctx->st);
+    normalize_set(ctx, W, Nv, n);
+    build_from_vectors(ctx, W, Nv, block);
+    // later iterations: w <- M w (inverse iteration with the current cycle)
+    for (int it = 1; it < ctx->p.setup_iters; ++it) {
+        blas_convert(QCD_FP64, W, prec, bp, (size_t)Nv * n, ctx->st);
+        mg_cycle_impl(ctx, prec, QCD_OP_D, Nv, bp, xp, zero_tau.data());
+        blas_convert(prec, xp, QCD_FP64, W, (size_t)Nv * n, ctx->st);
+        normalize_set(ctx, W, Nv, n);
+        build_from_vectors(ctx, W, Nv, block);
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+}
+
+// ------------------------------------------------------------------ shifted solves
+// Correction solves: nrhs systems op(tau_j) t_j = rhs_j to inner_tol (or tol),
+// in precision prec, FGMRES + MG or plain GMRES.  Returns iterations.
+GmresResult inner_solve(qcd_ctx* ctx, int prec, int op, int nrhs, const void* rhs, void* t, const double* tau,
+                        double tol, int maxit) {
+    const size_t n = ctx->nfine();
+    std::vector<double> tv(tau, tau + nrhs);
+    OpFn A = [ctx, prec, op, nrhs, tv](const void* in, void* out) {
+        apply_op(ctx->f, prec, op, nrhs, in, out, tv.data(), ctx->st);
+    };
+    if (ctx->p.use_mg) {
+        require_mg(ctx);
+        OpFn M = [ctx, prec, op, nrhs, tv](const void* in, void* out) {
+            mg_cycle_impl(ctx, prec, op, nrhs, in, out, tv.data());
+        };
+        return gmres_batched(ctx, prec, n, nrhs, A, &M, rhs, t, tol, maxit, "fine");
+    }
+    return gmres_batched(ctx, prec, n, nrhs, A, nullptr, rhs, t, tol, maxit, "fine");
+}
+
+// (Q - tau_j) x_j = b_j to relative tol, FP64 residuals; b, x arrays of
+// nrhs FP64 fields (contiguous).  Returns the max relative residual.
+double shifted_solve_impl(qcd_ctx* ctx, int nrhs, const double2* b, double2* x, const double* tau, double tol,
+                          qcd_solve_info* info) {
+    require_gauge(ctx);
+    const size_t n = ctx->nfine();
+    const int form = ctx->p.correction_form;
+    const int prec = ctx->p.precision == QCD_FP64 ? QCD_FP64 : QCD_FP32;
+    double2* r = (double2*)ctx->buf("ss.r", n * nrhs * sizeof(double2));
+    double2* rr = (double2*)ctx->buf("ss.rr", n * nrhs * sizeof(double2));
+    void* rl = ctx->buf("ss.rl", n * nrhs * esz(prec));
+    void* tl = ctx->buf("ss.tl", n * nrhs * esz(prec));
+    double2* nr = (double2*)ctx->buf("ss.nr", 2 * nrhs * sizeof(double2));
+    double2* part = (double2*)ctx->buf("ss.part", (size_t)2 * nrhs * 64 * sizeof(double2));
+    blas_multidot(QCD_FP64, b, 1, n * nrhs, b, nrhs, n, nr, part, ctx->st);
+    std::vector<double> bn(nrhs);
+    {
+        const double2* h = ctx->fetch(nr, nrhs);
+        for (int j = 0; j < nrhs; ++j) bn[j] = std::sqrt(h[j].x);
+    }
+    blas_zero(QCD_FP64, x, n * nrhs, ctx->st);
+    blas_copy(QCD_FP64, b, r, n * nrhs, ctx->st);
+    const double floor_tol = prec == QCD_FP64 ? 1e-13 : 2e-5;
+    int iters = 0, refine = 0;
+    double worst = 1.0;
+    const int max_refine = 200;
+    const int restart = std::max(ctx->p.inner_maxiter, 20);
+    std::vector<double> relres(nrhs, 1.0);
+    for (; refine < max_refine; ++refine) {
+        // current residuals
+        blas_multidot(QCD_FP64, r, 1, n * nrhs, r, nrhs, n, nr, part, ctx->st);
+        const double2* h = ctx->fetch(nr, nrhs);
+        worst = 0.0;
+        double maxr = 0.0;
+        for (int j = 0; j < nrhs; ++j) {
+            relres[j] = bn[j] > 0 ? std::sqrt(h[j].x) / bn[j] : 0.0;
+            worst = std::max(worst, relres[j]);
+            maxr = std::max(maxr, std::sqrt(h[j].x));
+        }
+        if (worst <= tol) break;
+        // correction equation on the chosen form: (D - tau G5) c = G5 r or (Q - tau) c = r
+        if (form == QCD_OP_D) blas_gamma5(QCD_FP64, r, rr, (size_t)ctx->f.g.V * nrhs, ctx->st);
+        else blas_copy(QCD_FP64, r, rr, n * nrhs, ctx->st);
+        blas_convert(QCD_FP64, rr, prec, rl, n * nrhs, ctx->st);
+        double itol = std::max(floor_tol, std::min(0.5, 0.5 * tol / std::max(worst, 1e-300)));
+        GmresResult g = inner_solve(ctx, prec, form, nrhs, rl, tl, tau, itol, restart);
+        iters += *std::max_element(g.iters.begin(), g.iters.end());
+        blas_convert(prec, tl, QCD_FP64, rr, n * nrhs, ctx->st);
+        blas_axpby(QCD_FP64, make_double2(1, 0), rr, make_double2(1, 0), x, n * nrhs, ctx->st);
+        residual_op(ctx->f, QCD_FP64, QCD_OP_Q, nrhs, b, x, r, tau, ctx->st);
+        check_launch("refinement");
+    }
+    if (info) {
+        info->iterations = iters;
+        info->refinements = refine;
+        info->residual = worst;
+    }
+    return worst;
+}
+
+// ------------------------------------------------------------------ GD-lambda-AMG
+// tall-skinny basis transform: Out[j] = sum_i C[i + j m] In[i] (j < p), FP64
+__global__ void basis_transform_kernel(const double2* __restrict__ In, int m, const double2* __restrict__ C, int p,
+                                       double2* __restrict__ Out, size_t n) {
+    extern __shared__ double2 Cs[];
+    for (int e = threadIdx.x; e < m * p; e += blockDim.x) Cs[e] = C[e];
+    __syncthreads();
+    const int j0 = blockIdx.y * 8;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        double2 acc[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[jj] = make_double2(0, 0);
+        for (int i = 0; i < m; ++i) {
+            double2 v = In[(size_t)i * n + k];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                if (j0 + jj < p) acc[jj] += Cs[(j0 + jj) * m + i] * v;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+            if (j0 + jj < p) Out[(size_t)(j0 + jj) * n + k] = acc[jj];
+    }
+}
+void basis_transform(const double2* In, int m, const double2* C, int p, double2* Out, size_t n, cudaStream_t st) {
+    int gx = (int)std::min<size_t>((n + 255) / 256, 2048);
+    dim3 grid(gx, (p + 7) / 8);
+    const size_t sm = (size_t)m * p * sizeof(double2);
+    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(basis_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    basis_transform_kernel<<<grid, 256, sm, st>>>(In, m, C, p, Out, n);
+}
+// G[i][m] = d1[i], G[m][i] = conj d1[i]; Hm[i][m] = d2[i]; Hm[m][i] = conj d3[i]  (ld = column stride)
+__global__ void gram_update_kernel(double2* G, double2* Hm, int ld, int m, const double2* d1, const double2* d2,
+                                   const double2* d3) {
+    int i = threadIdx.x;
+    if (i > m) return;
+    G[(size_t)m * ld + i] = d1[i];
+    G[(size_t)i * ld + m] = conj(d1[i]);
+    Hm[(size_t)m * ld + i] = d2[i];
+    Hm[(size_t)i * ld + m] = conj(d3[i]);
+}
+__global__ void gather_columns_kernel(const double2* S, int m, const int* idx, int p, double2* out) {
+    for (int e = threadIdx.x; e < m * p; e += blockDim.x) out[e] = S[(size_t)idx[e / m] * m + e % m];
+}
+__global__ void normalize_vec_kernel(double2* s, int m) {
+    __shared__ double nn;
+    if (threadIdx.x == 0) {
+        double a = 0;
+        for (int i = 0; i < m; ++i) a += s[i].x * s[i].x + s[i].y * s[i].y;
+        nn = a > 0 ? 1.0 / sqrt(a) : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = nn * s[i];
+}
+
+struct GD {
+    qcd_ctx* ctx;
+    size_t n;
+    int mcap, kcap;
+    double2 *V, *W, *Vt, *Wt, *X, *G, *Hm, *Gt, *Hmt, *S, *work, *C, *dots, *part, *u, *Qu, *R, *T, *tmp;
+    double* mu;
+    int* status;
+    int* idx;
+    int m = 0;        // current basis size
+    int nlock = 0;
+    std::vector<double> lam, lres;
+
+    void alloc(int mcap_, int kcap_, int block) {
+        mcap = mcap_;
+        kcap = kcap_;
+        auto B = [&](const char* nm, size_t cnt) { return (double2*)ctx->buf(std::string("gd.") + nm, cnt * sizeof(double2)); };
+        V = B("V", (size_t)mcap * n); W = B("W", (size_t)mcap * n);
+        Vt = B("Vt", (size_t)mcap * n); Wt = B("Wt", (size_t)mcap * n);
+        X = B("X", (size_t)kcap * n);
+        G = B("G", (size_t)mcap * mcap); Hm = B("Hm", (size_t)mcap * mcap);
+        Gt = B("Gt", (size_t)mcap * mcap); Hmt = B("Hmt", (size_t)mcap * mcap);
+        S = B("S", (size_t)mcap * mcap); work = B("work", (size_t)6 * mcap * mcap); C = B("C", (size_t)mcap * mcap);
+        dots = B("dots", (size_t)4 * (mcap + kcap + 8));
+        part = B("part", (size_t)(mcap + kcap + 8) * 64);
+        u = B("u", n); Qu = B("Qu", n); R = B("R", (size_t)block * n); T = B("T", (size_t)block * n); tmp = B("tmp", n);
+        mu = (double*)ctx->buf("gd.mu", mcap * sizeof(double));
+        status = (int*)ctx->buf("gd.status", 4 * sizeof(int));
+        idx = (int*)ctx->buf("gd.idx", mcap * sizeof(int));
+        CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), ctx->st));
+    }
+    void applyQ(const double2* in, double2* out) {
+        double z = 0.0;
+        apply_op(ctx->f, QCD_FP64, QCD_OP_Q, 1, in, out, &z, ctx->st);
+    }
+    // t orthogonalised against V and X (CGS twice), normalised into V[m]; W[m] = Q V[m]
+    bool add_vector(double2* t) {
+        cudaStream_t st = ctx->st;
+        for (int pass = 0; pass < 2; ++pass) {
+            if (m > 0) {
+                blas_multidot(QCD_FP64, V, m, n, t, 1, n, dots, part, st);
+                blas_multiaxpy(QCD_FP64, V, m, n, dots, -1.0, t, 1, n, st);
+            }
+            if (nlock > 0) {
+                blas_multidot(QCD_FP64, X, nlock, n, t, 1, n, dots, part, st);
+                blas_multiaxpy(QCD_FP64, X, nlock, n, dots, -1.0, t, 1, n, st);
+            }
+        }
+        blas_multidot(QCD_FP64, t, 1, n, t, 1, n, dots, part, st);
+        const double2* h = ctx->fetch(dots, 1);
+        double nt = std::sqrt(std::max(h[0].x, 0.0));
+        if (!(nt > 1e-12) || !std::isfinite(nt)) return false;
+        blas_axpby(QCD_FP64, make_double2(1.0 / nt, 0), t, make_double2(0, 0), V + (size_t)m * n, n, st);
+        applyQ(V + (size_t)m * n, W + (size_t)m * n);
+        // new Gram column / row
+        blas_multidot(QCD_FP64, W, m + 1, n, W + (size_t)m * n, 1, n, dots, part, st);
+        blas_multidot(QCD_FP64, W, m + 1, n, V + (size_t)m * n, 1, n, dots + mcap, part, st);
+        blas_multidot(QCD_FP64, V, m + 1, n, W + (size_t)m * n, 1, n, dots + 2 * mcap, part, st);
+        gram_update_kernel<<<1, 64, 0, st>>>(G, Hm, mcap, m, dots, dots + mcap, dots + 2 * mcap);
+        check_launch("add_vector");
+        ++m;
+        return true;
+    }
+    // harmonic Ritz pairs of the current basis; returns theta sorted by |theta| with the column index
+    void harmonic(std::vector<double>& theta, std::vector<int>& col) {
+        small_harmonic_eig(G, Hm, m, mcap, mu, S, work, status, ctx->st);
+        check_launch("harmonic eig");
+        double* hm = (double*)ctx->host(m);
+        CK(cudaMemcpyAsync(hm, mu, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        theta.resize(m);
+        col.resize(m);
+        for (int i = 0; i < m; ++i) {
+            theta[i] = hm[i] != 0.0 ? 1.0 / hm[i] : INFINITY;
+            col[i] = i;
+        }
+        std::sort(col.begin(), col.end(), [&](int a, int b) {
+            double fa = std::fabs(theta[a]), fb = std::fabs(theta[b]);
+            if (fa != fb) return fa < fb;
+            return theta[a] < theta[b];
+        });
+        std::vector<double> th(m);
+        for (int i = 0; i < m; ++i) th[i] = theta[col[i]];
+        theta = th;
+    }
+    // replace the basis by V C (m x p), W C and the Gram matrices by C^H G C
+    void transform(const double2* Cm, int p) {
+        cudaStream_t st = ctx->st;
+        basis_transform(V, m, Cm, p, Vt, n, st);
+        basis_transform(W, m, Cm, p, Wt, n, st);
+        std::swap(V, Vt);
+        std::swap(W, Wt);
+        small_gram_transform(G, m, mcap, Cm, p, Gt, mcap, work, st);
+        small_gram_transform(Hm, m, mcap, Cm, p, Hmt, mcap, work, st);
+        std::swap(G, Gt);
+        std::swap(Hm, Hmt);
+        check_launch("basis transform");
+        m = p;
+    }
+};
+
+std::vector<int> select_targets(const std::vector<double>& theta, int b, const std::vector<char>& allowed) {
+    std::vector<int> same, other, out;
+    int first = -1;
+    for (int i = 0; i < (int)theta.size(); ++i) {
+        if (!allowed[i]) continue;
+        if (first < 0) first = i;
+        ((theta[i] >= 0) == (theta[first] >= 0) ? same : other).push_back(i);
+    }
+    size_t a = 0, c = 0;
+    while ((int)out.size() < b && (a < same.size() || c < other.size())) {
+        if (a < same.size()) out.push_back(same[a++]);
+        if ((int)out.size() < b && c < other.size()) out.push_back(other[c++]);
+        if (b == 1) break;
+    }
+    return out;
+}
+
+int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qcd_eig_info* info) {
+    require_gauge(ctx);
+    const qcd_params& P = ctx->p;
+    if (P.use_mg) require_mg(ctx);
+    const size_t n = ctx->nfine();
+    const int block = P.block;
+    const int prec = P.precision == QCD_FP64 ? QCD_FP64 : QCD_FP32;
+    cudaStream_t st = ctx->st;
+    GD gd{};
+    gd.ctx = ctx;
+    gd.n = n;
+    const int n0 = P.use_mg ? ctx->n_test : P.n_init;
+    if (n0 + block > P.m_max) throw QcdError(QCD_EINVAL, "m_max too small for the start basis");
+    gd.alloc(P.m_max + block, k + P.m_max + 2 * block + 8, block);
+    double2* t0 = gd.tmp;
+    // start basis: setup test vectors (or random vectors without MG)
+    for (int i = 0; i < n0; ++i) {
+        if (P.use_mg) blas_copy(QCD_FP64, ctx->test_vectors + (size_t)i * n, t0, n, st);
+        else blas_gaussian(t0, n, P.seed, 0x1a0000000000ull + (unsigned long long)i * n, st);
+        gd.add_vector(t0);
+    }
+    for (int j = 0; j < block; ++j) blas_gaussian(gd.T + (size_t)j * n, n, P.seed, 0x2b0000000000ull + j * n, st);
+    int nT = block;
+    int outer = 0, inner = 0, updates = 0, locks_since_update = 0;
+    bool finished = false;
+    double2* vbuf = (double2*)ctx->buf("gd.vupd", (size_t)std::max(1, ctx->n_test) * n * sizeof(double2));
+    std::vector<double> theta;
+    std::vector<int> col;
+    std::vector<double> tsel;
+    int rnd = 0;
+    while (!finished && outer < P.max_outer) {
+        ++outer;
+        int added = 0;
+        for (int j = 0; j < nT; ++j) added += gd.add_vector(gd.T + (size_t)j * n) ? 1 : 0;
+        if (added == 0) {
+            blas_gaussian(gd.T, n, P.seed, 0x3c0000000000ull + (unsigned long long)(rnd++) * n, st);
+            nT = 1;
+            continue;
+        }
+        std::vector<int> tg;
+        while (true) {
+            gd.harmonic(theta, col);
+            std::vector<char> allowed(theta.size(), 1);
+            if (gd.nlock >= k) {
+                std::vector<double> al(gd.lam.size());
+                for (size_t i = 0; i < al.size(); ++i) al[i] = std::fabs(gd.lam[i]);
+                std::nth_element(al.begin(), al.begin() + (k - 1), al.end());
+                double lim = al[k - 1];
+                int cnt = 0;
+                for (size_t i = 0; i < theta.size(); ++i) { allowed[i] = std::fabs(theta[i]) < lim; cnt += allowed[i]; }
+                if (cnt == 0) { finished = true; break; }
+            }
+            tg = select_targets(theta, block, allowed);
+            bool locked = false;
+            tsel.clear();
+            int nr = 0;
+            for (int ti : tg) {
+                const double2* s = gd.S + (size_t)col[ti] * gd.m;   // column of S (ld = m)
+                blas_zero(QCD_FP64, gd.u, n, st);
+                blas_zero(QCD_FP64, gd.Qu, n, st);
+                blas_multiaxpy(QCD_FP64, gd.V, gd.m, n, s, 1.0, gd.u, 1, n, st);
+                blas_multiaxpy(QCD_FP64, gd.W, gd.m, n, s, 1.0, gd.Qu, 1, n, st);
+                blas_multidot(QCD_FP64, gd.u, 1, n, gd.u, 1, n, gd.dots, gd.part, st);
+                blas_multidot(QCD_FP64, gd.u, 1, n, gd.Qu, 1, n, gd.dots + 1, gd.part, st);
+                const double2* h = ctx->fetch(gd.dots, 2);
+                const double uu = h[0].x;
+                const double rho = h[1].x / uu;
+                const double iu = 1.0 / std::sqrt(uu);
+                double2* rj = gd.R + (size_t)nr * n;
+                // r = (Qu - rho u)/||u|| ; u <- u/||u||
+                blas_copy(QCD_FP64, gd.Qu, rj, n, st);
+                blas_axpby(QCD_FP64, make_double2(-rho * iu, 0), gd.u, make_double2(iu, 0), rj, n, st);
+                blas_axpby(QCD_FP64, make_double2(0, 0), gd.u, make_double2(iu, 0), gd.u, n, st);
+                blas_multidot(QCD_FP64, rj, 1, n, rj, 1, n, gd.dots, gd.part, st);
+                const double2* hr = ctx->fetch(gd.dots, 1);
+                const double rn = std::sqrt(std::max(hr[0].x, 0.0));
+                if (rn <= tol) {
+                    if (gd.nlock >= gd.kcap) throw QcdError(QCD_EINVAL, "too many locked vectors");
+                    blas_copy(QCD_FP64, gd.u, gd.X + (size_t)gd.nlock * n, n, st);
+                    gd.lam.push_back(rho);
+                    gd.lres.push_back(rn);
+                    ++gd.nlock;
+                    // deflate: V <- V C with C the complement of s/||s||
+                    CK(cudaMemcpyAsync(gd.work, s, gd.m * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+                    normalize_vec_kernel<<<1, 64, 0, st>>>(gd.work, gd.m);
+                    small_complement(gd.work, gd.m, gd.C, nullptr, st);
+                    gd.transform(gd.C, gd.m - 1);
+                    ++locks_since_update;
+                    locked = true;
+                    if (P.verbose)
+                        fprintf(stderr, "[qcd_eigs] lock %d lambda=% .12e res=%.2e outer=%d m=%d\n", gd.nlock, rho, rn,
+                                outer, gd.m);
+                    break;
+                }
+                tsel.push_back(theta[ti]);
+                ++nr;
+            }
+            if (!locked) break;
+            if (gd.m == 0) break;
+            if (P.use_mg && gd.nlock >= ctx->n_test && locks_since_update >= P.update_every) {
+                std::vector<double> th2;
+                std::vector<int> c2;
+                gd.harmonic(th2, c2);
+                double target = th2[0];
+                std::vector<int> ord(gd.nlock);
+                std::iota(ord.begin(), ord.end(), 0);
+                std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+                    return std::fabs(gd.lam[a] - target) < std::fabs(gd.lam[b] - target);
+                });
+                std::vector<int> pick(ord.begin(), ord.begin() + ctx->n_test);
+                std::sort(pick.begin(), pick.end());
+                for (int i = 0; i < ctx->n_test; ++i)
+                    blas_copy(QCD_FP64, gd.X + (size_t)pick[i] * n, vbuf + (size_t)i * n, n, st);
+                build_from_vectors(ctx, vbuf, ctx->n_test, ctx->c.B.b);
+                locks_since_update = 0;
+                ++updates;
+            }
+        }
+        if (finished) break;
+        if (gd.m == 0 || tsel.empty()) {
+            blas_gaussian(gd.T, n, P.seed, 0x3c0000000000ull + (unsigned long long)(rnd++) * n, st);
+            nT = 1;
+            continue;
+        }
+        // correction equations, batched over the targets
+        const int nb = (int)tsel.size();
+        void* rl = ctx->buf("gd.rl", (size_t)nb * n * esz(prec));
+        void* tl = ctx->buf("gd.tl", (size_t)nb * n * esz(prec));
+        if (P.correction_form == QCD_OP_D) blas_gamma5(QCD_FP64, gd.R, gd.R, (size_t)ctx->f.g.V * nb, st);
+        blas_convert(QCD_FP64, gd.R, prec, rl, (size_t)nb * n, st);
+        GmresResult g = inner_solve(ctx, prec, P.correction_form, nb, rl, tl, tsel.data(), P.inner_tol,
+                                    P.use_mg ? P.inner_maxiter : P.plain_maxiter);
+        for (int v : g.iters) inner += v;
+        blas_convert(prec, tl, QCD_FP64, gd.T, (size_t)nb * n, st);
+        nT = nb;
+        // thick restart
+        if (gd.m + nT > P.m_max) {
+            std::vector<double> th;
+            std::vector<int> cl;
+            gd.harmonic(th, cl);
+            int keep = std::min(P.m_min, gd.m);
+            CK(cudaMemcpyAsync(gd.idx, cl.data(), keep * sizeof(int), cudaMemcpyHostToDevice, st));
+            gather_columns_kernel<<<1, 256, 0, st>>>(gd.S, gd.m, gd.idx, keep, gd.work);
+            small_qr(gd.work, gd.m, keep, gd.m, gd.C, nullptr, st);
+            gd.transform(gd.C, keep);
+            CK(cudaStreamSynchronize(st));
+        }
+    }
+    // output: k smallest |lambda| of the locked pairs
+    std::vector<int> ord(gd.nlock);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+        double fa = std::fabs(gd.lam[a]), fb = std::fabs(gd.lam[b]);
+        if (fa != fb) return fa < fb;
+        return gd.lam[a] < gd.lam[b];
+    });
+    const int nout = std::min(k, gd.nlock);
+    double maxres = 0.0;
+    for (int i = 0; i < nout; ++i) {
+        lambda[i] = gd.lam[ord[i]];
+        maxres = std::max(maxres, gd.lres[ord[i]]);
+        if (Vout) blas_copy(QCD_FP64, gd.X + (size_t)ord[i] * n, Vout + (size_t)i * n, n, st);
+    }
+    for (int i = nout; i < k; ++i) lambda[i] = NAN;
+    CK(cudaStreamSynchronize(st));
+    const bool ok = finished && nout == k;
+    if (info) {
+        info->outer = outer;
+        info->inner = inner;
+        info->locked = gd.nlock;
+        info->updates = updates;
+        info->converged = ok ? 1 : 0;
+        info->max_residual = maxres;
+    }
+    return ok ? QCD_OK : QCD_ENOCONV;
+}
+
+void check_align(const void* p, const char* what) {
+    if (((uintptr_t)p) & 15) throw QcdError(QCD_EINVAL, std::string(what) + " must be 16-byte aligned");
+}
+
+template <typename F>
+int guarded(qcd_ctx* ctx, F&& fn) {
+    if (!ctx) return QCD_EINVAL;
+    try {
+        ctx->err.clear();
+        return fn();
+    } catch (const QcdError& e) {
+        ctx->err = e.what();
+        return e.code;
+    } catch (const std::exception& e) {
+        ctx->err = e.what();
+        return QCD_ECUDA;
+    }
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void qcd_default_params(qcd_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->antiperiodic_t = 1;
+    p->precision = QCD_MIXED;
+    p->correction_form = QCD_OP_D;
+    p->use_mg = 1;
+    p->setup_iters = 6;
+    p->smoother = QCD_SMOOTHER_SAP;
+    p->nu = 4;
+    for (int mu = 0; mu < 4; ++mu) p->sap_block[mu] = 2;
+    p->sap_block_iters = 10;
+    p->sap_block_tol = 1e-1;
+    p->gmres_smooth_iters = 4;
+    p->inner_tol = 1e-1;
+    p->inner_maxiter = 5;
+    p->coarse_tol = 0.5;
+    p->coarse_maxiter = 100;
+    p->plain_maxiter = 20;
+    p->m_min = 30;
+    p->m_max = 50;
+    p->block = 2;
+    p->n_init = 8;
+    p->update_every = 1;
+    p->max_outer = 100000;
+    p->seed = 20200417ull;
+    p->verbose = 0;
+}
+
+int qcd_create(qcd_ctx** out, const qcd_params* p, void* stream) {
+    if (!out || !p) return QCD_EINVAL;
+    *out = nullptr;
+    qcd_ctx* ctx = new (std::nothrow) qcd_ctx();
+    if (!ctx) return QCD_ENOMEM;
+    try {
+        validate_params(*p);
+    } catch (const QcdError& e) {
+        delete ctx;
+        return e.code;
+    }
+    ctx->p = *p;
+    ctx->st = (cudaStream_t)stream;
+    *out = ctx;
+    return QCD_OK;
+}
+
+int qcd_destroy(qcd_ctx* ctx) {
+    if (!ctx) return QCD_EINVAL;
+    cudaStreamSynchronize(ctx->st);
+    delete ctx;
+    return QCD_OK;
+}
+
+const char* qcd_last_error(qcd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int qcd_set_params(qcd_ctx* ctx, const qcd_params* p) {
+    return guarded(ctx, [&]() {
+        if (!p) throw QcdError(QCD_EINVAL, "null params");
+        validate_params(*p);
+        bool sap_changed = memcmp(p->sap_block, ctx->p.sap_block, sizeof(p->sap_block)) != 0;
+        bool bc_changed = p->antiperiodic_t != ctx->p.antiperiodic_t;
+        ctx->p = *p;
+        if (sap_changed && ctx->have_sap) {
+            cudaFree(ctx->sap.blocks_of_colour[0]);
+            cudaFree(ctx->sap.blocks_of_colour[1]);
+            ctx->sap.blocks_of_colour[0] = ctx->sap.blocks_of_colour[1] = nullptr;
+            ctx->have_sap = false;
+        }
+        if (bc_changed) ctx->f.g.antiperiodic = p->antiperiodic_t;
+        return QCD_OK;
+    });
+}
+
+int qcd_set_gauge(qcd_ctx* ctx, const double* U, const int dims[4], double m0, double csw) {
+    return guarded(ctx, [&]() {
+        if (!U || !dims) throw QcdError(QCD_EINVAL, "null gauge field or dims");
+        long long V = 1;
+        for (int mu = 0; mu < 4; ++mu) {
+            if (dims[mu] < 2 || dims[mu] > 4096) throw QcdError(QCD_EINVAL, "lattice extents must be in [2, 4096]");
+            V *= dims[mu];
+        }
+        if (V > (1ll << 28)) throw QcdError(QCD_EINVAL, "lattice too large");
+        CK(cudaStreamSynchronize(ctx->st));
+        ctx->release();
+        ctx->have_gauge = false;
+        FineOp& f = ctx->f;
+        for (int mu = 0; mu < 4; ++mu) f.g.L[mu] = dims[mu];
+        f.g.V = (int)V;
+        f.g.antiperiodic = ctx->p.antiperiodic_t;
+        f.m0 = m0;
+        f.csw = csw;
+        const size_t nl = (size_t)V * 36;
+        CK(cudaMalloc(&f.U64, nl * sizeof(double2)));
+        CK(cudaMalloc(&f.U32, nl * sizeof(float2)));
+        CK(cudaMalloc(&f.A64, (size_t)V * 72 * sizeof(double)));
+        CK(cudaMalloc(&f.A32, (size_t)V * 72 * sizeof(float)));
+        CK(cudaMemcpyAsync(f.U64, U, nl * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+        blas_convert(QCD_FP64, f.U64, QCD_FP32, f.U32, nl, ctx->st);
+        launch_clover_build(f, ctx->st);
+        check_launch("set_gauge");
+        CK(cudaStreamSynchronize(ctx->st));
+        ctx->have_gauge = true;
+        return QCD_OK;
+    });
+}
+
+int qcd_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* in, void* out, const double* tau) {
+    return guarded(ctx, [&]() {
+        require_gauge(ctx);
+        if (op != QCD_OP_D && op != QCD_OP_Q) throw QcdError(QCD_EINVAL, "bad op");
+        if (prec != QCD_FP64 && prec != QCD_FP32) throw QcdError(QCD_EINVAL, "bad precision");
+        if (nrhs < 1 || nrhs > kMaxRhs || !in || !out || !tau) throw QcdError(QCD_EINVAL, "bad nrhs or pointers");
+        check_align(in, "in");
+        check_align(out, "out");
+        const size_t bytes = ctx->nfine() * nrhs * esz(prec);
+        const char* a = (const char*)in;
+        const char* b = (const char*)out;
+        if (a < b + bytes && b < a + bytes) throw QcdError(QCD_EINVAL, "in and out overlap");
+        apply_op(ctx->f, prec, op, nrhs, in, out, tau, ctx->st);
+        check_launch("apply");
+        return QCD_OK;
+    });
+}
+
+int qcd_apply_Q(qcd_ctx* ctx, const void* in, void* out, double tau) {
+    return qcd_apply(ctx, QCD_OP_Q, QCD_FP64, 1, in, out, &tau);
+}
+
+int qcd_mg_setup(qcd_ctx* ctx, int Nv, const int block[4]) {
+    return guarded(ctx, [&]() {
+        if (!block) throw QcdError(QCD_EINVAL, "null block");
+        if (Nv < 1 || Nv > 32) throw QcdError(QCD_EINVAL, "need 1 <= Nv <= 32");
+        mg_setup_impl(ctx, Nv, block);
+        return QCD_OK;
+    });
+}
+
+int qcd_mg_update_from_eigvecs(qcd_ctx* ctx, const void* V, int nvec) {
+    return guarded(ctx, [&]() {
+        require_gauge(ctx);
+        if (!V || nvec < 1 || nvec > 32) throw QcdError(QCD_EINVAL, "need 1 <= nvec <= 32");
+        const int* blk = ctx->c.ready ? ctx->c.B.b : ctx->p.sap_block;
+        int b[4] = {blk[0], blk[1], blk[2], blk[3]};
+        build_from_vectors(ctx, (const double2*)V, nvec, b);
+        if (ctx->n_test != nvec || !ctx->test_vectors) {
+            if (ctx->test_vectors) CK(cudaFree(ctx->test_vectors));
+            CK(cudaMalloc(&ctx->test_vectors, (size_t)nvec * ctx->nfine() * sizeof(double2)));
+            ctx->n_test = nvec;
+        }
+        CK(cudaMemcpyAsync(ctx->test_vectors, V, (size_t)nvec * ctx->nfine() * sizeof(double2),
+                           cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        return QCD_OK;
+    });
+}
+
+int qcd_mg_info(qcd_ctx* ctx, int out[8]) {
+    return guarded(ctx, [&]() {
+        require_mg(ctx);
+        out[0] = ctx->c.gc.V;
+        out[1] = ctx->c.nv;
+        for (int mu = 0; mu < 4; ++mu) out[2 + mu] = ctx->c.gc.L[mu];
+        out[6] = ctx->c.B.bs;
+        out[7] = 0;
+        return QCD_OK;
+    });
+}
+
+int qcd_mg_restrict(qcd_ctx* ctx, int prec, int nrhs, const void* r, void* xc) {
+    return guarded(ctx, [&]() {
+        require_mg(ctx);
+        if (nrhs < 1 || nrhs > kMaxRhs || !r || !xc) throw QcdError(QCD_EINVAL, "bad arguments");
+        mg_restrict(ctx->f, ctx->c, prec, nrhs, r, xc, ctx->st);
+        check_launch("restrict");
+        return QCD_OK;
+    });
+}
+
+int qcd_mg_prolong(qcd_ctx* ctx, int prec, int nrhs, const void* xc, void* x) {
+    return guarded(ctx, [&]() {
+        require_mg(ctx);
+        if (nrhs < 1 || nrhs > kMaxRhs || !x || !xc) throw QcdError(QCD_EINVAL, "bad arguments");
+        mg_prolong(ctx->f, ctx->c, prec, nrhs, xc, x, false, ctx->st);
+        check_launch("prolong");
+        return QCD_OK;
+    });
+}
+
+int qcd_coarse_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* x, void* y, const double* tau) {
+    return guarded(ctx, [&]() {
+        require_mg(ctx);
+        if (nrhs < 1 || nrhs > kMaxRhs || !x || !y || !tau) throw QcdError(QCD_EINVAL, "bad arguments");
+        coarse_apply(ctx->c, prec, op, nrhs, x, y, tau, ctx->st);
+        check_launch("coarse apply");
+        return QCD_OK;
+    });
+}
+
+int qcd_mg_get_P(qcd_ctx* ctx, double* P_host) {
+    return guarded(ctx, [&]() {
+        require_mg(ctx);
+        size_t np = (size_t)ctx->c.B.nb * 2 * ctx->c.nv * ctx->c.B.bs * 6;
+        CK(cudaMemcpyAsync(P_host, ctx->c.P64, np * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        return QCD_OK;
+    });
+}
+
+int qcd_mg_get_coarse(qcd_ctx* ctx, double* A_host) {
+    return guarded(ctx, [&]() {
+        require_mg(ctx);
+        const int nc = ctx->c.nc;
+        size_t na = (size_t)ctx->c.B.nb * 9 * nc * nc;
+        std::vector<double2> tmp(na);
+        CK(cudaMemcpyAsync(tmp.data(), ctx->c.A64, na * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        // device storage is [site][d][col][row]; the ABI returns [site][d][row][col]
+        double2* out = (double2*)A_host;
+        for (size_t blk = 0; blk < (size_t)ctx->c.B.nb * 9; ++blk)
+            for (int r = 0; r < nc; ++r)
+                for (int c = 0; c < nc; ++c) out[(blk * nc + r) * nc + c] = tmp[(blk * nc + c) * nc + r];
+        return QCD_OK;
+    });
+}
+
+int qcd_sap(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x, const double* tau, int sweeps,
+            double block_tol) {
+    return guarded(ctx, [&]() {
+        require_gauge(ctx);
+        if (nrhs < 1 || nrhs > kMaxRhs || !b || !x || !tau || sweeps < 0) throw QcdError(QCD_EINVAL, "bad arguments");
+        check_align(b, "b");
+        check_align(x, "x");
+        sap_smooth(ctx, prec, op, nrhs, b, x, tau, sweeps, block_tol);
+        CK(cudaStreamSynchronize(ctx->st));
+        return QCD_OK;
+    });
+}
+
+int qcd_mg_cycle(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x, const double* tau) {
+    return guarded(ctx, [&]() {
+        require_mg(ctx);
+        if (nrhs < 1 || nrhs > kMaxRhs || !b || !x || !tau) throw QcdError(QCD_EINVAL, "bad arguments");
+        check_align(b, "b");
+        check_align(x, "x");
+        mg_cycle_impl(ctx, prec, op, nrhs, b, x, tau);
+        CK(cudaStreamSynchronize(ctx->st));
+        return QCD_OK;
+    });
+}
+
+int qcd_shifted_solve_batched(qcd_ctx* ctx, int nrhs, const void* const* b, void* const* x, const double* tau,
+                              double tol, qcd_solve_info* info) {
+    return guarded(ctx, [&]() {
+        require_gauge(ctx);
+        if (nrhs < 1 || nrhs > kMaxRhs || !b || !x || !tau || !(tol > 0)) throw QcdError(QCD_EINVAL, "bad arguments");
+        double t0 = now_s();
+        const size_t n = ctx->nfine();
+        double2* bb = (double2*)ctx->buf("ssb.b", n * nrhs * sizeof(double2));
+        double2* xx = (double2*)ctx->buf("ssb.x", n * nrhs * sizeof(double2));
+        for (int j = 0; j < nrhs; ++j) {
+            if (!b[j] || !x[j]) throw QcdError(QCD_EINVAL, "null field");
+            CK(cudaMemcpyAsync(bb + (size_t)j * n, b[j], n * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+        }
+        double res = shifted_solve_impl(ctx, nrhs, bb, xx, tau, tol, info);
+        for (int j = 0; j < nrhs; ++j)
+            CK(cudaMemcpyAsync(x[j], xx + (size_t)j * n, n * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if (info) info->seconds = now_s() - t0;
+        return res <= tol ? QCD_OK : QCD_ENOCONV;
+    });
+}
+
+int qcd_shifted_solve(qcd_ctx* ctx, const void* b, void* x, double tau, double tol, qcd_solve_info* info) {
+    const void* bs[1] = {b};
+    void* xs[1] = {x};
+    return qcd_shifted_solve_batched(ctx, 1, bs, xs, &tau, tol, info);
+}
+
+int qcd_eigs(qcd_ctx* ctx, int k, double tol, double* lambda, void* V, qcd_eig_info* info) {
+    return guarded(ctx, [&]() {
+        if (k < 1 || !lambda || !(tol > 0)) throw QcdError(QCD_EINVAL, "bad arguments");
+        double t0 = now_s();
+        int rc = eigs_impl(ctx, k, tol, lambda, (double2*)V, info);
+        if (info) info->seconds = now_s() - t0;
+        if (rc == QCD_ENOCONV) ctx->err = "qcd_eigs: outer iteration cap reached";
+        return rc;
+    });
+}
+
+}  // extern "C"

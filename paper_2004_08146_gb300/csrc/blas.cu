@@ -1,0 +1,214 @@
+// Level-1 kernels on complex fields: copies, precision conversion, batched
+// multi-dot products (deterministic two-pass reductions), multi-axpy for
+// Gram-Schmidt (Algorithm 2, first line of the loop; FGMRES Arnoldi), Gamma5
+// and a counter-based Gaussian generator for random start vectors.
+#include "internal.h"
+
+namespace qcd {
+
+namespace {
+constexpr int kThreads = 256;
+
+inline int grid_for(size_t n, int th = kThreads) {
+    size_t g = (n + th - 1) / th;
+    return (int)(g > 1048576 ? 1048576 : (g == 0 ? 1 : g));
+}
+
+template <typename Z>
+__global__ void zero_kernel(Z* x, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = Z{0, 0};
+}
+template <typename Zi, typename Zo>
+__global__ void convert_kernel(const Zi* __restrict__ x, Zo* __restrict__ y, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = cvt<Zo>(x[i]);
+}
+
+// partial[(v * nsplit) + split] = sum over this split of conj(X[i][j]) w[j]
+template <typename Z>
+__global__ void multidot_partial_kernel(const Z* __restrict__ X, size_t xstride_vec, const Z* __restrict__ w,
+                                        int nrhs, size_t n, int nsplit, double2* __restrict__ partial) {
+    const int v = blockIdx.y;            // v = i * nrhs + j
+    const int i = v / nrhs, j = v % nrhs;
+    const Z* x = X + (size_t)i * xstride_vec + (size_t)j * n;
+    const Z* y = w + (size_t)j * n;
+    const size_t chunk = (n + nsplit - 1) / nsplit;
+    const size_t lo = (size_t)blockIdx.x * chunk;
+    const size_t hi = lo + chunk < n ? lo + chunk : n;
+    double re = 0.0, im = 0.0;
+    for (size_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        Z a = x[k], b = y[k];
+        re += (double)a.x * b.x + (double)a.y * b.y;
+        im += (double)a.x * b.y - (double)a.y * b.x;
+    }
+    __shared__ double sre[32], sim[32];
+    re = warp_sum(re);
+    im = warp_sum(im);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sre[wid] = re; sim[wid] = im; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        re = lane < nw ? sre[lane] : 0.0;
+        im = lane < nw ? sim[lane] : 0.0;
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) partial[(size_t)v * nsplit + blockIdx.x] = make_double2(re, im);
+    }
+}
+__global__ void multidot_final_kernel(const double2* __restrict__ partial, int nsplit, int nv, double2* dots) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    double2 s = make_double2(0, 0);
+    for (int k = 0; k < nsplit; ++k) s += partial[(size_t)v * nsplit + k];
+    dots[v] = s;
+}
+
+template <typename Z, typename R>
+__global__ void multiaxpy_kernel(const Z* __restrict__ X, int nvec, size_t xstride_vec, const double2* __restrict__ c,
+                                 double sign, Z* __restrict__ w, int nrhs, size_t n) {
+    const size_t total = n * nrhs;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / n);
+        const size_t k = t - (size_t)j * n;
+        double2 acc = make_double2(0, 0);
+        for (int i = 0; i < nvec; ++i) {
+            double2 ci = c[i * nrhs + j];
+            Z xv = X[(size_t)i * xstride_vec + (size_t)j * n + k];
+            acc.x += ci.x * xv.x - ci.y * xv.y;
+            acc.y += ci.x * xv.y + ci.y * xv.x;
+        }
+        Z o = w[t];
+        o.x = (R)(o.x + sign * acc.x);
+        o.y = (R)(o.y + sign * acc.y);
+        w[t] = o;
+    }
+}
+
+template <typename Z, typename R>
+__global__ void scale_dev_kernel(const Z* __restrict__ x, Z* __restrict__ y, const double2* __restrict__ alpha,
+                                 int nrhs, size_t n, bool invert_real, bool accumulate) {
+    const size_t total = n * nrhs;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / n);
+        double2 a = alpha[j];
+        if (invert_real) a = make_double2(a.x != 0.0 ? 1.0 / a.x : 0.0, 0.0);
+        Z xv = x[t];
+        double re = a.x * xv.x - a.y * xv.y, im = a.x * xv.y + a.y * xv.x;
+        if (accumulate) { re += y[t].x; im += y[t].y; }
+        Z o; o.x = (R)re; o.y = (R)im;
+        y[t] = o;
+    }
+}
+
+template <typename Z>
+__global__ void gamma5_kernel(const Z* __restrict__ x, Z* __restrict__ y, size_t nsites) {
+    const size_t total = nsites * 12;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        Z v = x[t];
+        if ((t % 12) >= 6) { v.x = -v.x; v.y = -v.y; }
+        y[t] = v;
+    }
+}
+
+template <typename Z, typename R>
+__global__ void axpby_kernel(double2 a, const Z* __restrict__ x, double2 b, Z* __restrict__ y, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        Z xv = x[t], yv = y[t];
+        double re = a.x * xv.x - a.y * xv.y + b.x * yv.x - b.y * yv.y;
+        double im = a.x * xv.y + a.y * xv.x + b.x * yv.y + b.y * yv.x;
+        Z o; o.x = (R)re; o.y = (R)im;
+        y[t] = o;
+    }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) as a counter-based hash.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// Box-Muller: complex Gaussian with N(0,1) real and imaginary parts.
+__global__ void gaussian_kernel(double2* x, size_t n, unsigned long long seed, unsigned long long offset) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        unsigned long long k = splitmix64(seed ^ splitmix64(offset + t));
+        unsigned long long a = splitmix64(k), b = splitmix64(k + 1);
+        double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740993.0);   // (0, 1]
+        double u2 = (b >> 11) * (1.0 / 9007199254740992.0);           // [0, 1)
+        double r = sqrt(-2.0 * log(u1));
+        double s, c;
+        sincospi(2.0 * u2, &s, &c);
+        x[t] = make_double2(r * c, r * s);
+    }
+}
+}  // namespace
+
+void blas_zero(int prec, void* x, size_t n, cudaStream_t st) {
+    if (prec == QCD_FP64) zero_kernel<double2><<<grid_for(n), kThreads, 0, st>>>((double2*)x, n);
+    else zero_kernel<float2><<<grid_for(n), kThreads, 0, st>>>((float2*)x, n);
+}
+void blas_copy(int prec, const void* x, void* y, size_t n, cudaStream_t st) {
+    cudaMemcpyAsync(y, x, n * (prec == QCD_FP64 ? sizeof(double2) : sizeof(float2)), cudaMemcpyDeviceToDevice, st);
+}
+void blas_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, cudaStream_t st) {
+    if (prec_in == prec_out) { blas_copy(prec_in, x, y, n, st); return; }
+    if (prec_in == QCD_FP64)
+        convert_kernel<double2, float2><<<grid_for(n), kThreads, 0, st>>>((const double2*)x, (float2*)y, n);
+    else
+        convert_kernel<float2, double2><<<grid_for(n), kThreads, 0, st>>>((const float2*)x, (double2*)y, n);
+}
+void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const void* w, int nrhs, size_t n,
+                   double2* dots, double2* partial, cudaStream_t st) {
+    if (nvec <= 0) return;
+    int nsplit = (int)((n + 32767) / 32768);
+    if (nsplit > 64) nsplit = 64;
+    if (nsplit < 1) nsplit = 1;
+    dim3 grid(nsplit, nvec * nrhs);
+    if (prec == QCD_FP64)
+        multidot_partial_kernel<double2><<<grid, kThreads, 0, st>>>((const double2*)X, xstride_vec, (const double2*)w,
+                                                                   nrhs, n, nsplit, partial);
+    else
+        multidot_partial_kernel<float2><<<grid, kThreads, 0, st>>>((const float2*)X, xstride_vec, (const float2*)w,
+                                                                  nrhs, n, nsplit, partial);
+    int nv = nvec * nrhs;
+    multidot_final_kernel<<<(nv + 127) / 128, 128, 0, st>>>(partial, nsplit, nv, dots);
+}
+void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const double2* c, double sign, void* w,
+                    int nrhs, size_t n, cudaStream_t st) {
+    if (nvec <= 0) return;
+    size_t total = n * nrhs;
+    if (prec == QCD_FP64)
+        multiaxpy_kernel<double2, double><<<grid_for(total), kThreads, 0, st>>>((const double2*)X, nvec, xstride_vec, c,
+                                                                              sign, (double2*)w, nrhs, n);
+    else
+        multiaxpy_kernel<float2, float><<<grid_for(total), kThreads, 0, st>>>((const float2*)X, nvec, xstride_vec, c,
+                                                                            sign, (float2*)w, nrhs, n);
+}
+void blas_scale_dev(int prec, const void* x, void* y, const double2* alpha, int nrhs, size_t n, bool invert_real,
+                    bool accumulate, cudaStream_t st) {
+    size_t total = n * nrhs;
+    if (prec == QCD_FP64)
+        scale_dev_kernel<double2, double><<<grid_for(total), kThreads, 0, st>>>((const double2*)x, (double2*)y, alpha,
+                                                                              nrhs, n, invert_real, accumulate);
+    else
+        scale_dev_kernel<float2, float><<<grid_for(total), kThreads, 0, st>>>((const float2*)x, (float2*)y, alpha,
+                                                                            nrhs, n, invert_real, accumulate);
+}
+void blas_gamma5(int prec, const void* x, void* y, size_t nsites, cudaStream_t st) {
+    size_t total = nsites * 12;
+    if (prec == QCD_FP64) gamma5_kernel<double2><<<grid_for(total), kThreads, 0, st>>>((const double2*)x, (double2*)y, nsites);
+    else gamma5_kernel<float2><<<grid_for(total), kThreads, 0, st>>>((const float2*)x, (float2*)y, nsites);
+}
+void blas_gaussian(double2* x, size_t n, unsigned long long seed, unsigned long long offset, cudaStream_t st) {
+    gaussian_kernel<<<grid_for(n), kThreads, 0, st>>>(x, n, seed, offset);
+}
+void blas_axpby(int prec, double2 a, const void* x, double2 b, void* y, size_t n, cudaStream_t st) {
+    if (prec == QCD_FP64)
+        axpby_kernel<double2, double><<<grid_for(n), kThreads, 0, st>>>(a, (const double2*)x, b, (double2*)y, n);
+    else
+        axpby_kernel<float2, float><<<grid_for(n), kThreads, 0, st>>>(a, (const float2*)x, b, (float2*)y, n);
+}
+
+}  // namespace qcd

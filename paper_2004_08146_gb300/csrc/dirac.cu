@@ -1,0 +1,214 @@
+// Fine-lattice operator kernels: clover construction (Sec. 4, Table 1 clover
+// term; Sheikholeslami-Wohlert) and the Wilson-clover stencil of Eq. 2.5 in
+// the shifted forms D - tau Gamma5 (Eq. 3.7) and Q - tau (Eq. 3.6).
+#include "internal.h"
+#include "dirac.cuh"
+
+namespace qcd {
+
+// ------------------------------------------------------------------ SU(3) helpers
+template <typename R> struct M3 { cplx<R> e[3][3]; };
+__device__ __forceinline__ M3<double> m3_load(const double2* p) {
+    M3<double> m;
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) m.e[a][b] = p[a * 3 + b];
+    return m;
+}
+__device__ __forceinline__ M3<double> m3_mul(const M3<double>& x, const M3<double>& y) {
+    M3<double> r;
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+        double2 s = make_double2(0, 0);
+        for (int c = 0; c < 3; ++c) s += x.e[a][c] * y.e[c][b];
+        r.e[a][b] = s;
+    }
+    return r;
+}
+__device__ __forceinline__ M3<double> m3_dag(const M3<double>& x) {
+    M3<double> r;
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) r.e[a][b] = conj(x.e[b][a]);
+    return r;
+}
+
+__device__ __forceinline__ int shifted(const Geom& g, const int x[4], int mu, int dmu, int nu, int dnu) {
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    y[mu] = (y[mu] + dmu + g.L[mu]) % g.L[mu];
+    y[nu] = (y[nu] + dnu + g.L[nu]) % g.L[nu];
+    return site_index(g, y);
+}
+
+// sigma^chi_{mu nu} (2x2, chirality block chi) = (i/2)(B_mu B_nu^H - B_nu B_mu^H)
+// for chi = 0 and (i/2)(B_mu^H B_nu - B_nu^H B_mu) for chi = 1.
+__device__ void spin_block_dense(int mu, bool herm, double2 M[2][2]) {
+    SpinMono m = herm ? kBH(mu) : kB(mu);
+    for (int r = 0; r < 2; ++r) for (int c = 0; c < 2; ++c) M[r][c] = make_double2(0, 0);
+    for (int r = 0; r < 2; ++r) M[r][m.perm[r]] = mul_ipow(make_double2(1, 0), m.ph[r]);
+}
+__device__ void sigma_block(int mu, int nu, int chi, double2 S[2][2]) {
+    double2 A[2][2], Bh[2][2], Bn[2][2], Ah[2][2];
+    // chi = 0: X_mu = B_mu, Y_nu = B_nu^H ; chi = 1: X_mu = B_mu^H, Y_nu = B_nu
+    spin_block_dense(mu, chi == 1, A);
+    spin_block_dense(nu, chi == 0, Bh);
+    spin_block_dense(nu, chi == 1, Bn);
+    spin_block_dense(mu, chi == 0, Ah);
+    for (int r = 0; r < 2; ++r) for (int c = 0; c < 2; ++c) {
+        double2 s = make_double2(0, 0);
+        for (int k = 0; k < 2; ++k) s += A[r][k] * Bh[k][c] - Bn[r][k] * Ah[k][c];
+        S[r][c] = mul_ipow(0.5 * s, 1);
+    }
+}
+
+// One thread per site: the packed blocks A_chi = (m0 + 4) + C_chi with
+// C = c_sw (i/2) sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu},
+// F_{mu nu} = (Q_{mu nu} - Q_{mu nu}^H)/8 from the four plaquette leaves.
+__global__ void clover_build_kernel(const double2* __restrict__ U, Geom g, double m0, double csw,
+                                    double* __restrict__ A64, float* __restrict__ A32) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    int x[4];
+    site_coords(g, s, x);
+    double2 C[2][6][6];
+    for (int chi = 0; chi < 2; ++chi)
+        for (int i = 0; i < 6; ++i) for (int j = 0; j < 6; ++j) C[chi][i][j] = make_double2(0, 0);
+    if (csw != 0.0) {
+        for (int mu = 0; mu < 4; ++mu) {
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                auto L = [&](int site, int d) { return m3_load(U + ((size_t)site * 4 + d) * 9); };
+                M3<double> Umu = L(s, mu), Unu = L(s, nu);
+                M3<double> Umu_m = L(shifted(g, x, mu, -1, nu, 0), mu);
+                M3<double> Unu_m = L(shifted(g, x, mu, 0, nu, -1), nu);
+                M3<double> l1 = m3_mul(m3_mul(Umu, L(shifted(g, x, mu, 1, nu, 0), nu)),
+                                       m3_mul(m3_dag(L(shifted(g, x, mu, 0, nu, 1), mu)), m3_dag(Unu)));
+                M3<double> l2 = m3_mul(m3_mul(Unu, m3_dag(L(shifted(g, x, mu, -1, nu, 1), mu))),
+                                       m3_mul(m3_dag(L(shifted(g, x, mu, -1, nu, 0), nu)), Umu_m));
+                M3<double> l3 = m3_mul(m3_mul(m3_dag(Umu_m), m3_dag(L(shifted(g, x, mu, -1, nu, -1), nu))),
+                                       m3_mul(L(shifted(g, x, mu, -1, nu, -1), mu), Unu_m));
+                M3<double> l4 = m3_mul(m3_mul(m3_dag(Unu_m), L(shifted(g, x, mu, 0, nu, -1), mu)),
+                                       m3_mul(L(shifted(g, x, mu, 1, nu, -1), nu), m3_dag(Umu)));
+                double2 F[3][3];
+                for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+                    double2 q = l1.e[a][b] + l2.e[a][b] + l3.e[a][b] + l4.e[a][b];
+                    double2 qh = conj(l1.e[b][a] + l2.e[b][a] + l3.e[b][a] + l4.e[b][a]);
+                    F[a][b] = 0.125 * (q - qh);
+                }
+                for (int chi = 0; chi < 2; ++chi) {
+                    double2 S[2][2];
+                    sigma_block(mu, nu, chi, S);
+                    for (int si = 0; si < 2; ++si) for (int sj = 0; sj < 2; ++sj)
+                        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b)
+                            C[chi][si * 3 + a][sj * 3 + b] += S[si][sj] * F[a][b];
+                }
+            }
+        }
+    }
+    // scale by c_sw * i/2 and add the diagonal m0 + 4
+    for (int chi = 0; chi < 2; ++chi) {
+        double* out = A64 + (size_t)s * 72 + 36 * chi;
+        float* out32 = A32 + (size_t)s * 72 + 36 * chi;
+        for (int i = 0; i < 6; ++i) {
+            double2 d = mul_ipow(0.5 * csw * C[chi][i][i], 1);
+            out[i] = m0 + 4.0 + d.x;
+        }
+        for (int i = 0; i < 6; ++i) for (int j = i + 1; j < 6; ++j) {
+            double2 v = mul_ipow(0.5 * csw * C[chi][i][j], 1);
+            int o = herm_off(i, j);
+            out[o] = v.x;
+            out[o + 1] = v.y;
+        }
+        for (int k = 0; k < 36; ++k) out32[k] = (float)out[k];
+    }
+}
+
+// ------------------------------------------------------------------ stencil
+// out_j = op(tau_j) in_j, or out_j = b_j - op(tau_j) in_j when b != nullptr.
+// op = QCD_OP_D: D - tau Gamma5 ; op = QCD_OP_Q: Gamma5 D - tau.
+template <typename R>
+__global__ void __launch_bounds__(128) wilson_clover_kernel(
+    cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in, const cplx<R>* __restrict__ b,
+    const cplx<R>* __restrict__ U, const R* __restrict__ A, Geom g, int op, Shifts tau, size_t stride) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    const int j = blockIdx.y;
+    in += j * stride;
+    out += j * stride;
+    int x[4];
+    site_coords(g, s, x);
+    Spinor<R> psi, acc;
+    load_spinor<R>(in + (size_t)s * 12, psi);
+    clover_apply<R>(A + (size_t)s * 72, psi, acc);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        int neg;
+        Spinor<R> nb;
+        Link<R> u;
+        int sf = nb_fwd(g, x, s, mu, neg);
+        load_spinor<R>(in + (size_t)sf * 12, nb);
+        load_link<R>(U + ((size_t)s * 4 + mu) * 9, u);
+        R sg = neg ? R(-1) : R(1);
+        switch (mu) {
+            case 0: hop_accumulate<R, 0, true>(nb, u, sg, acc); break;
+            case 1: hop_accumulate<R, 1, true>(nb, u, sg, acc); break;
+            case 2: hop_accumulate<R, 2, true>(nb, u, sg, acc); break;
+            default: hop_accumulate<R, 3, true>(nb, u, sg, acc); break;
+        }
+        int sb = nb_bwd(g, x, s, mu, neg);
+        load_spinor<R>(in + (size_t)sb * 12, nb);
+        load_link<R>(U + ((size_t)sb * 4 + mu) * 9, u);
+        sg = neg ? R(-1) : R(1);
+        switch (mu) {
+            case 0: hop_accumulate<R, 0, false>(nb, u, sg, acc); break;
+            case 1: hop_accumulate<R, 1, false>(nb, u, sg, acc); break;
+            case 2: hop_accumulate<R, 2, false>(nb, u, sg, acc); break;
+            default: hop_accumulate<R, 3, false>(nb, u, sg, acc); break;
+        }
+    }
+    const R t = (R)tau.t[j];
+    if (op == QCD_OP_D) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc.c[k] -= t * psi.c[k];
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc.c[k] += t * psi.c[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc.c[k] -= t * psi.c[k];
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc.c[k] = -acc.c[k] - t * psi.c[k];
+    }
+    if (b != nullptr) {
+        Spinor<R> bb;
+        load_spinor<R>(b + j * stride + (size_t)s * 12, bb);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc.c[k] = bb.c[k] - acc.c[k];
+    }
+    store_spinor<R>(out + (size_t)s * 12, acc);
+}
+
+// ------------------------------------------------------------------ host launchers
+void launch_clover_build(const FineOp& f, cudaStream_t st) {
+    int th = 128;
+    clover_build_kernel<<<(f.g.V + th - 1) / th, th, 0, st>>>(f.U64, f.g, f.m0, f.csw, f.A64, f.A32);
+}
+
+template <typename R>
+void launch_dirac(const FineOp& f, int op, int nrhs, const void* in, void* out, const void* b,
+                  const double* tau, cudaStream_t st) {
+    Shifts sh{};
+    for (int j = 0; j < nrhs; ++j) sh.t[j] = tau ? tau[j] : 0.0;
+    dim3 grid((f.g.V + 127) / 128, nrhs);
+    const cplx<R>* U = std::is_same<R, double>::value ? (const cplx<R>*)f.U64 : (const cplx<R>*)f.U32;
+    const R* A = std::is_same<R, double>::value ? (const R*)f.A64 : (const R*)f.A32;
+    wilson_clover_kernel<R><<<grid, 128, 0, st>>>((cplx<R>*)out, (const cplx<R>*)in, (const cplx<R>*)b,
+                                                  U, A, f.g, op, sh, (size_t)f.g.V * 12);
+}
+
+void apply_op(const FineOp& f, int prec, int op, int nrhs, const void* in, void* out,
+              const double* tau, cudaStream_t st) {
+    if (prec == QCD_FP64) launch_dirac<double>(f, op, nrhs, in, out, nullptr, tau, st);
+    else launch_dirac<float>(f, op, nrhs, in, out, nullptr, tau, st);
+}
+
+void residual_op(const FineOp& f, int prec, int op, int nrhs, const void* b, const void* x, void* r,
+                 const double* tau, cudaStream_t st) {
+    if (prec == QCD_FP64) launch_dirac<double>(f, op, nrhs, x, r, b, tau, st);
+    else launch_dirac<float>(f, op, nrhs, x, r, b, tau, st);
+}
+
+}  // namespace qcd

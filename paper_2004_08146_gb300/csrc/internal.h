@@ -1,0 +1,123 @@
+// Internal declarations shared by the libqcd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <map>
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace qcd {
+
+// ------------------------------------------------------------------ fine operator
+struct FineOp {
+    Geom g{};
+    double2* U64 = nullptr;   // [V][4][3][3]
+    float2* U32 = nullptr;
+    double* A64 = nullptr;    // [V][2][36]: (m0 + 4) + clover, packed Hermitian 6x6
+    float* A32 = nullptr;
+    double m0 = 0, csw = 0;
+};
+
+// ------------------------------------------------------------------ blocking
+// A partition of the lattice into blocks of extent b[4]; blocks and local
+// sites are lexicographic (mu = 3 fastest), like the fine sites.
+struct Blocking {
+    int b[4] = {0, 0, 0, 0};   // block extents
+    int cd[4] = {0, 0, 0, 0};  // coarse (block-grid) extents
+    int bs = 0;                // sites per block
+    int nb = 0;                // number of blocks
+};
+
+__host__ __device__ __forceinline__ int block_fine_site(const Geom& g, const Blocking& B, int blk, int l) {
+    int c[4], o[4], x[4];
+    int t = blk;
+    c[3] = t % B.cd[3]; t /= B.cd[3];
+    c[2] = t % B.cd[2]; t /= B.cd[2];
+    c[1] = t % B.cd[1]; c[0] = t / B.cd[1];
+    t = l;
+    o[3] = t % B.b[3]; t /= B.b[3];
+    o[2] = t % B.b[2]; t /= B.b[2];
+    o[1] = t % B.b[1]; o[0] = t / B.b[1];
+    for (int mu = 0; mu < 4; ++mu) x[mu] = c[mu] * B.b[mu] + o[mu];
+    return site_index(g, x);
+}
+
+// ------------------------------------------------------------------ coarse level
+struct Coarse {
+    Blocking B;
+    Geom gc{};                // coarse lattice (antiperiodic unused)
+    int nv = 0, nc = 0;       // nc = 2 nv
+    double2* P64 = nullptr;   // [Vc][2][nv][bs][2][3]
+    float2* P32 = nullptr;
+    double2* A64 = nullptr;   // [Vc][9][col][row]  (column-major blocks)
+    float2* A32 = nullptr;
+    bool ready = false;
+};
+
+// ------------------------------------------------------------------ kernels (dirac.cu)
+void launch_clover_build(const FineOp& f, cudaStream_t st);
+void apply_op(const FineOp& f, int prec, int op, int nrhs, const void* in, void* out,
+              const double* tau, cudaStream_t st);
+void residual_op(const FineOp& f, int prec, int op, int nrhs, const void* b, const void* x, void* r,
+                 const double* tau, cudaStream_t st);
+
+// ------------------------------------------------------------------ kernels (blas.cu)
+// All vectors are complex (double2 / float2) of length n; "sets" are arrays of
+// nvec vectors for each of nrhs right-hand sides laid out [vec][rhs][n].
+void blas_zero(int prec, void* x, size_t n, cudaStream_t st);
+void blas_copy(int prec, const void* x, void* y, size_t n, cudaStream_t st);
+void blas_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, cudaStream_t st);
+// dots[i*nrhs + j] = <X[i][j], w[j]> for i < nvec (FP64 results, device)
+void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const void* w, int nrhs,
+                   size_t n, double2* dots, double2* partial, cudaStream_t st);
+// w[j] += sign * sum_i c[i*nrhs + j] X[i][j]
+void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const double2* c, double sign,
+                    void* w, int nrhs, size_t n, cudaStream_t st);
+// y[j] = alpha_j x[j] (+ y[j] when accumulate), alpha from device array of nrhs complex
+void blas_scale_dev(int prec, const void* x, void* y, const double2* alpha, int nrhs, size_t n,
+                    bool invert_real, bool accumulate, cudaStream_t st);
+void blas_gamma5(int prec, const void* x, void* y, size_t nsites_times_rhs, cudaStream_t st);
+void blas_gaussian(double2* x, size_t n, unsigned long long seed, unsigned long long offset, cudaStream_t st);
+// y = a*x + b*y (host scalars), complex
+void blas_axpby(int prec, double2 a, const void* x, double2 b, void* y, size_t n, cudaStream_t st);
+
+// ------------------------------------------------------------------ kernels (mg.cu)
+void mg_build_P(const FineOp& f, Coarse& c, const double2* vecs, int nvec, cudaStream_t st);
+void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st);
+void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st);
+void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* xc, void* x, bool accumulate,
+                cudaStream_t st);
+void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, void* y, const double* tau,
+                  cudaStream_t st);
+
+struct SapPlan {
+    Blocking B;
+    int* blocks_of_colour[2] = {nullptr, nullptr};  // device lists of block ids
+    int ncol[2] = {0, 0};
+};
+// x += block solves of op(tau) on the blocks of `colour`, rhs r (full fields)
+void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op, int nrhs,
+                const void* r, void* x, const double* tau, int iters, double tol,
+                void* scratch, cudaStream_t st);
+size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters);
+
+// ------------------------------------------------------------------ kernels (eig.cu)
+// Harmonic Ritz pairs of the pencil G s = theta H s (G = W^H W, H = W^H V):
+// returns mu = 1/theta and S (column-major m x m) in device buffers.
+void small_harmonic_eig(const double2* G, const double2* H, int m, int ld, double* mu, double2* S,
+                        double2* work, int* status, cudaStream_t st);
+// Orthonormal Q (m x k, column-major, leading dim m) of the columns of S
+// (m x k, leading dimension lds) by Householder QR.
+void small_qr(const double2* S, int m, int k, int lds, double2* Q, double2* work, cudaStream_t st);
+// Orthonormal complement (m x (m-1)) of a unit vector s of length m.
+void small_complement(const double2* s, int m, double2* C, double2* work, cudaStream_t st);
+// C (m x p) = A^H B for small column-major matrices: used for Gram updates
+void small_gram_transform(const double2* M, int m, int ldm, const double2* C, int p, double2* out,
+                          int ldo, double2* work, cudaStream_t st);
+
+}  // namespace qcd

@@ -1,0 +1,527 @@
+// Multigrid kernels: chirality-split aggregation P (Sec. 2, above Eq. 2.9),
+// restriction P^H and prolongation P (Eq. 2.8), the Galerkin coarse stencil
+// D_c = P^H D P (Eq. 2.8, 2.9) and the SAP block solves of Eq. 2.10.
+#include "internal.h"
+#include "dirac.cuh"
+
+namespace qcd {
+
+namespace {
+
+// sum of a double2 over the first blockDim.x (power of two) threads
+__device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
+    const int t = threadIdx.x;
+    red[t] = v;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+        if (t < s) red[t] += red[t + s];
+        __syncthreads();
+    }
+    double2 r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void block_coords(const Blocking& B, int blk, int c[4]) {
+    int t = blk;
+    c[3] = t % B.cd[3]; t /= B.cd[3];
+    c[2] = t % B.cd[2]; t /= B.cd[2];
+    c[1] = t % B.cd[1]; c[0] = t / B.cd[1];
+}
+__device__ __forceinline__ void local_coords(const Blocking& B, int l, int o[4]) {
+    int t = l;
+    o[3] = t % B.b[3]; t /= B.b[3];
+    o[2] = t % B.b[2]; t /= B.b[2];
+    o[1] = t % B.b[1]; o[0] = t / B.b[1];
+}
+__device__ __forceinline__ int coarse_index(const Blocking& B, const int c[4]) {
+    return ((c[0] * B.cd[1] + c[1]) * B.cd[2] + c[2]) * B.cd[3] + c[3];
+}
+__device__ __forceinline__ int local_index(const Blocking& B, const int o[4]) {
+    return ((o[0] * B.b[1] + o[1]) * B.b[2] + o[2]) * B.b[3] + o[3];
+}
+
+// ------------------------------------------------------------------ P build
+// One CTA per (coarse site, chirality): gather the nvec restricted test
+// vectors, then modified Gram-Schmidt applied twice (FP64).
+__global__ void build_P_kernel(Geom g, Blocking B, int nv, const double2* __restrict__ vecs, double2* __restrict__ P64,
+                               float2* __restrict__ P32) {
+    extern __shared__ double2 red[];
+    const int blk = blockIdx.x, chi = blockIdx.y;
+    const int nloc = B.bs * 6;
+    double2* Pb = P64 + ((size_t)blk * 2 + chi) * nv * nloc;
+    for (int i = 0; i < nv; ++i)
+        for (int d = threadIdx.x; d < nloc; d += blockDim.x) {
+            int l = d / 6, sc = d % 6;
+            int site = block_fine_site(g, B, blk, l);
+            Pb[(size_t)i * nloc + d] = vecs[(size_t)i * g.V * 12 + (size_t)site * 12 + 6 * chi + sc];
+        }
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i < nv; ++i) {
+            double2* pi = Pb + (size_t)i * nloc;
+            for (int j = 0; j < i; ++j) {
+                const double2* pj = Pb + (size_t)j * nloc;
+                double2 h = make_double2(0, 0);
+                for (int d = threadIdx.x; d < nloc; d += blockDim.x) h += cmulc(pj[d], pi[d]);
+                h = block_sum2(h, red);
+                for (int d = threadIdx.x; d < nloc; d += blockDim.x) pi[d] -= h * pj[d];
+                __syncthreads();
+            }
+            double2 nn = make_double2(0, 0);
+            for (int d = threadIdx.x; d < nloc; d += blockDim.x) nn.x += pi[d].x * pi[d].x + pi[d].y * pi[d].y;
+            nn = block_sum2(nn, red);
+            double inv = nn.x > 0 ? 1.0 / sqrt(nn.x) : 0.0;
+            for (int d = threadIdx.x; d < nloc; d += blockDim.x) pi[d] = inv * pi[d];
+            __syncthreads();
+        }
+    }
+    float2* Pb32 = P32 + ((size_t)blk * 2 + chi) * nv * nloc;
+    for (int d = threadIdx.x; d < nv * nloc; d += blockDim.x) Pb32[d] = cvt<float2>(Pb[d]);
+}
+
+// ------------------------------------------------------------------ restrict / prolong
+template <typename Z, typename R>
+__global__ void restrict_kernel(Geom g, Blocking B, int nv, const Z* __restrict__ P, const Z* __restrict__ r,
+                                Z* __restrict__ xc, int nrhs) {
+    const int nc = 2 * nv;
+    const int nloc = B.bs * 6;
+    const long total = (long)B.nb * nc * nrhs;
+    const int lane = threadIdx.x & 31;
+    for (long w = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; w < total; w += ((long)gridDim.x * blockDim.x) >> 5) {
+        const int j = (int)(w / ((long)B.nb * nc));
+        const int rem = (int)(w - (long)j * B.nb * nc);
+        const int blk = rem / nc, ci = rem % nc;
+        const int chi = ci / nv, i = ci % nv;
+        const Z* p = P + (((size_t)blk * 2 + chi) * nv + i) * nloc;
+        const Z* rr = r + (size_t)j * g.V * 12;
+        R re = 0, im = 0;
+        for (int d = lane; d < nloc; d += 32) {
+            int l = d / 6, sc = d % 6;
+            int site = block_fine_site(g, B, blk, l);
+            Z a = p[d], b = rr[(size_t)site * 12 + 6 * chi + sc];
+            re += a.x * b.x + a.y * b.y;
+            im += a.x * b.y - a.y * b.x;
+        }
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) { Z o; o.x = re; o.y = im; xc[(size_t)j * B.nb * nc + (size_t)blk * nc + ci] = o; }
+    }
+}
+
+template <typename Z>
+__global__ void prolong_kernel(Geom g, Blocking B, int nv, const Z* __restrict__ P, const Z* __restrict__ xc,
+                               Z* __restrict__ x, int nrhs, bool accumulate) {
+    const int nc = 2 * nv;
+    const int nloc = B.bs * 6;
+    const size_t total = (size_t)nrhs * B.nb * 2 * nloc;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / ((size_t)B.nb * 2 * nloc));
+        size_t rem = t - (size_t)j * B.nb * 2 * nloc;
+        const int blk = (int)(rem / (2 * nloc));
+        const int chi = (int)((rem / nloc) % 2);
+        const int d = (int)(rem % nloc);
+        const Z* p = P + ((size_t)blk * 2 + chi) * nv * nloc + d;
+        const Z* c = xc + (size_t)j * B.nb * nc + (size_t)blk * nc + chi * nv;
+        Z acc; acc.x = 0; acc.y = 0;
+        for (int i = 0; i < nv; ++i) acc += p[(size_t)i * nloc] * c[i];
+        int l = d / 6, sc = d % 6;
+        size_t idx = (size_t)j * g.V * 12 + (size_t)block_fine_site(g, B, blk, l) * 12 + 6 * chi + sc;
+        if (accumulate) acc += x[idx];
+        x[idx] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ coarse build
+// CTA (coarse site blk, direction d): column by column, h(l) = the part of
+// (D P e_col)(y_l) that D couples from block blk + d (d = 0: site-diagonal and
+// in-block hops), then A[blk][d][col][row] = P_blk[row]^H h.
+__device__ __forceinline__ void P_spinor(const double2* __restrict__ P, int nv, int nloc, int blk, int chi, int i, int l,
+                                         Spinor<double>& s) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s.c[k] = make_double2(0, 0);
+    const double2* p = P + (((size_t)blk * 2 + chi) * nv + i) * nloc + (size_t)l * 6;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s.c[6 * chi + k] = p[k];
+}
+
+template <bool fwd>
+__device__ __forceinline__ void hop_dispatch(int mu, const Spinor<double>& psi, const Link<double>& u, double sg,
+                                             Spinor<double>& acc) {
+    switch (mu) {
+        case 0: hop_accumulate<double, 0, fwd>(psi, u, sg, acc); break;
+        case 1: hop_accumulate<double, 1, fwd>(psi, u, sg, acc); break;
+        case 2: hop_accumulate<double, 2, fwd>(psi, u, sg, acc); break;
+        default: hop_accumulate<double, 3, fwd>(psi, u, sg, acc); break;
+    }
+}
+
+__global__ void build_coarse_kernel(Geom g, Blocking B, int nv, const double2* __restrict__ U, const double* __restrict__ A,
+                                    const double2* __restrict__ P, double2* __restrict__ Ac) {
+    extern __shared__ double2 hsm[];   // [bs][12]
+    const int blk = blockIdx.x, d = blockIdx.y;
+    const int nc = 2 * nv, nloc = B.bs * 6;
+    int cb[4];
+    block_coords(B, blk, cb);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int col = 0; col < nc; ++col) {
+        const int chic = col / nv, ic = col % nv;
+        for (int l = threadIdx.x; l < B.bs; l += blockDim.x) {
+            int o[4], x[4];
+            local_coords(B, l, o);
+            for (int mu = 0; mu < 4; ++mu) x[mu] = cb[mu] * B.b[mu] + o[mu];
+            const int y = site_index(g, x);
+            Spinor<double> acc;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc.c[k] = make_double2(0, 0);
+            if (d == 0) {
+                Spinor<double> ps;
+                P_spinor(P, nv, nloc, blk, chic, ic, l, ps);
+                clover_apply<double>(A + (size_t)y * 72, ps, acc);
+            }
+            for (int mu = 0; mu < 4; ++mu) {
+                for (int dir = 0; dir < 2; ++dir) {
+                    const bool fw = dir == 0;
+                    const bool face = (fw ? (o[mu] == B.b[mu] - 1) : (o[mu] == 0)) && B.cd[mu] > 1;
+                    const int want = face ? (fw ? 1 + mu : 5 + mu) : 0;
+                    if (want != d) continue;
+                    int neg;
+                    int yn = fw ? nb_fwd(g, x, y, mu, neg) : nb_bwd(g, x, y, mu, neg);
+                    int xn[4];
+                    site_coords(g, yn, xn);
+                    int cn[4], on[4];
+                    for (int k = 0; k < 4; ++k) { cn[k] = xn[k] / B.b[k]; on[k] = xn[k] % B.b[k]; }
+                    Spinor<double> ps;
+                    P_spinor(P, nv, nloc, coarse_index(B, cn), chic, ic, local_index(B, on), ps);
+                    Link<double> u;
+                    load_link<double>(U + ((size_t)(fw ? y : yn) * 4 + mu) * 9, u);
+                    if (fw) hop_dispatch<true>(mu, ps, u, neg ? -1.0 : 1.0, acc);
+                    else hop_dispatch<false>(mu, ps, u, neg ? -1.0 : 1.0, acc);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 12; ++k) hsm[l * 12 + k] = acc.c[k];
+        }
+        __syncthreads();
+        for (int row = warp; row < nc; row += nwarps) {
+            const int chir = row / nv, ir = row % nv;
+            const double2* pr = P + (((size_t)blk * 2 + chir) * nv + ir) * nloc;
+            double re = 0, im = 0;
+            for (int e = lane; e < nloc; e += 32) {
+                int l = e / 6, sc = e % 6;
+                double2 a = pr[e], h = hsm[l * 12 + 6 * chir + sc];
+                re += a.x * h.x + a.y * h.y;
+                im += a.x * h.y - a.y * h.x;
+            }
+            re = warp_sum(re);
+            im = warp_sum(im);
+            if (lane == 0) Ac[(((size_t)blk * 9 + d) * nc + col) * nc + row] = make_double2(re, im);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void narrow_kernel(const double2* __restrict__ a, float2* __restrict__ b, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        b[t] = cvt<float2>(a[t]);
+}
+
+// ------------------------------------------------------------------ coarse apply
+template <typename Z, typename R>
+__global__ void coarse_apply_kernel(Geom gc, int nc, const Z* __restrict__ A, const Z* __restrict__ x, Z* __restrict__ y,
+                                    int op, Shifts tau, int nrhs) {
+    const long total = (long)nrhs * gc.V * nc;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(t / ((long)gc.V * nc));
+        const int rem = (int)(t - (long)j * gc.V * nc);
+        const int s = rem / nc, r = rem % nc;
+        int c[4];
+        site_coords(gc, s, c);
+        const Z* xj = x + (size_t)j * gc.V * nc;
+        Z acc; acc.x = 0; acc.y = 0;
+        for (int d = 0; d < 9; ++d) {
+            int sn = s;
+            if (d > 0) {
+                int mu = (d - 1) & 3, step = d <= 4 ? 1 : -1;
+                int cn[4] = {c[0], c[1], c[2], c[3]};
+                cn[mu] = (cn[mu] + step + gc.L[mu]) % gc.L[mu];
+                sn = site_index(gc, cn);
+            }
+            const Z* a = A + (((size_t)s * 9 + d) * nc) * nc + r;
+            const Z* xs = xj + (size_t)sn * nc;
+            for (int col = 0; col < nc; ++col) acc += a[(size_t)col * nc] * xs[col];
+        }
+        const R sg = r < nc / 2 ? R(1) : R(-1);
+        const R tj = (R)tau.t[j];
+        Z xv = xj[(size_t)s * nc + r];
+        if (op == QCD_OP_D) { acc -= (tj * sg) * xv; }
+        else { acc = sg * acc; acc -= tj * xv; }
+        y[(size_t)j * gc.V * nc + (size_t)s * nc + r] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ SAP block solves
+// One CTA per (block of one colour, rhs), one thread per block site; GMRES
+// from zero on the Dirichlet block operator (hops leaving the block dropped),
+// Arnoldi by modified Gram-Schmidt, Krylov vectors in global scratch.
+template <typename R>
+__device__ __forceinline__ void block_op(const Geom& g, const Blocking& B, const cplx<R>* __restrict__ U,
+                                         const R* __restrict__ A, int y, int l, const int o[4],
+                                         const cplx<R>* vsm, int op, R t, Spinor<R>& acc) {
+    Spinor<R> psi;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) psi.c[k] = vsm[l * 12 + k];
+    clover_apply<R>(A + (size_t)y * 72, psi, acc);
+    int lstride = 1;
+#pragma unroll
+    for (int mu = 3; mu >= 0; --mu) {
+        Link<R> u;
+        Spinor<R> nb;
+        if (o[mu] < B.b[mu] - 1) {
+            const int ln = l + lstride;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) nb.c[k] = vsm[ln * 12 + k];
+            load_link<R>(U + ((size_t)y * 4 + mu) * 9, u);
+            switch (mu) {
+                case 0: hop_accumulate<R, 0, true>(nb, u, R(1), acc); break;
+                case 1: hop_accumulate<R, 1, true>(nb, u, R(1), acc); break;
+                case 2: hop_accumulate<R, 2, true>(nb, u, R(1), acc); break;
+                default: hop_accumulate<R, 3, true>(nb, u, R(1), acc); break;
+            }
+        }
+        if (o[mu] > 0) {
+            const int ln = l - lstride;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) nb.c[k] = vsm[ln * 12 + k];
+            int xb[4];
+            site_coords(g, y, xb);
+            xb[mu] -= 1;
+            load_link<R>(U + ((size_t)site_index(g, xb) * 4 + mu) * 9, u);
+            switch (mu) {
+                case 0: hop_accumulate<R, 0, false>(nb, u, R(1), acc); break;
+                case 1: hop_accumulate<R, 1, false>(nb, u, R(1), acc); break;
+                case 2: hop_accumulate<R, 2, false>(nb, u, R(1), acc); break;
+                default: hop_accumulate<R, 3, false>(nb, u, R(1), acc); break;
+            }
+        }
+        lstride *= B.b[mu];
+    }
+    if (op == QCD_OP_D) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc.c[k] -= t * psi.c[k];
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc.c[k] += t * psi.c[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc.c[k] -= t * psi.c[k];
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc.c[k] = -acc.c[k] - t * psi.c[k];
+    }
+}
+
+template <typename R>
+__global__ void sap_block_kernel(Geom g, Blocking B, const cplx<R>* __restrict__ U, const R* __restrict__ A,
+                                 const int* __restrict__ blocks, int op, Shifts tau, const cplx<R>* __restrict__ r,
+                                 cplx<R>* __restrict__ x, int iters, double tol, cplx<R>* __restrict__ scratch) {
+    extern __shared__ double2 sm[];
+    const int bs = B.bs;
+    cplx<R>* vsm = reinterpret_cast<cplx<R>*>(sm);                       // [bs][12]
+    double2* red = reinterpret_cast<double2*>(vsm + (size_t)bs * 12);    // [bs]
+    double2* H = red + bs;                              // [(iters+1) * iters]
+    double2* gv = H + (iters + 1) * iters;              // [iters + 1]
+    double2* sn = gv + iters + 1;                       // [iters]
+    double2* yv = sn + iters;                           // [iters]
+    double* cs = reinterpret_cast<double*>(yv + iters); // [iters]
+    int* flag = reinterpret_cast<int*>(cs + iters);     // [4]
+
+    const int j = blockIdx.y;
+    const int blk = blocks[blockIdx.x];
+    const int l = threadIdx.x;
+    const size_t fstride = (size_t)g.V * 12;
+    r += j * fstride;
+    x += j * fstride;
+    cplx<R>* kv = scratch + ((size_t)j * gridDim.x + blockIdx.x) * (size_t)(iters + 1) * bs * 12;
+    const R t = (R)tau.t[j];
+
+    int o[4];
+    local_coords(B, l, o);
+    const int y = block_fine_site(g, B, blk, l);
+
+    Spinor<R> w;
+    load_spinor<R>(r + (size_t)y * 12, w);
+    double2 nn = make_double2(0, 0);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) nn.x += (double)w.c[k].x * w.c[k].x + (double)w.c[k].y * w.c[k].y;
+    nn = block_sum2(nn, red);
+    const double beta = sqrt(nn.x);
+    if (!(beta > 0.0)) return;
+    {
+        const R ib = (R)(1.0 / beta);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) { w.c[k] = ib * w.c[k]; kv[(size_t)l * 12 + k] = w.c[k]; vsm[l * 12 + k] = w.c[k]; }
+    }
+    if (l == 0) { gv[0] = make_double2(beta, 0); flag[0] = 0; }
+    int kdim = 0;
+    for (int jj = 0; jj < iters; ++jj) {
+        __syncthreads();
+        block_op<R>(g, B, U, A, y, l, o, vsm, op, t, w);
+        for (int i = 0; i <= jj; ++i) {
+            const cplx<R>* vi = kv + (size_t)i * bs * 12 + (size_t)l * 12;
+            double2 h = make_double2(0, 0);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                cplx<R> a = vi[k];
+                h.x += (double)a.x * w.c[k].x + (double)a.y * w.c[k].y;
+                h.y += (double)a.x * w.c[k].y - (double)a.y * w.c[k].x;
+            }
+            h = block_sum2(h, red);
+            const cplx<R> hr = mk<R>((R)h.x, (R)h.y);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) w.c[k] -= hr * vi[k];
+            if (l == 0) H[i * iters + jj] = h;
+        }
+        double2 hn2 = make_double2(0, 0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) hn2.x += (double)w.c[k].x * w.c[k].x + (double)w.c[k].y * w.c[k].y;
+        hn2 = block_sum2(hn2, red);
+        const double hn = sqrt(hn2.x);
+        {
+            const R ih = hn > 0 ? (R)(1.0 / hn) : R(0);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                w.c[k] = ih * w.c[k];
+                kv[(size_t)(jj + 1) * bs * 12 + (size_t)l * 12 + k] = w.c[k];
+                vsm[l * 12 + k] = w.c[k];
+            }
+        }
+        if (l == 0) {
+            H[(jj + 1) * iters + jj] = make_double2(hn, 0);
+            for (int i = 0; i < jj; ++i) {
+                double2 a = H[i * iters + jj], c = H[(i + 1) * iters + jj];
+                H[i * iters + jj] = cs[i] * a + sn[i] * c;
+                H[(i + 1) * iters + jj] = cs[i] * c - conj(sn[i]) * a;
+            }
+            double2 a = H[jj * iters + jj];
+            double2 c = H[(jj + 1) * iters + jj];
+            double aa = sqrt(a.x * a.x + a.y * a.y), rr = sqrt(aa * aa + c.x * c.x + c.y * c.y);
+            if (aa > 0) {
+                cs[jj] = aa / rr;
+                sn[jj] = (1.0 / aa) * a * conj(c);
+                sn[jj] = (1.0 / rr) * sn[jj];
+            } else {
+                cs[jj] = 0.0;
+                sn[jj] = make_double2(1, 0);
+            }
+            H[jj * iters + jj] = cs[jj] * a + sn[jj] * c;
+            gv[jj + 1] = -1.0 * (conj(sn[jj]) * gv[jj]);
+            gv[jj] = cs[jj] * gv[jj];
+            const double res = sqrt(gv[jj + 1].x * gv[jj + 1].x + gv[jj + 1].y * gv[jj + 1].y);
+            flag[0] = (tol >= 0.0 && res <= tol * beta) ? 1 : 0;
+        }
+        __syncthreads();
+        kdim = jj + 1;
+        if (flag[0]) break;
+    }
+    if (l == 0) {
+        for (int i = kdim - 1; i >= 0; --i) {
+            double2 s = gv[i];
+            for (int k = i + 1; k < kdim; ++k) s -= H[i * iters + k] * yv[k];
+            double2 dd = H[i * iters + i];
+            double den = dd.x * dd.x + dd.y * dd.y;
+            yv[i] = den > 0 ? (1.0 / den) * cmulc(dd, s) : make_double2(0, 0);
+        }
+    }
+    __syncthreads();
+    Spinor<R> e;
+    load_spinor<R>(x + (size_t)y * 12, e);
+    for (int i = 0; i < kdim; ++i) {
+        const cplx<R> yi = mk<R>((R)yv[i].x, (R)yv[i].y);
+        const cplx<R>* vi = kv + (size_t)i * bs * 12 + (size_t)l * 12;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) e.c[k] += yi * vi[k];
+    }
+    store_spinor<R>(x + (size_t)y * 12, e);
+}
+
+inline int grid_for(size_t n, int th = 256) {
+    size_t gsz = (n + th - 1) / th;
+    return (int)(gsz > 1048576 ? 1048576 : (gsz == 0 ? 1 : gsz));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host launchers
+void mg_build_P(const FineOp& f, Coarse& c, const double2* vecs, int nvec, cudaStream_t st) {
+    dim3 grid(c.B.nb, 2);
+    build_P_kernel<<<grid, 256, 256 * sizeof(double2), st>>>(f.g, c.B, nvec, vecs, c.P64, c.P32);
+}
+
+void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st) {
+    dim3 grid(c.B.nb, 9);
+    size_t sm = (size_t)c.B.bs * 12 * sizeof(double2);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(build_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    build_coarse_kernel<<<grid, 256, sm, st>>>(f.g, c.B, c.nv, f.U64, f.A64, c.P64, c.A64);
+    size_t n = (size_t)c.B.nb * 9 * c.nc * c.nc;
+    narrow_kernel<<<grid_for(n), 256, 0, st>>>(c.A64, c.A32, n);
+}
+
+void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st) {
+    size_t warps = (size_t)c.B.nb * c.nc * nrhs;
+    int grid = grid_for(warps * 32);
+    if (prec == QCD_FP64)
+        restrict_kernel<double2, double><<<grid, 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)r, (double2*)xc, nrhs);
+    else
+        restrict_kernel<float2, float><<<grid, 256, 0, st>>>(f.g, c.B, c.nv, c.P32, (const float2*)r, (float2*)xc, nrhs);
+}
+
+void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* xc, void* x, bool accumulate,
+                cudaStream_t st) {
+    size_t n = (size_t)nrhs * c.B.nb * 2 * c.B.bs * 6;
+    if (prec == QCD_FP64)
+        prolong_kernel<double2><<<grid_for(n), 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)xc, (double2*)x, nrhs,
+                                                             accumulate);
+    else
+        prolong_kernel<float2><<<grid_for(n), 256, 0, st>>>(f.g, c.B, c.nv, c.P32, (const float2*)xc, (float2*)x, nrhs,
+                                                            accumulate);
+}
+
+void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, void* y, const double* tau,
+                  cudaStream_t st) {
+    Shifts sh{};
+    for (int j = 0; j < nrhs; ++j) sh.t[j] = tau ? tau[j] : 0.0;
+    size_t n = (size_t)nrhs * c.gc.V * c.nc;
+    if (prec == QCD_FP64)
+        coarse_apply_kernel<double2, double><<<grid_for(n), 256, 0, st>>>(c.gc, c.nc, c.A64, (const double2*)x,
+                                                                         (double2*)y, op, sh, nrhs);
+    else
+        coarse_apply_kernel<float2, float><<<grid_for(n), 256, 0, st>>>(c.gc, c.nc, c.A32, (const float2*)x, (float2*)y,
+                                                                       op, sh, nrhs);
+}
+
+size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters) {
+    size_t per = (size_t)(iters + 1) * sp.B.bs * 12 * (prec == QCD_FP64 ? sizeof(double2) : sizeof(float2));
+    int nmax = sp.ncol[0] > sp.ncol[1] ? sp.ncol[0] : sp.ncol[1];
+    return per * nmax * nrhs;
+}
+
+void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op, int nrhs, const void* r, void* x,
+                const double* tau, int iters, double tol, void* scratch, cudaStream_t st) {
+    Shifts sh{};
+    for (int j = 0; j < nrhs; ++j) sh.t[j] = tau ? tau[j] : 0.0;
+    dim3 grid(sp.ncol[colour], nrhs);
+    const int bs = sp.B.bs;
+    size_t sm = sizeof(double2) * ((size_t)bs + (size_t)(iters + 1) * iters + (iters + 1) + 2 * iters) +
+                sizeof(double) * iters + 4 * sizeof(int) +
+                (size_t)bs * 12 * (prec == QCD_FP64 ? sizeof(double2) : sizeof(float2));
+    if (prec == QCD_FP64) {
+        if (sm > 48 * 1024) cudaFuncSetAttribute(sap_block_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        sap_block_kernel<double><<<grid, bs, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour], op, sh,
+                                                       (const double2*)r, (double2*)x, iters, tol, (double2*)scratch);
+    } else {
+        if (sm > 48 * 1024) cudaFuncSetAttribute(sap_block_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        sap_block_kernel<float><<<grid, bs, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour], op, sh,
+                                                      (const float2*)r, (float2*)x, iters, tol, (float2*)scratch);
+    }
+}
+
+}  // namespace qcd
