@@ -76,6 +76,8 @@ typedef struct qcd_params {
     int    m_max;            /* Table 2: 50 */
     int    block;            /* targets per outer iteration (>= 1; default 2) */
     int    n_init;           /* random start vectors when use_mg = 0 (default 8) */
+    int    shift_rho;        /* 1: correction-equation shift = Rayleigh quotient rho of the
+                                target vector (default); 0: its harmonic Ritz value theta */
     int    update_every;     /* interpolation rebuild every k locks (default 1) */
     int    max_outer;        /* outer iteration cap (default 100000) */
     unsigned long long seed; /* counter-based RNG seed for setup / start vectors */
@@ -203,6 +205,28 @@ int qcd_sap(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x,
 /* One two-level cycle x = M b (Eq. 2.8 with post-smoothing only) on op(tau). */
 int qcd_mg_cycle(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x,
                  const double* tau);
+
+/* ---------------------------------------------------------------------
+ * Launch accounting (process-wide, not part of the method): every libqcd
+ * kernel launch is counted with its algorithmic bytes and flops; with
+ * mode 1 every launch, with mode 2 only launches of the kernel named
+ * `filter`, is bracketed by CUDA events on its stream.  qcd_stats_read waits
+ * for the recorded events and returns up to `max` per-kernel records (*n =
+ * number of kernels seen).  EINVAL on a bad mode or NULL n.
+ * ------------------------------------------------------------------- */
+typedef struct qcd_kernel_stat {
+    char      name[40];
+    long long launches;      /* launches since the last reset */
+    long long timed;         /* launches timed with events */
+    double    total_ms;      /* summed event time of the timed launches */
+    double    bytes;         /* algorithmic bytes, all launches */
+    double    flops;         /* algorithmic flops, all launches */
+    double    timed_bytes;   /* algorithmic bytes of the timed launches */
+    double    timed_flops;   /* algorithmic flops of the timed launches */
+} qcd_kernel_stat;
+
+int qcd_stats_reset(int mode, const char* filter);
+int qcd_stats_read(qcd_kernel_stat* out, int max, int* n);
 
 #ifdef __cplusplus
 }

@@ -555,6 +555,7 @@ void basis_transform(const double2* In, int m, const double2* C, int p, double2*
     dim3 grid(gx, (p + 7) / 8);
     const size_t sm = (size_t)m * p * sizeof(double2);
     if (sm > 48 * 1024) CK(cudaFuncSetAttribute(basis_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    KTimer kt("basis_transform", (double)(m + p) * n * 16, 8.0 * m * p * n, st);
     basis_transform_kernel<<<grid, 256, sm, st>>>(In, m, C, p, Out, n);
 }
 // G[i][m] = d1[i], G[m][i] = conj d1[i]; Hm[i][m] = d2[i]; Hm[m][i] = conj d3[i]  (ld = column stride)
@@ -638,6 +639,7 @@ struct GD {
         blas_multidot(QCD_FP64, W, m + 1, n, W + (size_t)m * n, 1, n, dots, part, st);
         blas_multidot(QCD_FP64, W, m + 1, n, V + (size_t)m * n, 1, n, dots + mcap, part, st);
         blas_multidot(QCD_FP64, V, m + 1, n, W + (size_t)m * n, 1, n, dots + 2 * mcap, part, st);
+        KTimer kt("gram_update", 0.0, 0.0, st);
         gram_update_kernel<<<1, 64, 0, st>>>(G, Hm, mcap, m, dots, dots + mcap, dots + 2 * mcap);
         check_launch("add_vector");
         ++m;
@@ -782,7 +784,10 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                     ++gd.nlock;
                     // deflate: V <- V C with C the complement of s/||s||
                     CK(cudaMemcpyAsync(gd.work, s, gd.m * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-                    normalize_vec_kernel<<<1, 64, 0, st>>>(gd.work, gd.m);
+                    {
+                        KTimer kt("normalize_vec", 0.0, 0.0, st);
+                        normalize_vec_kernel<<<1, 64, 0, st>>>(gd.work, gd.m);
+                    }
                     small_complement(gd.work, gd.m, gd.C, nullptr, st);
                     gd.transform(gd.C, gd.m - 1);
                     ++locks_since_update;
@@ -792,7 +797,10 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                                 outer, gd.m);
                     break;
                 }
-                tsel.push_back(theta[ti]);
+                if (P.verbose > 1)
+                    fprintf(stderr, "[qcd_eigs] outer=%d m=%d theta=% .6e rho=% .10e res=%.3e\n", outer, gd.m,
+                            theta[ti], rho, rn);
+                tsel.push_back(P.shift_rho ? rho : theta[ti]);
                 ++nr;
             }
             if (!locked) break;
@@ -840,6 +848,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
             gd.harmonic(th, cl);
             int keep = std::min(P.m_min, gd.m);
             CK(cudaMemcpyAsync(gd.idx, cl.data(), keep * sizeof(int), cudaMemcpyHostToDevice, st));
+            KTimer kt("gather_columns", 0.0, 0.0, st);
             gather_columns_kernel<<<1, 256, 0, st>>>(gd.S, gd.m, gd.idx, keep, gd.work);
             small_qr(gd.work, gd.m, keep, gd.m, gd.C, nullptr, st);
             gd.transform(gd.C, keep);
@@ -922,6 +931,7 @@ void qcd_default_params(qcd_params* p) {
     p->m_max = 50;
     p->block = 2;
     p->n_init = 8;
+    p->shift_rho = 1;
     p->update_every = 1;
     p->max_outer = 100000;
     p->seed = 20200417ull;

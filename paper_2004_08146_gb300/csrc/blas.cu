@@ -9,6 +9,8 @@ namespace qcd {
 namespace {
 constexpr int kThreads = 256;
 
+inline size_t esz_of(int prec) { return prec == QCD_FP64 ? sizeof(double2) : sizeof(float2); }
+
 inline int grid_for(size_t n, int th = kThreads) {
     size_t g = (n + th - 1) / th;
     return (int)(g > 1048576 ? 1048576 : (g == 0 ? 1 : g));
@@ -146,6 +148,7 @@ __global__ void gaussian_kernel(double2* x, size_t n, unsigned long long seed, u
 }  // namespace
 
 void blas_zero(int prec, void* x, size_t n, cudaStream_t st) {
+    KTimer kt("blas_zero", (double)n * esz_of(prec), 0.0, st);
     if (prec == QCD_FP64) zero_kernel<double2><<<grid_for(n), kThreads, 0, st>>>((double2*)x, n);
     else zero_kernel<float2><<<grid_for(n), kThreads, 0, st>>>((float2*)x, n);
 }
@@ -154,6 +157,7 @@ void blas_copy(int prec, const void* x, void* y, size_t n, cudaStream_t st) {
 }
 void blas_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, cudaStream_t st) {
     if (prec_in == prec_out) { blas_copy(prec_in, x, y, n, st); return; }
+    KTimer kt("blas_convert", (double)n * (esz_of(prec_in) + esz_of(prec_out)), 0.0, st);
     if (prec_in == QCD_FP64)
         convert_kernel<double2, float2><<<grid_for(n), kThreads, 0, st>>>((const double2*)x, (float2*)y, n);
     else
@@ -166,6 +170,8 @@ void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const 
     if (nsplit > 64) nsplit = 64;
     if (nsplit < 1) nsplit = 1;
     dim3 grid(nsplit, nvec * nrhs);
+    KTimer kt(prec == QCD_FP64 ? "multidot_f64" : "multidot_f32", (double)(nvec + 1) * nrhs * n * esz_of(prec),
+              8.0 * nvec * nrhs * n, st);
     if (prec == QCD_FP64)
         multidot_partial_kernel<double2><<<grid, kThreads, 0, st>>>((const double2*)X, xstride_vec, (const double2*)w,
                                                                    nrhs, n, nsplit, partial);
@@ -173,12 +179,15 @@ void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const 
         multidot_partial_kernel<float2><<<grid, kThreads, 0, st>>>((const float2*)X, xstride_vec, (const float2*)w,
                                                                   nrhs, n, nsplit, partial);
     int nv = nvec * nrhs;
+    KTimer kt2("multidot_final", 0.0, 0.0, st);
     multidot_final_kernel<<<(nv + 127) / 128, 128, 0, st>>>(partial, nsplit, nv, dots);
 }
 void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const double2* c, double sign, void* w,
                     int nrhs, size_t n, cudaStream_t st) {
     if (nvec <= 0) return;
     size_t total = n * nrhs;
+    KTimer kt(prec == QCD_FP64 ? "multiaxpy_f64" : "multiaxpy_f32", (double)(nvec + 2) * nrhs * n * esz_of(prec),
+              8.0 * nvec * nrhs * n, st);
     if (prec == QCD_FP64)
         multiaxpy_kernel<double2, double><<<grid_for(total), kThreads, 0, st>>>((const double2*)X, nvec, xstride_vec, c,
                                                                               sign, (double2*)w, nrhs, n);
@@ -189,6 +198,7 @@ void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const
 void blas_scale_dev(int prec, const void* x, void* y, const double2* alpha, int nrhs, size_t n, bool invert_real,
                     bool accumulate, cudaStream_t st) {
     size_t total = n * nrhs;
+    KTimer kt("blas_scale", (double)total * (accumulate ? 3 : 2) * esz_of(prec), 0.0, st);
     if (prec == QCD_FP64)
         scale_dev_kernel<double2, double><<<grid_for(total), kThreads, 0, st>>>((const double2*)x, (double2*)y, alpha,
                                                                               nrhs, n, invert_real, accumulate);
@@ -198,13 +208,16 @@ void blas_scale_dev(int prec, const void* x, void* y, const double2* alpha, int 
 }
 void blas_gamma5(int prec, const void* x, void* y, size_t nsites, cudaStream_t st) {
     size_t total = nsites * 12;
+    KTimer kt("blas_gamma5", (double)total * 2 * esz_of(prec), 0.0, st);
     if (prec == QCD_FP64) gamma5_kernel<double2><<<grid_for(total), kThreads, 0, st>>>((const double2*)x, (double2*)y, nsites);
     else gamma5_kernel<float2><<<grid_for(total), kThreads, 0, st>>>((const float2*)x, (float2*)y, nsites);
 }
 void blas_gaussian(double2* x, size_t n, unsigned long long seed, unsigned long long offset, cudaStream_t st) {
+    KTimer kt("gaussian", (double)n * 16, 0.0, st);
     gaussian_kernel<<<grid_for(n), kThreads, 0, st>>>(x, n, seed, offset);
 }
 void blas_axpby(int prec, double2 a, const void* x, double2 b, void* y, size_t n, cudaStream_t st) {
+    KTimer kt("blas_axpby", (double)n * 3 * esz_of(prec), 0.0, st);
     if (prec == QCD_FP64)
         axpby_kernel<double2, double><<<grid_for(n), kThreads, 0, st>>>(a, (const double2*)x, b, (double2*)y, n);
     else

@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(128) wilson_clover_kernel(
 // ------------------------------------------------------------------ host launchers
 void launch_clover_build(const FineOp& f, cudaStream_t st) {
     int th = 128;
+    KTimer kt("clover_build", 0.0, 0.0, st);
     clover_build_kernel<<<(f.g.V + th - 1) / th, th, 0, st>>>(f.U64, f.g, f.m0, f.csw, f.A64, f.A32);
 }
 
@@ -195,6 +196,9 @@ void launch_dirac(const FineOp& f, int op, int nrhs, const void* in, void* out, 
     dim3 grid((f.g.V + 127) / 128, nrhs);
     const cplx<R>* U = std::is_same<R, double>::value ? (const cplx<R>*)f.U64 : (const cplx<R>*)f.U32;
     const R* A = std::is_same<R, double>::value ? (const R*)f.A64 : (const R*)f.A32;
+    const double bytes = (double)f.g.V * (nrhs * (b ? 72.0 : 48.0) + 144.0) * sizeof(R);
+    KTimer kt(std::is_same<R, double>::value ? "wilson_clover_f64" : "wilson_clover_f32", bytes,
+              1824.0 * f.g.V * nrhs, st);
     wilson_clover_kernel<R><<<grid, 128, 0, st>>>((cplx<R>*)out, (const cplx<R>*)in, (const cplx<R>*)b,
                                                   U, A, f.g, op, sh, (size_t)f.g.V * 12);
 }

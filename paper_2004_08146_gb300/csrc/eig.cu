@@ -253,18 +253,22 @@ __global__ void __launch_bounds__(kT) gram_transform_kernel(const double2* __res
 
 void small_harmonic_eig(const double2* G, const double2* H, int m, int ld, double* mu, double2* S, double2* work,
                         int* status, cudaStream_t st) {
+    KTimer kt("harmonic_eig", 0.0, 0.0, st);
     harmonic_eig_kernel<<<1, kT, 0, st>>>(G, H, m, ld, mu, S, work, status);
 }
 void small_qr(const double2* S, int m, int k, int lds, double2* Q, double2* work, cudaStream_t st) {
     (void)work;
+    KTimer kt("small_qr", 0.0, 0.0, st);
     small_qr_kernel<<<1, kT, 0, st>>>(S, m, k, lds, Q);
 }
 void small_complement(const double2* s, int m, double2* C, double2* work, cudaStream_t st) {
     (void)work;
+    KTimer kt("complement", 0.0, 0.0, st);
     complement_kernel<<<1, kT, 0, st>>>(s, m, C);
 }
 void small_gram_transform(const double2* M, int m, int ldm, const double2* C, int p, double2* out, int ldo,
                           double2* work, cudaStream_t st) {
+    KTimer kt("gram_transform", 0.0, 0.0, st);
     gram_transform_kernel<<<1, kT, 0, st>>>(M, m, ldm, C, p, out, ldo, work);
 }
 

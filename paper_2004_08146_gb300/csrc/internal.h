@@ -13,6 +13,22 @@
 
 namespace qcd {
 
+// ------------------------------------------------------------------ launch accounting
+// Counts a launch with its algorithmic bytes/flops; optionally times it with
+// events on `st` (see qcd_stats_reset).  Construct right before the launch.
+class KTimer {
+public:
+    KTimer(const char* name, double bytes, double flops, cudaStream_t st);
+    ~KTimer();
+    KTimer(const KTimer&) = delete;
+    KTimer& operator=(const KTimer&) = delete;
+private:
+    const char* name_;
+    cudaStream_t st_;
+    double bytes_, flops_;
+    cudaEvent_t ea_ = nullptr, eb_ = nullptr;
+};
+
 // ------------------------------------------------------------------ fine operator
 struct FineOp {
     Geom g{};
@@ -112,7 +128,7 @@ size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters);
 void small_harmonic_eig(const double2* G, const double2* H, int m, int ld, double* mu, double2* S,
                         double2* work, int* status, cudaStream_t st);
 // Orthonormal Q (m x k, column-major, leading dim m) of the columns of S
-// (m x k, leading dimension lds) by Householder QR.
+// (m x k, leading dimension lds) by modified Gram-Schmidt applied twice.
 void small_qr(const double2* S, int m, int k, int lds, double2* Q, double2* work, cudaStream_t st);
 // Orthonormal complement (m x (m-1)) of a unit vector s of length m.
 void small_complement(const double2* s, int m, double2* C, double2* work, cudaStream_t st);

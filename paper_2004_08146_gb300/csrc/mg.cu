@@ -453,6 +453,7 @@ inline int grid_for(size_t n, int th = 256) {
 // ------------------------------------------------------------------ host launchers
 void mg_build_P(const FineOp& f, Coarse& c, const double2* vecs, int nvec, cudaStream_t st) {
     dim3 grid(c.B.nb, 2);
+    KTimer kt("build_P", 0.0, 0.0, st);
     build_P_kernel<<<grid, 256, 256 * sizeof(double2), st>>>(f.g, c.B, nvec, vecs, c.P64, c.P32);
 }
 
@@ -460,14 +461,20 @@ void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st) {
     dim3 grid(c.B.nb, 9);
     size_t sm = (size_t)c.B.bs * 12 * sizeof(double2);
     if (sm > 48 * 1024) cudaFuncSetAttribute(build_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    KTimer kt("build_coarse", 0.0, 0.0, st);
     build_coarse_kernel<<<grid, 256, sm, st>>>(f.g, c.B, c.nv, f.U64, f.A64, c.P64, c.A64);
     size_t n = (size_t)c.B.nb * 9 * c.nc * c.nc;
+    KTimer kt2("narrow", (double)n * 24, 0.0, st);
     narrow_kernel<<<grid_for(n), 256, 0, st>>>(c.A64, c.A32, n);
 }
 
 void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st) {
     size_t warps = (size_t)c.B.nb * c.nc * nrhs;
     int grid = grid_for(warps * 32);
+    const double es = prec == QCD_FP64 ? 16.0 : 8.0;
+    const double nfine = (double)f.g.V * 12;
+    KTimer kt(prec == QCD_FP64 ? "restrict_f64" : "restrict_f32",
+              es * (nfine * c.nv + nrhs * (nfine + (double)c.gc.V * c.nc)), 8.0 * nfine * c.nv * nrhs, st);
     if (prec == QCD_FP64)
         restrict_kernel<double2, double><<<grid, 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)r, (double2*)xc, nrhs);
     else
@@ -477,6 +484,11 @@ void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const voi
 void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* xc, void* x, bool accumulate,
                 cudaStream_t st) {
     size_t n = (size_t)nrhs * c.B.nb * 2 * c.B.bs * 6;
+    const double es = prec == QCD_FP64 ? 16.0 : 8.0;
+    const double nfine = (double)f.g.V * 12;
+    KTimer kt(prec == QCD_FP64 ? "prolong_f64" : "prolong_f32",
+              es * (nfine * c.nv + nrhs * (nfine * (accumulate ? 2 : 1) + (double)c.gc.V * c.nc)),
+              8.0 * nfine * c.nv * nrhs, st);
     if (prec == QCD_FP64)
         prolong_kernel<double2><<<grid_for(n), 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)xc, (double2*)x, nrhs,
                                                              accumulate);
@@ -490,6 +502,10 @@ void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, vo
     Shifts sh{};
     for (int j = 0; j < nrhs; ++j) sh.t[j] = tau ? tau[j] : 0.0;
     size_t n = (size_t)nrhs * c.gc.V * c.nc;
+    const double es = prec == QCD_FP64 ? 16.0 : 8.0;
+    KTimer kt(prec == QCD_FP64 ? "coarse_apply_f64" : "coarse_apply_f32",
+              es * ((double)c.gc.V * 9 * c.nc * c.nc + 2.0 * nrhs * c.gc.V * c.nc),
+              8.0 * 9 * c.nc * c.nc * (double)c.gc.V * nrhs, st);
     if (prec == QCD_FP64)
         coarse_apply_kernel<double2, double><<<grid_for(n), 256, 0, st>>>(c.gc, c.nc, c.A64, (const double2*)x,
                                                                          (double2*)y, op, sh, nrhs);
@@ -513,6 +529,10 @@ void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op
     size_t sm = sizeof(double2) * ((size_t)bs + (size_t)(iters + 1) * iters + (iters + 1) + 2 * iters) +
                 sizeof(double) * iters + 4 * sizeof(int) +
                 (size_t)bs * 12 * (prec == QCD_FP64 ? sizeof(double2) : sizeof(float2));
+    const double rs = prec == QCD_FP64 ? 8.0 : 4.0;
+    const double sites = (double)sp.ncol[colour] * bs;
+    KTimer kt(prec == QCD_FP64 ? "sap_block_f64" : "sap_block_f32", rs * sites * (nrhs * 72.0 + 144.0),
+              1824.0 * sites * nrhs * iters, st);
     if (prec == QCD_FP64) {
         if (sm > 48 * 1024) cudaFuncSetAttribute(sap_block_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         sap_block_kernel<double><<<grid, bs, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour], op, sh,

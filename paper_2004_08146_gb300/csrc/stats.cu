@@ -1,0 +1,130 @@
+// Launch accounting for libqcd: every kernel launch goes through a KTimer,
+// which counts it with its algorithmic bytes and flops and, when enabled,
+// brackets it with CUDA events on the launching stream.  Process-wide.
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace qcd {
+
+namespace {
+struct Agg {
+    long long launches = 0, timed = 0;
+    double bytes = 0, flops = 0, ms = 0, timed_bytes = 0, timed_flops = 0;
+};
+struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+    double bytes, flops;
+};
+struct Stats {
+    std::mutex mu;
+    int mode = 0;
+    std::string filter;
+    std::map<std::string, Agg> agg;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+};
+Stats& S() {
+    static Stats* s = new Stats();
+    return *s;
+}
+cudaEvent_t take_event(Stats& s) {
+    if (!s.pool.empty()) {
+        cudaEvent_t e = s.pool.back();
+        s.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+KTimer::KTimer(const char* name, double bytes, double flops, cudaStream_t st) : name_(name), st_(st), bytes_(bytes),
+                                                                                flops_(flops) {
+    Stats& s = S();
+    std::lock_guard<std::mutex> g(s.mu);
+    Agg& a = s.agg[name_];
+    a.launches += 1;
+    a.bytes += bytes;
+    a.flops += flops;
+    if (s.mode == 1 || (s.mode == 2 && s.filter == name_)) {
+        ea_ = take_event(s);
+        eb_ = take_event(s);
+        if (ea_ && eb_) cudaEventRecord(ea_, st_);
+    }
+}
+
+KTimer::~KTimer() {
+    if (!ea_ || !eb_) return;
+    cudaEventRecord(eb_, st_);
+    Stats& s = S();
+    std::lock_guard<std::mutex> g(s.mu);
+    s.pending.push_back(Pending{name_, ea_, eb_, bytes_, flops_});
+}
+
+}  // namespace qcd
+
+extern "C" {
+
+int qcd_stats_reset(int mode, const char* filter) {
+    using namespace qcd;
+    if (mode < 0 || mode > 2) return QCD_EINVAL;
+    Stats& s = S();
+    std::lock_guard<std::mutex> g(s.mu);
+    for (auto& p : s.pending) {
+        cudaEventSynchronize(p.b);
+        s.pool.push_back(p.a);
+        s.pool.push_back(p.b);
+    }
+    s.pending.clear();
+    s.agg.clear();
+    s.mode = mode;
+    s.filter = filter ? filter : "";
+    return QCD_OK;
+}
+
+int qcd_stats_read(qcd_kernel_stat* out, int max, int* n) {
+    using namespace qcd;
+    if (!n || (max > 0 && !out)) return QCD_EINVAL;
+    Stats& s = S();
+    std::lock_guard<std::mutex> g(s.mu);
+    for (auto& p : s.pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            Agg& a = s.agg[p.name];
+            a.timed += 1;
+            a.ms += ms;
+            a.timed_bytes += p.bytes;
+            a.timed_flops += p.flops;
+        }
+        s.pool.push_back(p.a);
+        s.pool.push_back(p.b);
+    }
+    s.pending.clear();
+    int k = 0;
+    for (auto& kv : s.agg) {
+        if (k < max) {
+            qcd_kernel_stat& o = out[k];
+            memset(&o, 0, sizeof(o));
+            strncpy(o.name, kv.first.c_str(), sizeof(o.name) - 1);
+            o.launches = kv.second.launches;
+            o.timed = kv.second.timed;
+            o.total_ms = kv.second.ms;
+            o.bytes = kv.second.bytes;
+            o.flops = kv.second.flops;
+            o.timed_bytes = kv.second.timed_bytes;
+            o.timed_flops = kv.second.timed_flops;
+        }
+        ++k;
+    }
+    *n = k;
+    return QCD_OK;
+}
+
+}  // extern "C"

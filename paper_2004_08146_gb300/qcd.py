@@ -46,6 +46,7 @@ class qcd_params(ctypes.Structure):
         ("m_max", ctypes.c_int),
         ("block", ctypes.c_int),
         ("n_init", ctypes.c_int),
+        ("shift_rho", ctypes.c_int),
         ("update_every", ctypes.c_int),
         ("max_outer", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
@@ -62,6 +63,12 @@ class qcd_eig_info(ctypes.Structure):
     _fields_ = [("outer", ctypes.c_int), ("inner", ctypes.c_int), ("locked", ctypes.c_int),
                 ("updates", ctypes.c_int), ("converged", ctypes.c_int),
                 ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class qcd_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_longlong), ("timed", ctypes.c_longlong),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double),
+                ("timed_bytes", ctypes.c_double), ("timed_flops", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -93,6 +100,8 @@ _SIGS = {
     "qcd_mg_get_coarse": (_I, [_P, _DP]),
     "qcd_sap": (_I, [_P, _I, _I, _I, _P, _P, _DP, _I, _D]),
     "qcd_mg_cycle": (_I, [_P, _I, _I, _I, _P, _P, _DP]),
+    "qcd_stats_reset": (_I, [_I, ctypes.c_char_p]),
+    "qcd_stats_read": (_I, [ctypes.POINTER(qcd_kernel_stat), _I, _IP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -119,6 +128,22 @@ def _ptr(x):
 def _dbl(arr):
     a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64))
     return a, a.ctypes.data_as(_DP)
+
+
+def qcd_stats_reset(mode=0, kernel=None):
+    """Launch accounting: mode 0 counts, 1 times every launch, 2 times `kernel`."""
+    rc = _lib.qcd_stats_reset(int(mode), kernel.encode() if kernel else None)
+    if rc != QCD_OK:
+        raise QcdError(rc, "qcd_stats_reset")
+
+
+def qcd_stats_read():
+    n = ctypes.c_int(0)
+    _lib.qcd_stats_read(None, 0, ctypes.byref(n))
+    arr = (qcd_kernel_stat * max(1, n.value))()
+    _lib.qcd_stats_read(arr, n.value, ctypes.byref(n))
+    return [dict(name=a.name.decode(), launches=a.launches, timed=a.timed, total_ms=a.total_ms, bytes=a.bytes,
+                 flops=a.flops, timed_bytes=a.timed_bytes, timed_flops=a.timed_flops) for a in arr[:n.value]]
 
 
 def default_params(**kw):

@@ -1,0 +1,25 @@
+"""Synthetic workloads standing in for the paper's gauge ensembles (Table 1).
+
+Each entry fixes the lattice, the link roughness eps of U = exp(i eps H), the
+clover coefficient, the seed of the input generator, the quark mass m0 and
+the solver shape.  The m0 values were chosen with the CPU oracle
+(tests/golden/tune_m0.py writes tests/golden/workloads.json, which a CPU test
+compares with this table) so that min |lambda(Q)| lands near the stated
+target, the stand-in for the paper's "comparable conditioning" (Sec. 4).
+"""
+
+WORKLOADS = {
+    # 4^4, plain GD with GMRES inner solves; the oracle diagonalises Q densely
+    "c1_4c4": dict(dims=(4, 4, 4, 4), eps=0.3, csw=1.0, m0=-0.2, seed=1001, k=10,
+                   use_mg=0, agg=None, nv=0, sap=(2, 2, 2, 2)),
+    # 16 x 8^3, two-level MG with 2^4 aggregates, Nv = 8, SAP on 2^4 blocks, 50 pairs
+    "c2_16x8c3": dict(dims=(16, 8, 8, 8), eps=0.5, csw=1.5, m0=None, seed=1002, k=50,
+                      use_mg=1, agg=(2, 2, 2, 2), nv=8, sap=(2, 2, 2, 2), target=1e-2),
+}
+
+
+def get(name):
+    w = dict(WORKLOADS[name])
+    if w["m0"] is None:
+        raise KeyError(f"workload {name}: m0 not tuned yet")
+    return w
