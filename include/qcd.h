@@ -70,7 +70,7 @@ typedef struct qcd_params {
     double inner_tol;        /* FGMRES relative residual (Table 2: 1e-1) */
     int    inner_maxiter;    /* FGMRES iterations (Table 2: 5) */
     double coarse_tol;       /* coarse GMRES reduction (Table 2: 5e-1) */
-    int    coarse_maxiter;   /* coarse GMRES iteration cap (default 100) */
+    int    coarse_maxiter;   /* coarse GMRES iteration cap (default 64, <= 200) */
     int    plain_maxiter;    /* plain GMRES inner iterations without MG (default 20) */
     int    m_min;            /* Table 2: 30 */
     int    m_max;            /* Table 2: 50 */
@@ -99,6 +99,8 @@ typedef struct qcd_eig_info {
     int    converged;        /* 1 when all k pairs met tol */
     double max_residual;     /* max ||Q v - lambda v|| over the returned pairs */
     double seconds;          /* wall time of the call */
+    long long coarse_solves;     /* coarse-grid GMRES solves (per right-hand side) */
+    long long coarse_iterations; /* coarse-grid GMRES iterations, summed */
 } qcd_eig_info;
 
 /* Fill *p with the defaults above. */

@@ -66,6 +66,7 @@ struct qcd_ctx {
     size_t pinned_n = 0;
     double2* test_vectors = nullptr;  // FP64 setup vectors [nv][V*12]
     int n_test = 0;
+    bool no_coop = false;             // cooperative coarse launch unavailable: host-driven GMRES
 
     ~qcd_ctx() { release(); }
 
@@ -123,6 +124,8 @@ struct qcd_ctx {
         return h;
     }
     size_t nfine() const { return (size_t)f.g.V * 12; }
+    // device counters: [0] coarse solves, [1] coarse iterations
+    unsigned long long* counters() { return (unsigned long long*)buf("counters", 2 * sizeof(unsigned long long)); }
 };
 
 namespace {
@@ -142,7 +145,9 @@ void validate_params(const qcd_params& p) {
 }
 
 // ------------------------------------------------------------------ linear operators
-using OpFn = std::function<void(const void* in, void* out)>;
+// operator / preconditioner: out = op(in) for the right-hand sides whose
+// device flag in `act` is set (act may be null: all)
+using OpFn = std::function<void(const void* in, void* out, const int* act)>;
 
 struct GmresResult {
     std::vector<int> iters;
@@ -199,10 +204,10 @@ GmresResult gmres_batched(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn
         void* vj = Vk + (size_t)it * vs * eb;
         if (M) {
             void* zj = Zk + (size_t)it * vs * eb;
-            (*M)(vj, zj);
-            A(zj, w);
+            (*M)(vj, zj, nullptr);
+            A(zj, w, nullptr);
         } else {
-            A(vj, w);
+            A(vj, w, nullptr);
         }
         blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h1, part, st);
         blas_multiaxpy(prec, Vk, it + 1, vs, h1, -1.0, w, nrhs, n, st);
@@ -275,6 +280,64 @@ GmresResult gmres_batched(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn
     return out;
 }
 
+// Batched (F)GMRES with device-side control: the same algorithm as
+// gmres_batched (CGS twice, Givens), but the Hessenberg bookkeeping runs in
+// kry_* kernels and converged right-hand sides are skipped through the
+// device `active` flags, so the solve is one launch sequence with no host
+// round trip.  `outer_act` (may be null) masks right-hand sides from the start.
+struct DevGmresOut {
+    KryDev K;
+};
+DevGmresOut gmres_dev(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn& A, const OpFn* M, const void* b,
+                      void* x, double tol, int maxit, const std::string& tag, const int* outer_act) {
+    cudaStream_t st = ctx->st;
+    if (maxit > kMaxKry) throw QcdError(QCD_EINVAL, "too many Krylov steps");
+    const size_t vs = n * nrhs;
+    const size_t eb = esz(prec);
+    char* Vk = (char*)ctx->buf(tag + ".V", (size_t)(maxit + 1) * vs * eb);
+    char* Zk = M ? (char*)ctx->buf(tag + ".Z", (size_t)maxit * vs * eb) : nullptr;
+    void* w = ctx->buf(tag + ".w", vs * eb);
+    double2* h1 = (double2*)ctx->buf(tag + ".h1", (size_t)(maxit + 1) * nrhs * sizeof(double2));
+    double2* h2 = (double2*)ctx->buf(tag + ".h2", (size_t)(maxit + 1) * nrhs * sizeof(double2));
+    double2* nr = (double2*)ctx->buf(tag + ".nr", (size_t)nrhs * sizeof(double2));
+    double2* part = (double2*)ctx->buf(tag + ".part", (size_t)(maxit + 2) * nrhs * 64 * sizeof(double2));
+    KryDev K = kry_layout(ctx->buf(tag + ".K", kry_bytes(nrhs, maxit)), nrhs, maxit, tol);
+    blas_multidot(prec, b, 1, vs, b, nrhs, n, nr, part, st);
+    kry_init(K, nr, outer_act, st);
+    blas_zero(prec, x, vs, st);
+    blas_scale_dev(prec, b, Vk, K.scale, nrhs, n, false, false, st, K.active);
+    for (int it = 0; it < maxit; ++it) {
+        void* vj = Vk + (size_t)it * vs * eb;
+        if (M) {
+            void* zj = Zk + (size_t)it * vs * eb;
+            (*M)(vj, zj, K.active);
+            A(zj, w, K.active);
+        } else {
+            A(vj, w, K.active);
+        }
+        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h1, part, st, K.active);
+        blas_multiaxpy(prec, Vk, it + 1, vs, h1, -1.0, w, nrhs, n, st, K.active);
+        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h2, part, st, K.active);
+        blas_multiaxpy(prec, Vk, it + 1, vs, h2, -1.0, w, nrhs, n, st, K.active);
+        blas_multidot(prec, w, 1, vs, w, nrhs, n, nr, part, st, K.active);
+        kry_step(K, it, h1, h2, nr, st);
+        if (it + 1 < maxit) blas_scale_dev(prec, w, Vk + (size_t)(it + 1) * vs * eb, K.scale, nrhs, n, false, false, st,
+                                           K.active);
+    }
+    kry_finish(K, st);
+    blas_multiaxpy(prec, M ? (const void*)Zk : (const void*)Vk, maxit, vs, K.coef, 1.0, x, nrhs, n, st, outer_act);
+    check_launch("gmres_dev");
+    return DevGmresOut{K};
+}
+
+// per-right-hand-side steps of a finished gmres_dev (one device-to-host copy)
+std::vector<int> kry_iters(qcd_ctx* ctx, const KryDev& K) {
+    std::vector<int> it(K.nrhs);
+    CK(cudaMemcpyAsync(it.data(), K.k, K.nrhs * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return it;
+}
+
 // ------------------------------------------------------------------ hierarchy pieces
 void require_gauge(qcd_ctx* ctx) {
     if (!ctx->have_gauge) throw QcdError(QCD_ENOTSETUP, "no gauge field: call qcd_set_gauge first");
@@ -322,54 +385,88 @@ void ensure_sap(qcd_ctx* ctx) {
 
 // nu SAP sweeps (Eq. 2.10) on op(tau) x = b, x updated in place
 void sap_smooth(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau, int sweeps,
-                double tol) {
+                double tol, const int* act = nullptr) {
     ensure_sap(ctx);
     const size_t n = ctx->nfine();
     void* r = ctx->buf("sap.r", n * nrhs * esz(prec));
     void* scr = ctx->buf("sap.scratch", sap_scratch_bytes(ctx->sap, prec, nrhs, ctx->p.sap_block_iters));
     for (int s = 0; s < sweeps; ++s) {
         for (int colour = 0; colour < 2; ++colour) {
-            residual_op(ctx->f, prec, op, nrhs, b, x, r, tau, ctx->st);
-            sap_blocks(ctx->f, ctx->sap, colour, prec, op, nrhs, r, x, tau, ctx->p.sap_block_iters, tol, scr, ctx->st);
+            residual_op(ctx->f, prec, op, nrhs, b, x, r, tau, ctx->st, act);
+            sap_blocks(ctx->f, ctx->sap, colour, prec, op, nrhs, r, x, tau, ctx->p.sap_block_iters, tol, scr, ctx->st,
+                       act);
         }
     }
     check_launch("sap");
 }
 
-void smooth(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau) {
+void smooth(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau,
+            const int* act = nullptr) {
     if (ctx->p.nu <= 0) return;
     if (ctx->p.smoother == QCD_SMOOTHER_SAP) {
-        sap_smooth(ctx, prec, op, nrhs, b, x, tau, ctx->p.nu, ctx->p.sap_block_tol);
+        sap_smooth(ctx, prec, op, nrhs, b, x, tau, ctx->p.nu, ctx->p.sap_block_tol, act);
         return;
     }
     const size_t n = ctx->nfine();
     void* r = ctx->buf("gsm.r", n * nrhs * esz(prec));
     void* e = ctx->buf("gsm.e", n * nrhs * esz(prec));
     std::vector<double> tv(tau, tau + nrhs);
-    OpFn A = [ctx, prec, op, nrhs, tv](const void* in, void* out) {
-        apply_op(ctx->f, prec, op, nrhs, in, out, tv.data(), ctx->st);
+    OpFn A = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int* a) {
+        apply_op(ctx->f, prec, op, nrhs, in, out, tv.data(), ctx->st, a);
     };
+    double2* one = (double2*)ctx->buf("gsm.one", (size_t)nrhs * sizeof(double2));
+    {
+        std::vector<double2> ones(nrhs, make_double2(1, 0));
+        CK(cudaMemcpyAsync(one, ones.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+    }
     for (int s = 0; s < ctx->p.nu; ++s) {
-        residual_op(ctx->f, prec, op, nrhs, b, x, r, tau, ctx->st);
-        gmres_batched(ctx, prec, n, nrhs, A, nullptr, r, e, 0.0, ctx->p.gmres_smooth_iters, "gsm");
-        blas_axpby(prec, make_double2(1, 0), e, make_double2(1, 0), x, n * nrhs, ctx->st);
+        residual_op(ctx->f, prec, op, nrhs, b, x, r, tau, ctx->st, act);
+        gmres_dev(ctx, prec, n, nrhs, A, nullptr, r, e, 0.0, ctx->p.gmres_smooth_iters, "gsm", act);
+        blas_scale_dev(prec, e, x, one, nrhs, n, false, true, ctx->st, act);
     }
 }
 
 // two-level cycle x = M b (Eq. 2.8, post-smoothing only)
-void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau) {
+void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau,
+                   const int* act = nullptr) {
     const Coarse& c = ctx->c;
     const size_t nco = (size_t)c.gc.V * c.nc;
     void* rc = ctx->buf("cyc.rc", nco * nrhs * esz(prec));
     void* xc = ctx->buf("cyc.xc", nco * nrhs * esz(prec));
-    mg_restrict(ctx->f, c, prec, nrhs, b, rc, ctx->st);
-    std::vector<double> tv(tau, tau + nrhs);
-    OpFn Ac = [ctx, prec, op, nrhs, tv](const void* in, void* out) {
-        coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st);
-    };
-    gmres_batched(ctx, prec, nco, nrhs, Ac, nullptr, rc, xc, ctx->p.coarse_tol, ctx->p.coarse_maxiter, "coarse");
-    mg_prolong(ctx->f, c, prec, nrhs, xc, x, false, ctx->st);
-    smooth(ctx, prec, op, nrhs, b, x, tau);
+    mg_restrict(ctx->f, c, prec, nrhs, b, rc, ctx->st, act);
+    // coarse solve: one cooperative launch per group of <= kMaxCoarseRhs right-hand sides
+    double* taud = (double*)ctx->buf("cyc.tau", (size_t)nrhs * sizeof(double));
+    CK(cudaMemcpyAsync(taud, tau, nrhs * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    const int maxit = std::min(ctx->p.coarse_maxiter, kMaxCoarse);
+    bool done = !ctx->no_coop;
+    if (done) {
+        const int grp = std::min(nrhs, coarse_gmres_group(c, prec, maxit));
+        if (grp < 1) throw QcdError(QCD_EINVAL, "coarse level too large for the shared-memory Krylov basis");
+        void* scr = ctx->buf("cyc.scr", coarse_gmres_scratch(c, prec, grp, maxit, coarse_gmres_grid()));
+        int* its = (int*)ctx->buf("cyc.its", (size_t)nrhs * sizeof(int));
+        double* res = (double*)ctx->buf("cyc.res", (size_t)nrhs * sizeof(double));
+        for (int j0 = 0; j0 < nrhs && done; j0 += grp) {
+            const int nj = std::min(grp, nrhs - j0);
+            int rcode = coarse_gmres(c, prec, op, nj, (const char*)rc + (size_t)j0 * nco * esz(prec),
+                                     (char*)xc + (size_t)j0 * nco * esz(prec), taud + j0, act ? act + j0 : nullptr,
+                                     ctx->p.coarse_tol, maxit, scr, its + j0, res + j0, ctx->counters(), ctx->st);
+            if (rcode != 0) {
+                cudaGetLastError();
+                if (j0 > 0) throw QcdError(QCD_ECUDA, "cooperative coarse solve failed mid-batch");
+                ctx->no_coop = true;
+                done = false;
+            }
+        }
+    }
+    if (!done) {
+        std::vector<double> tv(tau, tau + nrhs);
+        OpFn Ac = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int*) {
+            coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st);
+        };
+        gmres_batched(ctx, prec, nco, nrhs, Ac, nullptr, rc, xc, ctx->p.coarse_tol, ctx->p.coarse_maxiter, "coarse");
+    }
+    mg_prolong(ctx->f, c, prec, nrhs, xc, x, false, ctx->st, act);
+    smooth(ctx, prec, op, nrhs, b, x, tau, act);
     check_launch("mg cycle");
 }
 
@@ -454,17 +551,23 @@ GmresResult inner_solve(qcd_ctx* ctx, int prec, int op, int nrhs, const void* rh
                         double tol, int maxit) {
     const size_t n = ctx->nfine();
     std::vector<double> tv(tau, tau + nrhs);
-    OpFn A = [ctx, prec, op, nrhs, tv](const void* in, void* out) {
-        apply_op(ctx->f, prec, op, nrhs, in, out, tv.data(), ctx->st);
+    OpFn A = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int* a) {
+        apply_op(ctx->f, prec, op, nrhs, in, out, tv.data(), ctx->st, a);
     };
+    DevGmresOut d;
     if (ctx->p.use_mg) {
         require_mg(ctx);
-        OpFn M = [ctx, prec, op, nrhs, tv](const void* in, void* out) {
-            mg_cycle_impl(ctx, prec, op, nrhs, in, out, tv.data());
+        OpFn M = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int* a) {
+            mg_cycle_impl(ctx, prec, op, nrhs, in, out, tv.data(), a);
         };
-        return gmres_batched(ctx, prec, n, nrhs, A, &M, rhs, t, tol, maxit, "fine");
+        d = gmres_dev(ctx, prec, n, nrhs, A, &M, rhs, t, tol, maxit, "fine", nullptr);
+    } else {
+        d = gmres_dev(ctx, prec, n, nrhs, A, nullptr, rhs, t, tol, maxit, "fine", nullptr);
     }
-    return gmres_batched(ctx, prec, n, nrhs, A, nullptr, rhs, t, tol, maxit, "fine");
+    GmresResult out;
+    out.iters = kry_iters(ctx, d.K);
+    out.resest.assign(nrhs, 0.0);
+    return out;
 }
 
 // (Q - tau_j) x_j = b_j to relative tol, FP64 residuals; b, x arrays of
@@ -714,6 +817,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
     const int n0 = P.use_mg ? ctx->n_test : P.n_init;
     if (n0 + block > P.m_max) throw QcdError(QCD_EINVAL, "m_max too small for the start basis");
     gd.alloc(P.m_max + block, k + P.m_max + 2 * block + 8, block);
+    CK(cudaMemsetAsync(ctx->counters(), 0, 2 * sizeof(unsigned long long), st));
     double2* t0 = gd.tmp;
     // start basis: setup test vectors (or random vectors without MG)
     for (int i = 0; i < n0; ++i) {
@@ -848,8 +952,10 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
             gd.harmonic(th, cl);
             int keep = std::min(P.m_min, gd.m);
             CK(cudaMemcpyAsync(gd.idx, cl.data(), keep * sizeof(int), cudaMemcpyHostToDevice, st));
-            KTimer kt("gather_columns", 0.0, 0.0, st);
-            gather_columns_kernel<<<1, 256, 0, st>>>(gd.S, gd.m, gd.idx, keep, gd.work);
+            {
+                KTimer kt("gather_columns", 0.0, 0.0, st);
+                gather_columns_kernel<<<1, 256, 0, st>>>(gd.S, gd.m, gd.idx, keep, gd.work);
+            }
             small_qr(gd.work, gd.m, keep, gd.m, gd.C, nullptr, st);
             gd.transform(gd.C, keep);
             CK(cudaStreamSynchronize(st));
@@ -874,6 +980,10 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
     CK(cudaStreamSynchronize(st));
     const bool ok = finished && nout == k;
     if (info) {
+        unsigned long long cnt[2] = {0, 0};
+        CK(cudaMemcpy(cnt, ctx->counters(), sizeof(cnt), cudaMemcpyDeviceToHost));
+        info->coarse_solves = (long long)cnt[0];
+        info->coarse_iterations = (long long)cnt[1];
         info->outer = outer;
         info->inner = inner;
         info->locked = gd.nlock;
@@ -925,7 +1035,7 @@ void qcd_default_params(qcd_params* p) {
     p->inner_tol = 1e-1;
     p->inner_maxiter = 5;
     p->coarse_tol = 0.5;
-    p->coarse_maxiter = 100;
+    p->coarse_maxiter = 64;
     p->plain_maxiter = 20;
     p->m_min = 30;
     p->m_max = 50;

@@ -30,9 +30,11 @@ __global__ void convert_kernel(const Zi* __restrict__ x, Zo* __restrict__ y, siz
 // partial[(v * nsplit) + split] = sum over this split of conj(X[i][j]) w[j]
 template <typename Z>
 __global__ void multidot_partial_kernel(const Z* __restrict__ X, size_t xstride_vec, const Z* __restrict__ w,
-                                        int nrhs, size_t n, int nsplit, double2* __restrict__ partial) {
+                                        int nrhs, size_t n, int nsplit, double2* __restrict__ partial,
+                                        const int* __restrict__ act) {
     const int v = blockIdx.y;            // v = i * nrhs + j
     const int i = v / nrhs, j = v % nrhs;
+    if (act != nullptr && !act[j]) return;
     const Z* x = X + (size_t)i * xstride_vec + (size_t)j * n;
     const Z* y = w + (size_t)j * n;
     const size_t chunk = (n + nsplit - 1) / nsplit;
@@ -69,14 +71,16 @@ __global__ void multidot_final_kernel(const double2* __restrict__ partial, int n
 
 template <typename Z, typename R>
 __global__ void multiaxpy_kernel(const Z* __restrict__ X, int nvec, size_t xstride_vec, const double2* __restrict__ c,
-                                 double sign, Z* __restrict__ w, int nrhs, size_t n) {
+                                 double sign, Z* __restrict__ w, int nrhs, size_t n, const int* __restrict__ act) {
     const size_t total = n * nrhs;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(t / n);
+        if (act != nullptr && !act[j]) continue;
         const size_t k = t - (size_t)j * n;
         double2 acc = make_double2(0, 0);
         for (int i = 0; i < nvec; ++i) {
             double2 ci = c[i * nrhs + j];
+            if (ci.x == 0.0 && ci.y == 0.0) continue;   // unused basis slots may hold stale data
             Z xv = X[(size_t)i * xstride_vec + (size_t)j * n + k];
             acc.x += ci.x * xv.x - ci.y * xv.y;
             acc.y += ci.x * xv.y + ci.y * xv.x;
@@ -90,10 +94,11 @@ __global__ void multiaxpy_kernel(const Z* __restrict__ X, int nvec, size_t xstri
 
 template <typename Z, typename R>
 __global__ void scale_dev_kernel(const Z* __restrict__ x, Z* __restrict__ y, const double2* __restrict__ alpha,
-                                 int nrhs, size_t n, bool invert_real, bool accumulate) {
+                                 int nrhs, size_t n, bool invert_real, bool accumulate, const int* __restrict__ act) {
     const size_t total = n * nrhs;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(t / n);
+        if (act != nullptr && !act[j]) continue;
         double2 a = alpha[j];
         if (invert_real) a = make_double2(a.x != 0.0 ? 1.0 / a.x : 0.0, 0.0);
         Z xv = x[t];
@@ -164,47 +169,49 @@ void blas_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, c
         convert_kernel<float2, double2><<<grid_for(n), kThreads, 0, st>>>((const float2*)x, (double2*)y, n);
 }
 void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const void* w, int nrhs, size_t n,
-                   double2* dots, double2* partial, cudaStream_t st) {
+                   double2* dots, double2* partial, cudaStream_t st, const int* act) {
     if (nvec <= 0) return;
-    int nsplit = (int)((n + 32767) / 32768);
+    // enough CTAs to fill the GPU (about 4 per SM), at least 2048 elements each
+    int nsplit = 608 / (nvec * nrhs);
     if (nsplit > 64) nsplit = 64;
+    if ((size_t)nsplit * 2048 > n) nsplit = (int)(n / 2048);
     if (nsplit < 1) nsplit = 1;
     dim3 grid(nsplit, nvec * nrhs);
     KTimer kt(prec == QCD_FP64 ? "multidot_f64" : "multidot_f32", (double)(nvec + 1) * nrhs * n * esz_of(prec),
               8.0 * nvec * nrhs * n, st);
     if (prec == QCD_FP64)
         multidot_partial_kernel<double2><<<grid, kThreads, 0, st>>>((const double2*)X, xstride_vec, (const double2*)w,
-                                                                   nrhs, n, nsplit, partial);
+                                                                   nrhs, n, nsplit, partial, act);
     else
         multidot_partial_kernel<float2><<<grid, kThreads, 0, st>>>((const float2*)X, xstride_vec, (const float2*)w,
-                                                                  nrhs, n, nsplit, partial);
+                                                                  nrhs, n, nsplit, partial, act);
     int nv = nvec * nrhs;
     KTimer kt2("multidot_final", 0.0, 0.0, st);
     multidot_final_kernel<<<(nv + 127) / 128, 128, 0, st>>>(partial, nsplit, nv, dots);
 }
 void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const double2* c, double sign, void* w,
-                    int nrhs, size_t n, cudaStream_t st) {
+                    int nrhs, size_t n, cudaStream_t st, const int* act) {
     if (nvec <= 0) return;
     size_t total = n * nrhs;
     KTimer kt(prec == QCD_FP64 ? "multiaxpy_f64" : "multiaxpy_f32", (double)(nvec + 2) * nrhs * n * esz_of(prec),
               8.0 * nvec * nrhs * n, st);
     if (prec == QCD_FP64)
         multiaxpy_kernel<double2, double><<<grid_for(total), kThreads, 0, st>>>((const double2*)X, nvec, xstride_vec, c,
-                                                                              sign, (double2*)w, nrhs, n);
+                                                                              sign, (double2*)w, nrhs, n, act);
     else
         multiaxpy_kernel<float2, float><<<grid_for(total), kThreads, 0, st>>>((const float2*)X, nvec, xstride_vec, c,
-                                                                            sign, (float2*)w, nrhs, n);
+                                                                            sign, (float2*)w, nrhs, n, act);
 }
 void blas_scale_dev(int prec, const void* x, void* y, const double2* alpha, int nrhs, size_t n, bool invert_real,
-                    bool accumulate, cudaStream_t st) {
+                    bool accumulate, cudaStream_t st, const int* act) {
     size_t total = n * nrhs;
     KTimer kt("blas_scale", (double)total * (accumulate ? 3 : 2) * esz_of(prec), 0.0, st);
     if (prec == QCD_FP64)
         scale_dev_kernel<double2, double><<<grid_for(total), kThreads, 0, st>>>((const double2*)x, (double2*)y, alpha,
-                                                                              nrhs, n, invert_real, accumulate);
+                                                                              nrhs, n, invert_real, accumulate, act);
     else
         scale_dev_kernel<float2, float><<<grid_for(total), kThreads, 0, st>>>((const float2*)x, (float2*)y, alpha,
-                                                                            nrhs, n, invert_real, accumulate);
+                                                                            nrhs, n, invert_real, accumulate, act);
 }
 void blas_gamma5(int prec, const void* x, void* y, size_t nsites, cudaStream_t st) {
     size_t total = nsites * 12;

@@ -123,10 +123,12 @@ __global__ void clover_build_kernel(const double2* __restrict__ U, Geom g, doubl
 template <typename R>
 __global__ void __launch_bounds__(128) wilson_clover_kernel(
     cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in, const cplx<R>* __restrict__ b,
-    const cplx<R>* __restrict__ U, const R* __restrict__ A, Geom g, int op, Shifts tau, size_t stride) {
+    const cplx<R>* __restrict__ U, const R* __restrict__ A, Geom g, int op, Shifts tau, size_t stride,
+    const int* __restrict__ act) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.V) return;
     const int j = blockIdx.y;
+    if (act != nullptr && !act[j]) return;
     in += j * stride;
     out += j * stride;
     int x[4];
@@ -190,7 +192,7 @@ void launch_clover_build(const FineOp& f, cudaStream_t st) {
 
 template <typename R>
 void launch_dirac(const FineOp& f, int op, int nrhs, const void* in, void* out, const void* b,
-                  const double* tau, cudaStream_t st) {
+                  const double* tau, const int* act, cudaStream_t st) {
     Shifts sh{};
     for (int j = 0; j < nrhs; ++j) sh.t[j] = tau ? tau[j] : 0.0;
     dim3 grid((f.g.V + 127) / 128, nrhs);
@@ -200,19 +202,19 @@ void launch_dirac(const FineOp& f, int op, int nrhs, const void* in, void* out, 
     KTimer kt(std::is_same<R, double>::value ? "wilson_clover_f64" : "wilson_clover_f32", bytes,
               1824.0 * f.g.V * nrhs, st);
     wilson_clover_kernel<R><<<grid, 128, 0, st>>>((cplx<R>*)out, (const cplx<R>*)in, (const cplx<R>*)b,
-                                                  U, A, f.g, op, sh, (size_t)f.g.V * 12);
+                                                  U, A, f.g, op, sh, (size_t)f.g.V * 12, act);
 }
 
 void apply_op(const FineOp& f, int prec, int op, int nrhs, const void* in, void* out,
-              const double* tau, cudaStream_t st) {
-    if (prec == QCD_FP64) launch_dirac<double>(f, op, nrhs, in, out, nullptr, tau, st);
-    else launch_dirac<float>(f, op, nrhs, in, out, nullptr, tau, st);
+              const double* tau, cudaStream_t st, const int* act) {
+    if (prec == QCD_FP64) launch_dirac<double>(f, op, nrhs, in, out, nullptr, tau, act, st);
+    else launch_dirac<float>(f, op, nrhs, in, out, nullptr, tau, act, st);
 }
 
 void residual_op(const FineOp& f, int prec, int op, int nrhs, const void* b, const void* x, void* r,
-                 const double* tau, cudaStream_t st) {
-    if (prec == QCD_FP64) launch_dirac<double>(f, op, nrhs, x, r, b, tau, st);
-    else launch_dirac<float>(f, op, nrhs, x, r, b, tau, st);
+                 const double* tau, cudaStream_t st, const int* act) {
+    if (prec == QCD_FP64) launch_dirac<double>(f, op, nrhs, x, r, b, tau, act, st);
+    else launch_dirac<float>(f, op, nrhs, x, r, b, tau, act, st);
 }
 
 }  // namespace qcd

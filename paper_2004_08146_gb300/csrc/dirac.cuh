@@ -112,6 +112,29 @@ __device__ __forceinline__ void clover_apply(const R* __restrict__ A, const Spin
     }
 }
 
+// Same product with the packed blocks in shared memory.
+template <typename R>
+__device__ __forceinline__ void clover_apply_smem(const R* A, const Spinor<R>& x, Spinor<R>& y) {
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        const R* a = A + 36 * chi;
+        const cplx<R>* xs = x.c + 6 * chi;
+        cplx<R>* ys = y.c + 6 * chi;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) ys[i] = a[i] * xs[i];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+#pragma unroll
+            for (int j = i + 1; j < 6; ++j) {
+                const int o = herm_off(i, j);
+                cplx<R> aij = mk<R>(a[o], a[o + 1]);
+                ys[i] += aij * xs[j];
+                ys[j] += cmulc(aij, xs[i]);
+            }
+        }
+    }
+}
+
 // neighbour site and boundary sign
 __device__ __forceinline__ int nb_fwd(const Geom& g, const int x[4], int s, int mu, int& sgn_neg) {
     int y[4] = {x[0], x[1], x[2], x[3]};

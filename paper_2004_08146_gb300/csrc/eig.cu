@@ -10,6 +10,7 @@ namespace qcd {
 
 namespace {
 constexpr int kT = 256;
+constexpr int kTE = 512;   // threads of the harmonic eigen kernel
 
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
@@ -29,8 +30,10 @@ __device__ double block_reduce_sum(double v, double* red) {
     return r;
 }
 
-// work layout: L[m*m], Li[m*m], T[m*m], C[m*m], Z[m*m] (column-major, ld = m)
-__global__ void __launch_bounds__(kT) harmonic_eig_kernel(const double2* __restrict__ G, const double2* __restrict__ Hm,
+// work layout: L[m*m], Li[m*m], T[m*m] in global memory; C and Z (the Jacobi
+// working matrix and its accumulated rotations) in 2*m*m double2 of shared
+// memory (column-major, ld = m)
+__global__ void __launch_bounds__(kTE) harmonic_eig_kernel(const double2* __restrict__ G, const double2* __restrict__ Hm,
                                                           int m, int ld, double* __restrict__ mu,
                                                           double2* __restrict__ S, double2* __restrict__ work,
                                                           int* __restrict__ status) {
@@ -39,11 +42,12 @@ __global__ void __launch_bounds__(kT) harmonic_eig_kernel(const double2* __restr
     __shared__ double pc[32], ps[32];
     __shared__ double2 pph[32];
     const int tid = threadIdx.x;
+    extern __shared__ double2 shm[];
     double2* L = work;
     double2* Li = L + m * m;
     double2* T = Li + m * m;
-    double2* C = T + m * m;
-    double2* Z = C + m * m;
+    double2* C = shm;            // working matrix and eigenvectors in shared memory
+    double2* Z = shm + m * m;
 #define IDX(i, j) ((j) * m + (i))
     for (int e = tid; e < m * m; e += blockDim.x) {
         int i = e % m, j = e / m;
@@ -107,7 +111,10 @@ __global__ void __launch_bounds__(kT) harmonic_eig_kernel(const double2* __restr
         double off = 0.0;
         for (int e = tid; e < m * m; e += blockDim.x) if (e % m != e / m) off += cabs2(C[e]);
         off = block_reduce_sum(off, red);
-        if (off <= 1e-30 * fro || m < 2) break;
+        // stop at an off-diagonal norm of 1e-14 relative: the FP64 round-off
+        // floor of m^2 entries sits near (m eps)^2 ~ 1e-28, so a stricter test
+        // would never pass and would run every sweep
+        if (off <= 1e-28 * fro || m < 2) break;
         for (int rnd = 0; rnd < mm - 1; ++rnd) {
             if (tid < npair) {
                 int k = tid;
@@ -254,7 +261,9 @@ __global__ void __launch_bounds__(kT) gram_transform_kernel(const double2* __res
 void small_harmonic_eig(const double2* G, const double2* H, int m, int ld, double* mu, double2* S, double2* work,
                         int* status, cudaStream_t st) {
     KTimer kt("harmonic_eig", 0.0, 0.0, st);
-    harmonic_eig_kernel<<<1, kT, 0, st>>>(G, H, m, ld, mu, S, work, status);
+    const size_t sm = (size_t)2 * m * m * sizeof(double2);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(harmonic_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    harmonic_eig_kernel<<<1, kTE, sm, st>>>(G, H, m, ld, mu, S, work, status);
 }
 void small_qr(const double2* S, int m, int k, int lds, double2* Q, double2* work, cudaStream_t st) {
     (void)work;

@@ -77,10 +77,12 @@ struct Coarse {
 
 // ------------------------------------------------------------------ kernels (dirac.cu)
 void launch_clover_build(const FineOp& f, cudaStream_t st);
+// `act` (device, per right-hand side, may be null): skip right-hand sides
+// whose flag is 0 (converged systems of a batched Krylov solve).
 void apply_op(const FineOp& f, int prec, int op, int nrhs, const void* in, void* out,
-              const double* tau, cudaStream_t st);
+              const double* tau, cudaStream_t st, const int* act = nullptr);
 void residual_op(const FineOp& f, int prec, int op, int nrhs, const void* b, const void* x, void* r,
-                 const double* tau, cudaStream_t st);
+                 const double* tau, cudaStream_t st, const int* act = nullptr);
 
 // ------------------------------------------------------------------ kernels (blas.cu)
 // All vectors are complex (double2 / float2) of length n; "sets" are arrays of
@@ -90,13 +92,13 @@ void blas_copy(int prec, const void* x, void* y, size_t n, cudaStream_t st);
 void blas_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, cudaStream_t st);
 // dots[i*nrhs + j] = <X[i][j], w[j]> for i < nvec (FP64 results, device)
 void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const void* w, int nrhs,
-                   size_t n, double2* dots, double2* partial, cudaStream_t st);
+                   size_t n, double2* dots, double2* partial, cudaStream_t st, const int* act = nullptr);
 // w[j] += sign * sum_i c[i*nrhs + j] X[i][j]
 void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const double2* c, double sign,
-                    void* w, int nrhs, size_t n, cudaStream_t st);
+                    void* w, int nrhs, size_t n, cudaStream_t st, const int* act = nullptr);
 // y[j] = alpha_j x[j] (+ y[j] when accumulate), alpha from device array of nrhs complex
 void blas_scale_dev(int prec, const void* x, void* y, const double2* alpha, int nrhs, size_t n,
-                    bool invert_real, bool accumulate, cudaStream_t st);
+                    bool invert_real, bool accumulate, cudaStream_t st, const int* act = nullptr);
 void blas_gamma5(int prec, const void* x, void* y, size_t nsites_times_rhs, cudaStream_t st);
 void blas_gaussian(double2* x, size_t n, unsigned long long seed, unsigned long long offset, cudaStream_t st);
 // y = a*x + b*y (host scalars), complex
@@ -105,9 +107,10 @@ void blas_axpby(int prec, double2 a, const void* x, double2 b, void* y, size_t n
 // ------------------------------------------------------------------ kernels (mg.cu)
 void mg_build_P(const FineOp& f, Coarse& c, const double2* vecs, int nvec, cudaStream_t st);
 void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st);
-void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st);
+void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st,
+                 const int* act = nullptr);
 void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* xc, void* x, bool accumulate,
-                cudaStream_t st);
+                cudaStream_t st, const int* act = nullptr);
 void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, void* y, const double* tau,
                   cudaStream_t st);
 
@@ -119,8 +122,42 @@ struct SapPlan {
 // x += block solves of op(tau) on the blocks of `colour`, rhs r (full fields)
 void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op, int nrhs,
                 const void* r, void* x, const double* tau, int iters, double tol,
-                void* scratch, cudaStream_t st);
+                void* scratch, cudaStream_t st, const int* act = nullptr);
 size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters);
+
+// ------------------------------------------------------------------ kernels (krylov.cu)
+constexpr int kMaxKry = 64;        // fine (F)GMRES steps per solve
+constexpr int kMaxCoarse = 200;    // coarse GMRES steps per solve
+constexpr int kMaxCoarseRhs = 16;  // right-hand sides per coarse launch
+
+// Device-resident state of a batched (F)GMRES solve (see krylov.cu).
+struct KryDev {
+    int nrhs = 0, maxit = 0;
+    double tol = 0;
+    double* beta = nullptr;    // [nrhs] ||b_j||
+    double* resid = nullptr;   // [nrhs] relative residual estimates
+    int* active = nullptr;     // [nrhs] 1 while right-hand side j iterates
+    int* k = nullptr;          // [nrhs] steps taken
+    double* cs = nullptr;      // [nrhs][maxit]
+    double2* sn = nullptr;     // [nrhs][maxit]
+    double2* g = nullptr;      // [nrhs][maxit + 1]
+    double2* R = nullptr;      // [nrhs][maxit][maxit] rotated Hessenberg
+    double2* coef = nullptr;   // [maxit][nrhs] solution coefficients
+    double2* scale = nullptr;  // [nrhs] normalisation of the next basis vector
+};
+size_t kry_bytes(int nrhs, int maxit);
+KryDev kry_layout(void* buf, int nrhs, int maxit, double tol);
+void kry_init(const KryDev& K, const double2* nrm, const int* outer_act, cudaStream_t st);
+void kry_step(const KryDev& K, int it, const double2* h1, const double2* h2, const double2* nrm, cudaStream_t st);
+void kry_finish(const KryDev& K, cudaStream_t st);
+// Whole batched GMRES on the coarse stencil in one cooperative launch;
+// returns 0 on success, < 0 when the cooperative launch is not possible.
+size_t coarse_gmres_scratch(const Coarse& c, int prec, int nrhs, int maxit, int nct);
+int coarse_gmres_grid();
+int coarse_gmres_group(const Coarse& c, int prec, int maxit);   // right-hand sides per launch
+int coarse_gmres(const Coarse& c, int prec, int op, int nrhs, const void* b, void* x, const double* tau_dev,
+                 const int* act, double tol, int maxit, void* scratch, int* iters, double* resid,
+                 unsigned long long* counter, cudaStream_t st);
 
 // ------------------------------------------------------------------ kernels (eig.cu)
 // Harmonic Ritz pairs of the pencil G s = theta H s (G = W^H W, H = W^H V):

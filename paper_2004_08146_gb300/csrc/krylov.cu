@@ -1,0 +1,574 @@
+// Device-resident Krylov control.
+//
+// (1) The Hessenberg bookkeeping of batched (F)GMRES -- Givens rotations,
+//     residual estimates, per-right-hand-side stopping and the final
+//     triangular solve -- as tiny kernels, so that a whole (F)GMRES solve is a
+//     fixed launch sequence without host round trips (converged right-hand
+//     sides are skipped by every kernel through the `active` flags).
+// (2) A persistent cooperative kernel that runs a complete batched GMRES on
+//     the coarse stencil (the coarse-grid solve to a fixed reduction, Table 2
+//     "coarse grid tolerance") in one launch: operator apply, classical
+//     Gram-Schmidt applied twice, Givens and the solution update, separated by
+//     grid-wide barriers of the cooperative launch.
+#include <cooperative_groups.h>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace qcd {
+
+namespace {
+
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// Givens update of column `it` of one right-hand side; h[0..it] is the new
+// Hessenberg column, hn its sub-diagonal entry.  Returns |g_{it+1}|.
+__device__ double givens_column(double2* h, double hn, double* cs, double2* sn, double2* g, int it) {
+    for (int i = 0; i < it; ++i) {
+        double2 a = h[i], c = h[i + 1];
+        h[i] = cs[i] * a + sn[i] * c;
+        h[i + 1] = cs[i] * c - conj(sn[i]) * a;
+    }
+    double2 a = h[it];
+    double2 c = make_double2(hn, 0.0);
+    double aa = sqrt(cabs2(a)), rr = sqrt(aa * aa + hn * hn);
+    if (aa > 0) {
+        cs[it] = aa / rr;
+        sn[it] = (1.0 / rr) * ((1.0 / aa) * a * conj(c));
+    } else {
+        cs[it] = 0.0;
+        sn[it] = make_double2(1, 0);
+    }
+    h[it] = cs[it] * a + sn[it] * c;
+    g[it + 1] = -1.0 * (conj(sn[it]) * g[it]);
+    g[it] = cs[it] * g[it];
+    return sqrt(cabs2(g[it + 1]));
+}
+
+__global__ void kry_init_kernel(KryDev K, const double2* __restrict__ nrm, const int* __restrict__ outer_act) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K.nrhs) return;
+    const double b = sqrt(fmax(nrm[j].x, 0.0));
+    const bool on = b > 0.0 && (outer_act == nullptr || outer_act[j] != 0);
+    K.beta[j] = b;
+    K.g[(size_t)j * (K.maxit + 1)] = make_double2(b, 0.0);
+    K.active[j] = on ? 1 : 0;
+    K.k[j] = 0;
+    K.scale[j] = make_double2(on ? 1.0 / b : 0.0, 0.0);
+}
+
+__global__ void kry_step_kernel(KryDev K, int it, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                                const double2* __restrict__ nrm) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K.nrhs || !K.active[j]) return;
+    double2 h[kMaxKry + 1];
+    for (int i = 0; i <= it; ++i) h[i] = h1[i * K.nrhs + j] + h2[i * K.nrhs + j];
+    const double hn = sqrt(fmax(nrm[j].x, 0.0));
+    double* cs = K.cs + (size_t)j * K.maxit;
+    double2* sn = K.sn + (size_t)j * K.maxit;
+    double2* g = K.g + (size_t)j * (K.maxit + 1);
+    const double res = givens_column(h, hn, cs, sn, g, it);
+    double2* R = K.R + (size_t)j * K.maxit * K.maxit;
+    for (int i = 0; i <= it; ++i) R[(size_t)i * K.maxit + it] = h[i];
+    K.k[j] = it + 1;
+    K.scale[j] = make_double2(hn > 0 ? 1.0 / hn : 0.0, 0.0);
+    if (res <= K.tol * K.beta[j]) K.active[j] = 0;
+    K.resid[j] = K.beta[j] > 0 ? res / K.beta[j] : 0.0;
+}
+
+__global__ void kry_finish_kernel(KryDev K) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K.nrhs) return;
+    const int kd = K.k[j];
+    const double2* R = K.R + (size_t)j * K.maxit * K.maxit;
+    const double2* g = K.g + (size_t)j * (K.maxit + 1);
+    double2 y[kMaxKry];
+    for (int i = kd - 1; i >= 0; --i) {
+        double2 s = g[i];
+        for (int l = i + 1; l < kd; ++l) s -= R[(size_t)i * K.maxit + l] * y[l];
+        double2 d = R[(size_t)i * K.maxit + i];
+        double den = cabs2(d);
+        y[i] = den > 0 ? (1.0 / den) * cmulc(d, s) : make_double2(0, 0);
+    }
+    for (int i = 0; i < K.maxit; ++i) K.coef[(size_t)i * K.nrhs + j] = i < kd ? y[i] : make_double2(0, 0);
+}
+
+// ------------------------------------------------------------------ coarse GMRES
+// Each CTA owns the chunk [lo, hi) of every coarse vector.  It keeps its
+// chunk of the whole Krylov basis in shared memory; only the newest basis
+// vector is published to global memory (double-buffered) for the neighbour
+// reads of the stencil.  Inner products are accumulated into FP64 totals
+// with atomics, one grid barrier per reduction; the totals are double-
+// buffered by iteration parity, so zeroing the next iteration's buffer never
+// races with readers of the current one.  Every CTA performs the (tiny)
+// Givens updates itself on identical totals.
+template <typename Z, typename R>
+struct CoarseArgs {
+    Geom gc;
+    int nc;
+    const Z* A;          // [Vc][9][col][row]
+    const Z* b;          // nrhs coarse vectors
+    Z* x;                // nrhs coarse vectors (output)
+    Z* Vg;               // [2][nrhs][nco] newest basis vector, double-buffered
+    double2* tot;        // [2 parities][2 passes][npair] FP64 totals
+    double2* Rg;         // [nrhs][maxit][maxit] triangular factor (written by CTA 0)
+    double2* yv;         // [nrhs][maxit]
+    int* iters;          // [nrhs] iterations used (written by CTA 0)
+    unsigned long long* counter;   // [2] solves, iterations (accumulated, may be null)
+    double* resid;       // [nrhs] relative residual estimates
+    int op;
+    const double* tau;   // device [nrhs]
+    const int* act;      // device [nrhs] or null
+    double tol;
+    int maxit;
+    int nrhs;
+    int E;               // chunk length per CTA (= sites per CTA * nc)
+    int sps;             // coarse sites per CTA
+    int a_smem;          // 1: this CTA's stencil blocks are staged in shared memory
+};
+
+template <typename Z, typename R>
+__device__ __forceinline__ void coarse_row(const CoarseArgs<Z, R>& a, const Z* xj, int s, int r, const int c[4], R tj,
+                                           Z& out) {
+    Z acc; acc.x = 0; acc.y = 0;
+    for (int d = 0; d < 9; ++d) {
+        int sn = s;
+        if (d > 0) {
+            int mu = (d - 1) & 3, step = d <= 4 ? 1 : -1;
+            int cn[4] = {c[0], c[1], c[2], c[3]};
+            cn[mu] = (cn[mu] + step + a.gc.L[mu]) % a.gc.L[mu];
+            sn = site_index(a.gc, cn);
+        }
+        const Z* am = a.A + (((size_t)s * 9 + d) * a.nc) * a.nc + r;
+        const Z* xs = xj + (size_t)sn * a.nc;
+        for (int col = 0; col < a.nc; ++col) acc += am[(size_t)col * a.nc] * xs[col];
+    }
+    const R sg = r < a.nc / 2 ? R(1) : R(-1);
+    Z xv = xj[(size_t)s * a.nc + r];
+    if (a.op == QCD_OP_D) { acc -= (tj * sg) * xv; }
+    else { acc = sg * acc; acc -= tj * xv; }
+    out = acc;
+}
+
+struct CoarseSmem { size_t As, xn, Vs, ws, hc, h1, hcol, cs, sn, g, beta, live, kd, total; };
+template <typename Z>
+__host__ __device__ inline CoarseSmem coarse_smem(int nrhs, int maxit, int E, int sps = 0, int nc = 0) {
+    auto up = [](size_t v) { return (v + 15) & ~size_t(15); };
+    CoarseSmem L;
+    size_t o = 0;
+    L.As = o;   o = up(o + sizeof(Z) * (size_t)sps * 9 * nc * nc);
+    L.xn = o;   o = up(o + sizeof(Z) * (size_t)nrhs * sps * 9 * nc);
+    L.Vs = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 1) * nrhs * E);
+    L.ws = o;   o = up(o + sizeof(Z) * (size_t)nrhs * E);
+    L.hc = o;   o = up(o + sizeof(double2) * (size_t)(maxit + 2) * nrhs);
+    L.h1 = o;   o = up(o + sizeof(double2) * (size_t)(maxit + 2) * nrhs);
+    L.hcol = o; o = up(o + sizeof(double2) * (size_t)(maxit + 1) * nrhs);
+    L.cs = o;   o = up(o + sizeof(double) * (size_t)nrhs * maxit);
+    L.sn = o;   o = up(o + sizeof(double2) * (size_t)nrhs * maxit);
+    L.g = o;    o = up(o + sizeof(double2) * (size_t)nrhs * (maxit + 1));
+    L.beta = o; o = up(o + sizeof(double) * nrhs);
+    L.live = o; o = up(o + sizeof(int) * nrhs);
+    L.kd = o;   o = up(o + sizeof(int) * nrhs);
+    L.total = o;
+    return L;
+}
+
+template <typename Z, typename R>
+__global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ __align__(16) unsigned char sraw[];
+    const int nrhs = a.nrhs, maxit = a.maxit, E = a.E, nc = a.nc;
+    const CoarseSmem LY = coarse_smem<Z>(nrhs, maxit, E, a.a_smem ? a.sps : 0, a.a_smem ? nc : 0);
+    Z* As = reinterpret_cast<Z*>(sraw + LY.As);          // [sps][9][col][row] stencil blocks of my sites
+    Z* xn = reinterpret_cast<Z*>(sraw + LY.xn);          // [nrhs][sps][9][nc] neighbour vectors
+    Z* Vs = reinterpret_cast<Z*>(sraw + LY.Vs);          // [(maxit+1)][nrhs][E]
+    Z* ws = reinterpret_cast<Z*>(sraw + LY.ws);          // [nrhs][E]
+    double2* hc = reinterpret_cast<double2*>(sraw + LY.hc);   // coefficients of the current pass
+    double2* h1s = reinterpret_cast<double2*>(sraw + LY.h1);  // pass-1 coefficients, kept for the Hessenberg column
+    double2* hcol = reinterpret_cast<double2*>(sraw + LY.hcol);   // [nrhs][maxit+1] column under rotation
+    double* cs = reinterpret_cast<double*>(sraw + LY.cs);
+    double2* sn = reinterpret_cast<double2*>(sraw + LY.sn);
+    double2* g = reinterpret_cast<double2*>(sraw + LY.g);
+    double* beta = reinterpret_cast<double*>(sraw + LY.beta);
+    int* live = reinterpret_cast<int*>(sraw + LY.live);
+    int* kd = reinterpret_cast<int*>(sraw + LY.kd);
+
+    const size_t nco = (size_t)a.gc.V * a.nc;
+    const size_t lo = (size_t)blockIdx.x * E;
+    const int len = lo >= nco ? 0 : (int)min((size_t)E, nco - lo);
+    const int s0 = blockIdx.x * a.sps;
+    const int nsl = len / nc;                               // sites owned by this CTA
+    if (a.a_smem) {
+        const Z* src = a.A + (size_t)s0 * 9 * nc * nc;
+        for (size_t t = threadIdx.x; t < (size_t)nsl * 9 * nc * nc; t += blockDim.x) As[t] = src[t];
+    }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int npair = (maxit + 2) * nrhs;
+    auto TOT = [&](int parity, int pass) { return a.tot + ((size_t)parity * 2 + pass) * npair; };
+    auto VS = [&](int i, int j) { return Vs + ((size_t)i * nrhs + j) * E; };
+
+    // partial inner products of this chunk: <Vs_i[j], ws[j]> for i < ni (+ ||ws_j||^2), added to `tot`
+    auto dots = [&](double2* tot, int ni, bool with_norm, const Z* Y) {
+        const int np = ni * nrhs + (with_norm ? nrhs : 0);
+        for (int p = warp; p < np; p += nw) {
+            int j;
+            const Z* xa;
+            if (p < ni * nrhs) { j = p % nrhs; xa = VS(p / nrhs, j); }
+            else { j = p - ni * nrhs; xa = Y + (size_t)j * E; }
+            if (!live[j]) continue;
+            const Z* ya = Y + (size_t)j * E;
+            double re = 0, im = 0;
+            for (int e = lane; e < len; e += 32) {
+                Z u = xa[e], v = ya[e];
+                re += (double)u.x * v.x + (double)u.y * v.y;
+                im += (double)u.x * v.y - (double)u.y * v.x;
+            }
+            re = warp_sum(re);
+            im = warp_sum(im);
+            const int slot = p < ni * nrhs ? p : (maxit + 1) * nrhs + j;
+            if (lane == 0 && len > 0) {
+                atomicAdd(&tot[slot].x, re);
+                atomicAdd(&tot[slot].y, im);
+            }
+        }
+    };
+    // ws[j] -= sum_i hc[i][j] Vs_i[j]
+    auto project = [&](int ni) {
+        for (int t = tid; t < nrhs * len; t += blockDim.x) {
+            const int j = t / len, e = t % len;
+            if (!live[j]) continue;
+            Z acc = ws[(size_t)j * E + e];
+            for (int i = 0; i < ni; ++i) {
+                double2 h = hc[i * nrhs + j];
+                Z v = VS(i, j)[e];
+                acc.x -= (R)(h.x * v.x - h.y * v.y);
+                acc.y -= (R)(h.x * v.y + h.y * v.x);
+            }
+            ws[(size_t)j * E + e] = acc;
+        }
+    };
+
+    // ---- load b, beta = ||b||
+    for (int j = tid; j < nrhs; j += blockDim.x) live[j] = (a.act == nullptr || a.act[j]) ? 1 : 0;
+    for (int t = tid; t < nrhs * len; t += blockDim.x) {
+        const int j = t / len, e = t % len;
+        ws[(size_t)j * E + e] = a.b[(size_t)j * nco + lo + e];
+    }
+    __syncthreads();
+    dots(TOT(1, 1), 0, true, ws);           // parity 1 pass 1 region: unused by iteration 0
+    grid.sync();
+    for (int j = tid; j < nrhs; j += blockDim.x) {
+        const double bb = live[j] ? sqrt(fmax(TOT(1, 1)[(maxit + 1) * nrhs + j].x, 0.0)) : 0.0;
+        beta[j] = bb;
+        if (!(bb > 0)) live[j] = 0;
+        kd[j] = 0;
+        g[(size_t)j * (maxit + 1)] = make_double2(bb, 0);
+    }
+    __syncthreads();
+    for (int t = tid; t < nrhs * len; t += blockDim.x) {
+        const int j = t / len, e = t % len;
+        const R ib = live[j] ? (R)(1.0 / beta[j]) : R(0);
+        Z v = ws[(size_t)j * E + e];
+        v.x *= ib; v.y *= ib;
+        VS(0, j)[e] = v;
+        a.Vg[(size_t)j * nco + lo + e] = v;
+    }
+    int it = 0;
+    for (; it < maxit; ++it) {
+        int any = 0;
+        for (int j = 0; j < nrhs; ++j) any |= live[j];
+        if (!any) break;
+        const int par = it & 1;
+        grid.sync();
+        // zero the other parity's totals: every CTA has passed the barrier, so
+        // nobody still reads them (they held the previous iteration's sums, or
+        // beta in iteration 0), and the next atomics into them follow the
+        // next barrier
+        if (blockIdx.x == 0)
+            for (int t = tid; t < 2 * npair; t += blockDim.x) a.tot[(size_t)(par ^ 1) * 2 * npair + t] = make_double2(0, 0);
+        // w = A v_it on this chunk
+        const Z* Vit = a.Vg + (size_t)par * nrhs * nco;
+        if (a.a_smem) {
+            // gather the 9 neighbour blocks of every owned site, then multiply from shared memory
+            for (int t = tid; t < nrhs * nsl * 9 * nc; t += blockDim.x) {
+                const int col = t % nc, d = (t / nc) % 9, sl = (t / (9 * nc)) % nsl, j = t / (9 * nc * nsl);
+                if (!live[j]) continue;
+                int c[4];
+                site_coords(a.gc, s0 + sl, c);
+                int sn = s0 + sl;
+                if (d > 0) {
+                    int mu = (d - 1) & 3, step = d <= 4 ? 1 : -1;
+                    c[mu] = (c[mu] + step + a.gc.L[mu]) % a.gc.L[mu];
+                    sn = site_index(a.gc, c);
+                }
+                xn[(((size_t)j * nsl + sl) * 9 + d) * nc + col] = Vit[(size_t)j * nco + (size_t)sn * nc + col];
+            }
+            __syncthreads();
+            for (int t = tid; t < nrhs * len; t += blockDim.x) {
+                const int j = t / len, e = t % len;
+                if (!live[j]) continue;
+                const int sl = e / nc, r = e % nc;
+                const Z* am = As + (size_t)sl * 9 * nc * nc + r;
+                const Z* xs = xn + ((size_t)j * nsl + sl) * 9 * nc;
+                Z acc; acc.x = 0; acc.y = 0;
+                for (int dc = 0; dc < 9 * nc; ++dc) acc += am[(size_t)dc * nc] * xs[dc];
+                const R sg = r < nc / 2 ? R(1) : R(-1);
+                const R tj = (R)a.tau[j];
+                const Z xv = xs[r];      // direction 0 is the site itself
+                if (a.op == QCD_OP_D) { acc -= (tj * sg) * xv; }
+                else { acc = sg * acc; acc -= tj * xv; }
+                ws[(size_t)j * E + e] = acc;
+            }
+        } else {
+            for (int t = tid; t < nrhs * len; t += blockDim.x) {
+                const int j = t / len, e = t % len;
+                if (!live[j]) continue;
+                const size_t ge = lo + e;
+                const int s = (int)(ge / a.nc), r = (int)(ge % a.nc);
+                int c[4];
+                site_coords(a.gc, s, c);
+                Z out;
+                coarse_row<Z, R>(a, Vit + (size_t)j * nco, s, r, c, (R)a.tau[j], out);
+                ws[(size_t)j * E + e] = out;
+            }
+        }
+        __syncthreads();
+        // classical Gram-Schmidt, pass 1
+        dots(TOT(par, 0), it + 1, false, ws);
+        grid.sync();
+        for (int t = tid; t < (it + 1) * nrhs; t += blockDim.x) hc[t] = h1s[t] = TOT(par, 0)[t];
+        __syncthreads();
+        project(it + 1);
+        __syncthreads();
+        // pass 2 and ||w||^2 before its update
+        dots(TOT(par, 1), it + 1, true, ws);
+        grid.sync();
+        for (int t = tid; t < (it + 1) * nrhs; t += blockDim.x) hc[t] = TOT(par, 1)[t];
+        for (int t = tid; t < nrhs; t += blockDim.x) hc[(maxit + 1) * nrhs + t] = TOT(par, 1)[(maxit + 1) * nrhs + t];
+        __syncthreads();
+        project(it + 1);
+        if (tid < nrhs) {
+            const int j = tid;
+            if (live[j]) {
+                double2* h = hcol + (size_t)j * (maxit + 1);
+                double h2n = 0.0;
+                for (int i = 0; i <= it; ++i) {
+                    const double2 p2 = hc[i * nrhs + j];
+                    h[i] = h1s[i * nrhs + j] + p2;
+                    h2n += cabs2(p2);
+                }
+                const double hn = sqrt(fmax(hc[(maxit + 1) * nrhs + j].x - h2n, 0.0));
+                hc[(maxit + 1) * nrhs + j] = make_double2(hn, 0.0);
+                const double res = givens_column(h, hn, cs + (size_t)j * maxit, sn + (size_t)j * maxit,
+                                                 g + (size_t)j * (maxit + 1), it);
+                if (blockIdx.x == 0) {
+                    for (int i = 0; i <= it; ++i) a.Rg[((size_t)j * maxit + i) * maxit + it] = h[i];
+                    a.resid[j] = beta[j] > 0 ? res / beta[j] : 0.0;
+                }
+                kd[j] = it + 1;
+                if (res <= a.tol * beta[j]) live[j] = -1;   // converged: finish this step, then stop
+            }
+        }
+        __syncthreads();
+        // v_{it+1} = w / hn
+        for (int t = tid; t < nrhs * len; t += blockDim.x) {
+            const int j = t / len, e = t % len;
+            if (kd[j] != it + 1) continue;
+            const double hn = hc[(maxit + 1) * nrhs + j].x;
+            const R ih = hn > 0 ? (R)(1.0 / hn) : R(0);
+            Z v = ws[(size_t)j * E + e];
+            v.x *= ih; v.y *= ih;
+            VS(it + 1, j)[e] = v;
+            a.Vg[((size_t)(par ^ 1) * nrhs + j) * nco + lo + e] = v;
+        }
+        __syncthreads();
+        for (int j = tid; j < nrhs; j += blockDim.x) if (live[j] < 0) live[j] = 0;
+        __syncthreads();
+    }
+    // triangular solve (CTA 0) and x = V y
+    if (blockIdx.x == 0 && tid < nrhs) {
+        const int j = tid, k = kd[j];
+        const double2* Rj = a.Rg + (size_t)j * maxit * maxit;
+        const double2* gj = g + (size_t)j * (maxit + 1);
+        double2* y = a.yv + (size_t)j * maxit;
+        for (int i = k - 1; i >= 0; --i) {
+            double2 sacc = gj[i];
+            for (int l = i + 1; l < k; ++l) sacc -= Rj[(size_t)i * maxit + l] * y[l];
+            double2 d = Rj[(size_t)i * maxit + i];
+            double den = cabs2(d);
+            y[i] = den > 0 ? (1.0 / den) * cmulc(d, sacc) : make_double2(0, 0);
+        }
+        a.iters[j] = k;
+        if (a.counter != nullptr && (a.act == nullptr || a.act[j])) {
+            atomicAdd(a.counter, 1ull);
+            atomicAdd(a.counter + 1, (unsigned long long)k);
+        }
+    }
+    grid.sync();
+    for (int t = tid; t < nrhs * len; t += blockDim.x) {
+        const int j = t / len, e = t % len;
+        if (a.act != nullptr && !a.act[j]) continue;
+        const int k = kd[j];
+        const double2* y = a.yv + (size_t)j * maxit;
+        double re = 0, im = 0;
+        for (int i = 0; i < k; ++i) {
+            Z v = VS(i, j)[e];
+            re += y[i].x * v.x - y[i].y * v.y;
+            im += y[i].x * v.y + y[i].y * v.x;
+        }
+        Z o; o.x = (R)re; o.y = (R)im;
+        a.x[(size_t)j * nco + lo + e] = o;
+    }
+}
+
+}  // namespace
+
+size_t kry_bytes(int nrhs, int maxit) {
+    return sizeof(double) * nrhs * 2 + sizeof(int) * nrhs * 2 + sizeof(double) * (size_t)nrhs * maxit +
+           sizeof(double2) * ((size_t)nrhs * maxit + (size_t)nrhs * (maxit + 1) + (size_t)nrhs * maxit * maxit +
+                              (size_t)maxit * nrhs + nrhs) + 256;
+}
+
+KryDev kry_layout(void* buf, int nrhs, int maxit, double tol) {
+    KryDev K;
+    K.nrhs = nrhs;
+    K.maxit = maxit;
+    K.tol = tol;
+    char* p = (char*)buf;
+    auto take = [&](size_t bytes) { char* q = p; p += (bytes + 15) & ~size_t(15); return (void*)q; };
+    K.g = (double2*)take(sizeof(double2) * (size_t)nrhs * (maxit + 1));
+    K.sn = (double2*)take(sizeof(double2) * (size_t)nrhs * maxit);
+    K.R = (double2*)take(sizeof(double2) * (size_t)nrhs * maxit * maxit);
+    K.coef = (double2*)take(sizeof(double2) * (size_t)maxit * nrhs);
+    K.scale = (double2*)take(sizeof(double2) * nrhs);
+    K.cs = (double*)take(sizeof(double) * (size_t)nrhs * maxit);
+    K.beta = (double*)take(sizeof(double) * nrhs);
+    K.resid = (double*)take(sizeof(double) * nrhs);
+    K.active = (int*)take(sizeof(int) * nrhs);
+    K.k = (int*)take(sizeof(int) * nrhs);
+    return K;
+}
+
+void kry_init(const KryDev& K, const double2* nrm, const int* outer_act, cudaStream_t st) {
+    KTimer kt("kry_init", 0.0, 0.0, st);
+    kry_init_kernel<<<1, 64, 0, st>>>(K, nrm, outer_act);
+}
+void kry_step(const KryDev& K, int it, const double2* h1, const double2* h2, const double2* nrm, cudaStream_t st) {
+    KTimer kt("kry_step", 0.0, 0.0, st);
+    kry_step_kernel<<<1, 64, 0, st>>>(K, it, h1, h2, nrm);
+}
+void kry_finish(const KryDev& K, cudaStream_t st) {
+    KTimer kt("kry_finish", 0.0, 0.0, st);
+    kry_finish_kernel<<<1, 64, 0, st>>>(K);
+}
+
+size_t coarse_gmres_scratch(const Coarse& c, int prec, int nrhs, int maxit, int nct) {
+    const size_t nco = (size_t)c.gc.V * c.nc;
+    const size_t es = prec == QCD_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t npair = (size_t)(maxit + 2) * nrhs;
+    (void)nct;
+    return es * nco * nrhs * 2 + sizeof(double2) * (4 * npair + (size_t)nrhs * maxit * maxit + (size_t)nrhs * maxit) +
+           4096;
+}
+
+int coarse_gmres_grid() {
+    static int nct = 0;
+    if (nct == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        nct = sms > 0 ? sms : 1;
+    }
+    return nct;
+}
+
+// Site-based partition: each CTA owns `sps` consecutive coarse sites.
+static void coarse_partition(const Coarse& c, int& sps, int& nblk) {
+    const int nct = coarse_gmres_grid();
+    sps = (c.gc.V + nct - 1) / nct;
+    nblk = (c.gc.V + sps - 1) / sps;
+}
+constexpr size_t kCoarseSmemCap = 200 * 1024;
+
+// Largest right-hand-side group whose basis chunks fit in shared memory.
+int coarse_gmres_group(const Coarse& c, int prec, int maxit) {
+    int sps, nblk;
+    coarse_partition(c, sps, nblk);
+    const int E = sps * c.nc;
+    int best = 0;
+    for (int g = 1; g <= kMaxCoarseRhs; ++g) {
+        size_t sm = prec == QCD_FP64 ? coarse_smem<double2>(g, maxit, E).total : coarse_smem<float2>(g, maxit, E).total;
+        if (sm <= kCoarseSmemCap) best = g;
+    }
+    return best;
+}
+
+template <typename Z, typename R>
+static int launch_coarse(const Coarse& c, int op, int nrhs, const void* b, void* x, const double* tau_dev,
+                         const int* act, double tol, int maxit, void* scratch, int* iters, double* resid,
+                         unsigned long long* counter, cudaStream_t st) {
+    const size_t nco = (size_t)c.gc.V * c.nc;
+    int sps, nblk;
+    coarse_partition(c, sps, nblk);
+    const int E = sps * c.nc;
+    CoarseSmem LY = coarse_smem<Z>(nrhs, maxit, E, sps, c.nc);
+    int a_smem = 1;
+    if (LY.total > kCoarseSmemCap) {
+        a_smem = 0;
+        LY = coarse_smem<Z>(nrhs, maxit, E);
+    }
+    if (LY.total > kCoarseSmemCap) return -4;
+    const size_t npair = (size_t)(maxit + 2) * nrhs;
+    char* p = (char*)scratch;
+    auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return (void*)q; };
+    CoarseArgs<Z, R> a;
+    a.gc = c.gc;
+    a.nc = c.nc;
+    a.A = std::is_same<R, double>::value ? (const Z*)c.A64 : (const Z*)c.A32;
+    a.b = (const Z*)b;
+    a.x = (Z*)x;
+    a.Vg = (Z*)take(sizeof(Z) * nco * nrhs * 2);
+    a.tot = (double2*)take(sizeof(double2) * 4 * npair);
+    a.Rg = (double2*)take(sizeof(double2) * (size_t)nrhs * maxit * maxit);
+    a.yv = (double2*)take(sizeof(double2) * (size_t)nrhs * maxit);
+    a.iters = iters;
+    a.counter = counter;
+    a.resid = resid;
+    a.op = op;
+    a.tau = tau_dev;
+    a.act = act;
+    a.tol = tol;
+    a.maxit = maxit;
+    a.nrhs = nrhs;
+    a.E = E;
+    a.sps = sps;
+    a.a_smem = a_smem;
+    cudaMemsetAsync(a.tot, 0, sizeof(double2) * 4 * npair, st);
+    auto kern = coarse_gmres_kernel<Z, R>;
+    const size_t sm = LY.total;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
+    if (per_sm < 1) return -1;
+    void* args[] = {&a};
+    const double es = sizeof(Z);
+    KTimer kt(std::is_same<R, double>::value ? "coarse_gmres_f64" : "coarse_gmres_f32",
+              es * ((double)c.gc.V * 9 * c.nc * c.nc + 4.0 * nrhs * nco), 0.0, st);
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)kern, dim3(nblk), dim3(256), args, sm, st);
+    (void)E;
+    return e == cudaSuccess ? 0 : -2;
+}
+
+int coarse_gmres(const Coarse& c, int prec, int op, int nrhs, const void* b, void* x, const double* tau_dev,
+                 const int* act, double tol, int maxit, void* scratch, int* iters, double* resid,
+                 unsigned long long* counter, cudaStream_t st) {
+    if (nrhs < 1 || nrhs > kMaxCoarseRhs || maxit < 1 || maxit > kMaxCoarse) return -3;
+    if (prec == QCD_FP64)
+        return launch_coarse<double2, double>(c, op, nrhs, b, x, tau_dev, act, tol, maxit, scratch, iters, resid,
+                                              counter, st);
+    return launch_coarse<float2, float>(c, op, nrhs, b, x, tau_dev, act, tol, maxit, scratch, iters, resid, counter,
+                                        st);
+}
+
+}  // namespace qcd

@@ -83,13 +83,14 @@ __global__ void build_P_kernel(Geom g, Blocking B, int nv, const double2* __rest
 // ------------------------------------------------------------------ restrict / prolong
 template <typename Z, typename R>
 __global__ void restrict_kernel(Geom g, Blocking B, int nv, const Z* __restrict__ P, const Z* __restrict__ r,
-                                Z* __restrict__ xc, int nrhs) {
+                                Z* __restrict__ xc, int nrhs, const int* __restrict__ act) {
     const int nc = 2 * nv;
     const int nloc = B.bs * 6;
     const long total = (long)B.nb * nc * nrhs;
     const int lane = threadIdx.x & 31;
     for (long w = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; w < total; w += ((long)gridDim.x * blockDim.x) >> 5) {
         const int j = (int)(w / ((long)B.nb * nc));
+        if (act != nullptr && !act[j]) continue;
         const int rem = (int)(w - (long)j * B.nb * nc);
         const int blk = rem / nc, ci = rem % nc;
         const int chi = ci / nv, i = ci % nv;
@@ -111,12 +112,13 @@ __global__ void restrict_kernel(Geom g, Blocking B, int nv, const Z* __restrict_
 
 template <typename Z>
 __global__ void prolong_kernel(Geom g, Blocking B, int nv, const Z* __restrict__ P, const Z* __restrict__ xc,
-                               Z* __restrict__ x, int nrhs, bool accumulate) {
+                               Z* __restrict__ x, int nrhs, bool accumulate, const int* __restrict__ act) {
     const int nc = 2 * nv;
     const int nloc = B.bs * 6;
     const size_t total = (size_t)nrhs * B.nb * 2 * nloc;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(t / ((size_t)B.nb * 2 * nloc));
+        if (act != nullptr && !act[j]) continue;
         size_t rem = t - (size_t)j * B.nb * 2 * nloc;
         const int blk = (int)(rem / (2 * nloc));
         const int chi = (int)((rem / nloc) % 2);
@@ -322,7 +324,8 @@ __device__ __forceinline__ void block_op(const Geom& g, const Blocking& B, const
 template <typename R>
 __global__ void sap_block_kernel(Geom g, Blocking B, const cplx<R>* __restrict__ U, const R* __restrict__ A,
                                  const int* __restrict__ blocks, int op, Shifts tau, const cplx<R>* __restrict__ r,
-                                 cplx<R>* __restrict__ x, int iters, double tol, cplx<R>* __restrict__ scratch) {
+                                 cplx<R>* __restrict__ x, int iters, double tol, cplx<R>* __restrict__ scratch,
+                                 const int* __restrict__ act) {
     extern __shared__ double2 sm[];
     const int bs = B.bs;
     cplx<R>* vsm = reinterpret_cast<cplx<R>*>(sm);                       // [bs][12]
@@ -335,6 +338,7 @@ __global__ void sap_block_kernel(Geom g, Blocking B, const cplx<R>* __restrict__
     int* flag = reinterpret_cast<int*>(cs + iters);     // [4]
 
     const int j = blockIdx.y;
+    if (act != nullptr && !act[j]) return;
     const int blk = blocks[blockIdx.x];
     const int l = threadIdx.x;
     const size_t fstride = (size_t)g.V * 12;
@@ -443,6 +447,231 @@ __global__ void sap_block_kernel(Geom g, Blocking B, const cplx<R>* __restrict__
     store_spinor<R>(x + (size_t)y * 12, e);
 }
 
+// ------------------------------------------------------------------ SAP, small blocks
+// Blocks of BS <= 32 sites: each SAP block is a BS-lane segment of one warp
+// (32 / BS blocks per CTA of one warp).  The block's links and clover and the
+// whole Krylov basis live in shared memory; inner products are reduced with
+// xor-shuffles inside the segment; Arnoldi by modified Gram-Schmidt, as in the
+// 256-site path.  Only __syncwarp() orders shared-memory traffic.
+struct SapSmemLayout {
+    size_t basis, links, clover, H, g, sn, y, cs, flag, total;
+};
+template <typename R>
+__host__ __device__ inline SapSmemLayout sap_layout(int BS, int iters) {
+    auto up = [](size_t v) { return (v + 15) & ~size_t(15); };
+    SapSmemLayout L;
+    size_t o = 0;
+    L.basis = o;  o = up(o + (size_t)(iters + 1) * BS * 12 * sizeof(cplx<R>));
+    L.links = o;  o = up(o + (size_t)BS * 36 * sizeof(cplx<R>));
+    L.clover = o; o = up(o + (size_t)BS * 72 * sizeof(R));
+    L.H = o;      o = up(o + (size_t)(iters + 1) * iters * sizeof(double2));
+    L.g = o;      o = up(o + (size_t)(iters + 1) * sizeof(double2));
+    L.sn = o;     o = up(o + (size_t)iters * sizeof(double2));
+    L.y = o;      o = up(o + (size_t)iters * sizeof(double2));
+    L.cs = o;     o = up(o + (size_t)iters * sizeof(double));
+    L.flag = o;   o = up(o + 4 * sizeof(int));
+    L.total = o;
+    return L;
+}
+
+template <int BS>
+__device__ __forceinline__ double seg_sum(double v) {
+#pragma unroll
+    for (int o = BS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R, int BS>
+__global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const cplx<R>* __restrict__ U,
+                                                      const R* __restrict__ A, const int* __restrict__ blocks, int ncol,
+                                                      int op, Shifts tau, const cplx<R>* __restrict__ r,
+                                                      cplx<R>* __restrict__ x, int iters, double tol,
+                                                      const int* __restrict__ act) {
+    constexpr int SPW = 32 / BS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x;
+    const int seg = lane / BS, l = lane % BS;
+    const SapSmemLayout LY = sap_layout<R>(BS, iters);
+    unsigned char* base = smraw + (size_t)seg * LY.total;
+    cplx<R>* basis = reinterpret_cast<cplx<R>*>(base + LY.basis);
+    cplx<R>* slink = reinterpret_cast<cplx<R>*>(base + LY.links);
+    R* sclov = reinterpret_cast<R*>(base + LY.clover);
+    double2* H = reinterpret_cast<double2*>(base + LY.H);
+    double2* gv = reinterpret_cast<double2*>(base + LY.g);
+    double2* sn = reinterpret_cast<double2*>(base + LY.sn);
+    double2* yv = reinterpret_cast<double2*>(base + LY.y);
+    double* cs = reinterpret_cast<double*>(base + LY.cs);
+    int* flag = reinterpret_cast<int*>(base + LY.flag);
+
+    const int j = blockIdx.y;
+    if (act != nullptr && !act[j]) return;
+    const int bidx = blockIdx.x * SPW + seg;
+    const bool valid = bidx < ncol;
+    const int blk = valid ? blocks[bidx] : blocks[0];
+    const size_t fstride = (size_t)g.V * 12;
+    r += j * fstride;
+    x += j * fstride;
+    const R t = (R)tau.t[j];
+    int o[4];
+    {
+        int tt = l;
+        o[3] = tt % B.b[3]; tt /= B.b[3];
+        o[2] = tt % B.b[2]; tt /= B.b[2];
+        o[1] = tt % B.b[1]; o[0] = tt / B.b[1];
+    }
+    const int y = block_fine_site(g, B, blk, l);
+    // stage links (forward, this site) and clover
+#pragma unroll
+    for (int k = 0; k < 36; ++k) slink[l * 36 + k] = __ldg(U + (size_t)y * 36 + k);
+#pragma unroll 8
+    for (int k = 0; k < 72; ++k) sclov[l * 72 + k] = __ldg(A + (size_t)y * 72 + k);
+    Spinor<R> w;
+    load_spinor<R>(r + (size_t)y * 12, w);
+    double nn = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) nn += (double)w.c[k].x * w.c[k].x + (double)w.c[k].y * w.c[k].y;
+    nn = seg_sum<BS>(nn);
+    const double beta = valid ? sqrt(nn) : 0.0;
+    {
+        const R ib = beta > 0 ? (R)(1.0 / beta) : R(0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) basis[l * 12 + k] = ib * w.c[k];
+    }
+    if (l == 0) { gv[0] = make_double2(beta, 0); flag[0] = beta > 0 ? 0 : 1; flag[1] = 0; }
+    __syncwarp();
+    int lstride[4];
+    lstride[3] = 1;
+    lstride[2] = B.b[3];
+    lstride[1] = B.b[3] * B.b[2];
+    lstride[0] = B.b[3] * B.b[2] * B.b[1];
+    for (int jj = 0; jj < iters; ++jj) {
+        const bool active = flag[0] == 0;
+        if (__all_sync(0xffffffffu, !active)) break;
+        const cplx<R>* vj = basis + (size_t)jj * BS * 12;
+        // w = A_block v_j
+        Spinor<R> psi, acc;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) psi.c[k] = vj[l * 12 + k];
+        clover_apply_smem<R>(sclov + l * 72, psi, acc);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            Spinor<R> nb;
+            Link<R> u;
+            if (o[mu] < B.b[mu] - 1) {
+                const int ln = l + lstride[mu];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) nb.c[k] = vj[ln * 12 + k];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) u.e[k] = slink[l * 36 + mu * 9 + k];
+                switch (mu) {
+                    case 0: hop_accumulate<R, 0, true>(nb, u, R(1), acc); break;
+                    case 1: hop_accumulate<R, 1, true>(nb, u, R(1), acc); break;
+                    case 2: hop_accumulate<R, 2, true>(nb, u, R(1), acc); break;
+                    default: hop_accumulate<R, 3, true>(nb, u, R(1), acc); break;
+                }
+            }
+            if (o[mu] > 0) {
+                const int ln = l - lstride[mu];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) nb.c[k] = vj[ln * 12 + k];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) u.e[k] = slink[ln * 36 + mu * 9 + k];
+                switch (mu) {
+                    case 0: hop_accumulate<R, 0, false>(nb, u, R(1), acc); break;
+                    case 1: hop_accumulate<R, 1, false>(nb, u, R(1), acc); break;
+                    case 2: hop_accumulate<R, 2, false>(nb, u, R(1), acc); break;
+                    default: hop_accumulate<R, 3, false>(nb, u, R(1), acc); break;
+                }
+            }
+        }
+        if (op == QCD_OP_D) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc.c[k] -= t * psi.c[k];
+#pragma unroll
+            for (int k = 6; k < 12; ++k) acc.c[k] += t * psi.c[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc.c[k] -= t * psi.c[k];
+#pragma unroll
+            for (int k = 6; k < 12; ++k) acc.c[k] = -acc.c[k] - t * psi.c[k];
+        }
+        // modified Gram-Schmidt against v_0 .. v_jj
+        for (int i = 0; i <= jj; ++i) {
+            const cplx<R>* vi = basis + (size_t)i * BS * 12 + l * 12;
+            double hr = 0.0, hi = 0.0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                cplx<R> a = vi[k];
+                hr += (double)a.x * acc.c[k].x + (double)a.y * acc.c[k].y;
+                hi += (double)a.x * acc.c[k].y - (double)a.y * acc.c[k].x;
+            }
+            hr = seg_sum<BS>(hr);
+            hi = seg_sum<BS>(hi);
+            const cplx<R> h = mk<R>((R)hr, (R)hi);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc.c[k] -= h * vi[k];
+            if (l == 0 && active) H[i * iters + jj] = make_double2(hr, hi);
+        }
+        double hn2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) hn2 += (double)acc.c[k].x * acc.c[k].x + (double)acc.c[k].y * acc.c[k].y;
+        hn2 = seg_sum<BS>(hn2);
+        const double hn = sqrt(hn2);
+        {
+            const R ih = hn > 0 ? (R)(1.0 / hn) : R(0);
+            cplx<R>* vn = basis + (size_t)(jj + 1) * BS * 12 + l * 12;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) vn[k] = ih * acc.c[k];
+        }
+        if (l == 0 && active) {
+            H[(jj + 1) * iters + jj] = make_double2(hn, 0);
+            for (int i = 0; i < jj; ++i) {
+                double2 a = H[i * iters + jj], c = H[(i + 1) * iters + jj];
+                H[i * iters + jj] = cs[i] * a + sn[i] * c;
+                H[(i + 1) * iters + jj] = cs[i] * c - conj(sn[i]) * a;
+            }
+            double2 a = H[jj * iters + jj];
+            double2 c = H[(jj + 1) * iters + jj];
+            double aa = sqrt(a.x * a.x + a.y * a.y), rr = sqrt(aa * aa + c.x * c.x + c.y * c.y);
+            if (aa > 0) {
+                cs[jj] = aa / rr;
+                sn[jj] = (1.0 / rr) * ((1.0 / aa) * a * conj(c));
+            } else {
+                cs[jj] = 0.0;
+                sn[jj] = make_double2(1, 0);
+            }
+            H[jj * iters + jj] = cs[jj] * a + sn[jj] * c;
+            gv[jj + 1] = -1.0 * (conj(sn[jj]) * gv[jj]);
+            gv[jj] = cs[jj] * gv[jj];
+            const double res = sqrt(gv[jj + 1].x * gv[jj + 1].x + gv[jj + 1].y * gv[jj + 1].y);
+            flag[1] = jj + 1;
+            if (tol >= 0.0 && res <= tol * beta) flag[0] = 1;
+        }
+        __syncwarp();
+    }
+    const int kdim = flag[1];
+    if (l == 0) {
+        for (int i = kdim - 1; i >= 0; --i) {
+            double2 sacc = gv[i];
+            for (int k = i + 1; k < kdim; ++k) sacc -= H[i * iters + k] * yv[k];
+            double2 dd = H[i * iters + i];
+            double den = dd.x * dd.x + dd.y * dd.y;
+            yv[i] = den > 0 ? (1.0 / den) * cmulc(dd, sacc) : make_double2(0, 0);
+        }
+    }
+    __syncwarp();
+    if (!valid || kdim == 0) return;
+    Spinor<R> e;
+    load_spinor<R>(x + (size_t)y * 12, e);
+    for (int i = 0; i < kdim; ++i) {
+        const cplx<R> yi = mk<R>((R)yv[i].x, (R)yv[i].y);
+        const cplx<R>* vi = basis + (size_t)i * BS * 12 + l * 12;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) e.c[k] += yi * vi[k];
+    }
+    store_spinor<R>(x + (size_t)y * 12, e);
+}
+
 inline int grid_for(size_t n, int th = 256) {
     size_t gsz = (n + th - 1) / th;
     return (int)(gsz > 1048576 ? 1048576 : (gsz == 0 ? 1 : gsz));
@@ -468,7 +697,8 @@ void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st) {
     narrow_kernel<<<grid_for(n), 256, 0, st>>>(c.A64, c.A32, n);
 }
 
-void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st) {
+void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st,
+                 const int* act) {
     size_t warps = (size_t)c.B.nb * c.nc * nrhs;
     int grid = grid_for(warps * 32);
     const double es = prec == QCD_FP64 ? 16.0 : 8.0;
@@ -476,13 +706,13 @@ void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const voi
     KTimer kt(prec == QCD_FP64 ? "restrict_f64" : "restrict_f32",
               es * (nfine * c.nv + nrhs * (nfine + (double)c.gc.V * c.nc)), 8.0 * nfine * c.nv * nrhs, st);
     if (prec == QCD_FP64)
-        restrict_kernel<double2, double><<<grid, 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)r, (double2*)xc, nrhs);
+        restrict_kernel<double2, double><<<grid, 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)r, (double2*)xc, nrhs, act);
     else
-        restrict_kernel<float2, float><<<grid, 256, 0, st>>>(f.g, c.B, c.nv, c.P32, (const float2*)r, (float2*)xc, nrhs);
+        restrict_kernel<float2, float><<<grid, 256, 0, st>>>(f.g, c.B, c.nv, c.P32, (const float2*)r, (float2*)xc, nrhs, act);
 }
 
 void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* xc, void* x, bool accumulate,
-                cudaStream_t st) {
+                cudaStream_t st, const int* act) {
     size_t n = (size_t)nrhs * c.B.nb * 2 * c.B.bs * 6;
     const double es = prec == QCD_FP64 ? 16.0 : 8.0;
     const double nfine = (double)f.g.V * 12;
@@ -491,10 +721,10 @@ void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void
               8.0 * nfine * c.nv * nrhs, st);
     if (prec == QCD_FP64)
         prolong_kernel<double2><<<grid_for(n), 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)xc, (double2*)x, nrhs,
-                                                             accumulate);
+                                                             accumulate, act);
     else
         prolong_kernel<float2><<<grid_for(n), 256, 0, st>>>(f.g, c.B, c.nv, c.P32, (const float2*)xc, (float2*)x, nrhs,
-                                                            accumulate);
+                                                            accumulate, act);
 }
 
 void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, void* y, const double* tau,
@@ -521,26 +751,54 @@ size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters) {
 }
 
 void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op, int nrhs, const void* r, void* x,
-                const double* tau, int iters, double tol, void* scratch, cudaStream_t st) {
+                const double* tau, int iters, double tol, void* scratch, cudaStream_t st, const int* act) {
     Shifts sh{};
     for (int j = 0; j < nrhs; ++j) sh.t[j] = tau ? tau[j] : 0.0;
-    dim3 grid(sp.ncol[colour], nrhs);
     const int bs = sp.B.bs;
-    size_t sm = sizeof(double2) * ((size_t)bs + (size_t)(iters + 1) * iters + (iters + 1) + 2 * iters) +
-                sizeof(double) * iters + 4 * sizeof(int) +
-                (size_t)bs * 12 * (prec == QCD_FP64 ? sizeof(double2) : sizeof(float2));
     const double rs = prec == QCD_FP64 ? 8.0 : 4.0;
     const double sites = (double)sp.ncol[colour] * bs;
     KTimer kt(prec == QCD_FP64 ? "sap_block_f64" : "sap_block_f32", rs * sites * (nrhs * 72.0 + 144.0),
               1824.0 * sites * nrhs * iters, st);
+    if (bs == 16 || bs == 32) {
+        const int spw = 32 / bs;
+        dim3 grid((sp.ncol[colour] + spw - 1) / spw, nrhs);
+        if (prec == QCD_FP64) {
+            size_t sm = sap_layout<double>(bs, iters).total * spw;
+            if (bs == 16) {
+                if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                sap_warp_kernel<double, 16><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
+                    sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
+            } else {
+                if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                sap_warp_kernel<double, 32><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
+                    sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
+            }
+        } else {
+            size_t sm = sap_layout<float>(bs, iters).total * spw;
+            if (bs == 16) {
+                if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                sap_warp_kernel<float, 16><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
+                    sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
+            } else {
+                if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                sap_warp_kernel<float, 32><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
+                    sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
+            }
+        }
+        return;
+    }
+    dim3 grid(sp.ncol[colour], nrhs);
+    size_t sm = sizeof(double2) * ((size_t)bs + (size_t)(iters + 1) * iters + (iters + 1) + 2 * iters) +
+                sizeof(double) * iters + 4 * sizeof(int) +
+                (size_t)bs * 12 * (prec == QCD_FP64 ? sizeof(double2) : sizeof(float2));
     if (prec == QCD_FP64) {
         if (sm > 48 * 1024) cudaFuncSetAttribute(sap_block_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         sap_block_kernel<double><<<grid, bs, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour], op, sh,
-                                                       (const double2*)r, (double2*)x, iters, tol, (double2*)scratch);
+                                                       (const double2*)r, (double2*)x, iters, tol, (double2*)scratch, act);
     } else {
         if (sm > 48 * 1024) cudaFuncSetAttribute(sap_block_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         sap_block_kernel<float><<<grid, bs, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour], op, sh,
-                                                      (const float2*)r, (float2*)x, iters, tol, (float2*)scratch);
+                                                      (const float2*)r, (float2*)x, iters, tol, (float2*)scratch, act);
     }
 }
 

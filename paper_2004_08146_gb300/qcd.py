@@ -62,7 +62,8 @@ class qcd_solve_info(ctypes.Structure):
 class qcd_eig_info(ctypes.Structure):
     _fields_ = [("outer", ctypes.c_int), ("inner", ctypes.c_int), ("locked", ctypes.c_int),
                 ("updates", ctypes.c_int), ("converged", ctypes.c_int),
-                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("coarse_solves", ctypes.c_longlong), ("coarse_iterations", ctypes.c_longlong)]
 
 
 class qcd_kernel_stat(ctypes.Structure):
