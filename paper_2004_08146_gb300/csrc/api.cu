@@ -136,6 +136,7 @@ void validate_params(const qcd_params& p) {
     if (p.m_min < 1 || p.m_max < p.m_min + 1 || p.m_max > 64)
         throw QcdError(QCD_EINVAL, "need 1 <= m_min < m_max <= 64");
     if (p.block < 1 || p.block > 16) throw QcdError(QCD_EINVAL, "block must be in [1, 16]");
+    if (p.m_max + p.block > 64) throw QcdError(QCD_EINVAL, "need m_max + block <= 64");
     if (p.nu < 0 || p.sap_block_iters < 1 || p.sap_block_iters > 32) throw QcdError(QCD_EINVAL, "bad smoother params");
     if (p.inner_maxiter < 1 || p.inner_maxiter > 64 || p.coarse_maxiter < 1 || p.coarse_maxiter > 200 ||
         p.plain_maxiter < 1 || p.plain_maxiter > 200)
@@ -706,7 +707,7 @@ struct GD {
         X = B("X", (size_t)kcap * n);
         G = B("G", (size_t)mcap * mcap); Hm = B("Hm", (size_t)mcap * mcap);
         Gt = B("Gt", (size_t)mcap * mcap); Hmt = B("Hmt", (size_t)mcap * mcap);
-        S = B("S", (size_t)mcap * mcap); work = B("work", (size_t)6 * mcap * mcap); C = B("C", (size_t)mcap * mcap);
+        S = B("S", (size_t)mcap * mcap); work = B("work", (size_t)(6 + block) * mcap * mcap); C = B("C", (size_t)mcap * mcap);
         dots = B("dots", (size_t)4 * (mcap + kcap + 8));
         part = B("part", (size_t)(mcap + kcap + 8) * 64);
         u = B("u", n); Qu = B("Qu", n); R = B("R", (size_t)block * n); T = B("T", (size_t)block * n); tmp = B("tmp", n);
@@ -857,6 +858,17 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                 if (cnt == 0) { finished = true; break; }
             }
             tg = select_targets(theta, block, allowed);
+            // FP64 refinement of the targeted pairs (the full decomposition is FP32)
+            {
+                std::vector<int> cols(tg.size());
+                for (size_t q = 0; q < tg.size(); ++q) cols[q] = col[tg[q]];
+                CK(cudaMemcpyAsync(gd.idx, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+                small_refine_targets(gd.G, gd.Hm, gd.m, gd.mcap, gd.S, gd.mu, gd.idx, (int)cols.size(), gd.work, st);
+                double* hm = (double*)ctx->host(gd.m);
+                CK(cudaMemcpyAsync(hm, gd.mu, gd.m * sizeof(double), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                for (size_t q = 0; q < tg.size(); ++q) theta[tg[q]] = hm[cols[q]] != 0.0 ? 1.0 / hm[cols[q]] : INFINITY;
+            }
             bool locked = false;
             tsel.clear();
             int nr = 0;

@@ -40,15 +40,18 @@ __global__ void multidot_partial_kernel(const Z* __restrict__ X, size_t xstride_
     const size_t chunk = (n + nsplit - 1) / nsplit;
     const size_t lo = (size_t)blockIdx.x * chunk;
     const size_t hi = lo + chunk < n ? lo + chunk : n;
-    double re = 0.0, im = 0.0;
+    // per-thread and per-warp sums in the vector precision (FP64 arithmetic
+    // is ~64x slower than FP32 on this part); the cross-warp sum in FP64
+    using Rt = decltype(Z{}.x);
+    Rt ret = 0, imt = 0;
     for (size_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
         Z a = x[k], b = y[k];
-        re += (double)a.x * b.x + (double)a.y * b.y;
-        im += (double)a.x * b.y - (double)a.y * b.x;
+        ret += a.x * b.x + a.y * b.y;
+        imt += a.x * b.y - a.y * b.x;
     }
     __shared__ double sre[32], sim[32];
-    re = warp_sum(re);
-    im = warp_sum(im);
+    double re = (double)warp_sum(ret);
+    double im = (double)warp_sum(imt);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) { sre[wid] = re; sim[wid] = im; }
     __syncthreads();
@@ -69,25 +72,36 @@ __global__ void multidot_final_kernel(const double2* __restrict__ partial, int n
     dots[v] = s;
 }
 
+constexpr int kAxpyCoef = 2048;   // coefficients staged per CTA (nvec * nrhs)
+
 template <typename Z, typename R>
 __global__ void multiaxpy_kernel(const Z* __restrict__ X, int nvec, size_t xstride_vec, const double2* __restrict__ c,
                                  double sign, Z* __restrict__ w, int nrhs, size_t n, const int* __restrict__ act) {
+    // coefficients converted once per CTA to the working precision (a
+    // conversion per element would run on the slow FP64 path)
+    __shared__ Z cs[kAxpyCoef];
+    const int nco = nvec * nrhs;
+    const bool staged = nco <= kAxpyCoef;
+    if (staged)
+        for (int e = threadIdx.x; e < nco; e += blockDim.x) { cs[e].x = (R)c[e].x; cs[e].y = (R)c[e].y; }
+    __syncthreads();
     const size_t total = n * nrhs;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(t / n);
         if (act != nullptr && !act[j]) continue;
         const size_t k = t - (size_t)j * n;
-        double2 acc = make_double2(0, 0);
+        Z acc; acc.x = 0; acc.y = 0;
         for (int i = 0; i < nvec; ++i) {
-            double2 ci = c[i * nrhs + j];
-            if (ci.x == 0.0 && ci.y == 0.0) continue;   // unused basis slots may hold stale data
-            Z xv = X[(size_t)i * xstride_vec + (size_t)j * n + k];
-            acc.x += ci.x * xv.x - ci.y * xv.y;
-            acc.y += ci.x * xv.y + ci.y * xv.x;
+            Z ci;
+            if (staged) ci = cs[i * nrhs + j];
+            else { ci.x = (R)c[i * nrhs + j].x; ci.y = (R)c[i * nrhs + j].y; }
+            if (ci.x == R(0) && ci.y == R(0)) continue;   // unused basis slots may hold stale data
+            acc += ci * X[(size_t)i * xstride_vec + (size_t)j * n + k];
         }
         Z o = w[t];
-        o.x = (R)(o.x + sign * acc.x);
-        o.y = (R)(o.y + sign * acc.y);
+        const R sg = (R)sign;
+        o.x += sg * acc.x;
+        o.y += sg * acc.y;
         w[t] = o;
     }
 }
@@ -101,10 +115,9 @@ __global__ void scale_dev_kernel(const Z* __restrict__ x, Z* __restrict__ y, con
         if (act != nullptr && !act[j]) continue;
         double2 a = alpha[j];
         if (invert_real) a = make_double2(a.x != 0.0 ? 1.0 / a.x : 0.0, 0.0);
-        Z xv = x[t];
-        double re = a.x * xv.x - a.y * xv.y, im = a.x * xv.y + a.y * xv.x;
-        if (accumulate) { re += y[t].x; im += y[t].y; }
-        Z o; o.x = (R)re; o.y = (R)im;
+        Z ar; ar.x = (R)a.x; ar.y = (R)a.y;
+        Z o = ar * x[t];
+        if (accumulate) o += y[t];
         y[t] = o;
     }
 }
@@ -122,11 +135,10 @@ __global__ void gamma5_kernel(const Z* __restrict__ x, Z* __restrict__ y, size_t
 template <typename Z, typename R>
 __global__ void axpby_kernel(double2 a, const Z* __restrict__ x, double2 b, Z* __restrict__ y, size_t n) {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-        Z xv = x[t], yv = y[t];
-        double re = a.x * xv.x - a.y * xv.y + b.x * yv.x - b.y * yv.y;
-        double im = a.x * xv.y + a.y * xv.x + b.x * yv.y + b.y * yv.x;
-        Z o; o.x = (R)re; o.y = (R)im;
-        y[t] = o;
+        Z ar, br;
+        ar.x = (R)a.x; ar.y = (R)a.y;
+        br.x = (R)b.x; br.y = (R)b.y;
+        y[t] = ar * x[t] + br * y[t];
     }
 }
 

@@ -164,6 +164,10 @@ int coarse_gmres(const Coarse& c, int prec, int op, int nrhs, const void* b, voi
 // returns mu = 1/theta and S (column-major m x m) in device buffers.
 void small_harmonic_eig(const double2* G, const double2* H, int m, int ld, double* mu, double2* S,
                         double2* work, int* status, cudaStream_t st);
+// FP64 refinement of the targeted pairs (columns idx[0..nb) of S, entries
+// of mu) by inverse iteration on the pencil; work >= nb * m * m double2.
+void small_refine_targets(const double2* G, const double2* H, int m, int ld, double2* S, double* mu, const int* idx,
+                          int nb, double2* work, cudaStream_t st);
 // Orthonormal Q (m x k, column-major, leading dim m) of the columns of S
 // (m x k, leading dimension lds) by modified Gram-Schmidt applied twice.
 void small_qr(const double2* S, int m, int k, int lds, double2* Q, double2* work, cudaStream_t st);

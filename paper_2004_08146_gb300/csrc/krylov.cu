@@ -24,6 +24,7 @@ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.
 
 // Givens update of column `it` of one right-hand side; h[0..it] is the new
 // Hessenberg column, hn its sub-diagonal entry.  Returns |g_{it+1}|.
+// (FP64: the host-side FGMRES bookkeeping and FP64 coarse solves.)
 __device__ double givens_column(double2* h, double hn, double* cs, double2* sn, double2* g, int it) {
     for (int i = 0; i < it; ++i) {
         double2 a = h[i], c = h[i + 1];
@@ -44,6 +45,31 @@ __device__ double givens_column(double2* h, double hn, double* cs, double2* sn, 
     g[it + 1] = -1.0 * (conj(sn[it]) * g[it]);
     g[it] = cs[it] * g[it];
     return sqrt(cabs2(g[it + 1]));
+}
+
+// Same update in the working precision R of a coarse solve (FP32 for the
+// mixed-precision path: the coarse system only needs a 0.5 reduction).
+template <typename R>
+__device__ double givens_column_t(cplx<R>* h, R hn, R* cs, cplx<R>* sn, cplx<R>* g, int it) {
+    for (int i = 0; i < it; ++i) {
+        cplx<R> a = h[i], c = h[i + 1];
+        h[i] = cs[i] * a + sn[i] * c;
+        h[i + 1] = cs[i] * c - conj(sn[i]) * a;
+    }
+    cplx<R> a = h[it];
+    cplx<R> c = mk<R>(hn, R(0));
+    R aa = sqrt(a.x * a.x + a.y * a.y), rr = sqrt(aa * aa + hn * hn);
+    if (aa > R(0)) {
+        cs[it] = aa / rr;
+        sn[it] = (R(1) / rr) * ((R(1) / aa) * a * conj(c));
+    } else {
+        cs[it] = R(0);
+        sn[it] = mk<R>(R(1), R(0));
+    }
+    h[it] = cs[it] * a + sn[it] * c;
+    g[it + 1] = R(-1) * (conj(sn[it]) * g[it]);
+    g[it] = cs[it] * g[it];
+    return (double)sqrt(g[it + 1].x * g[it + 1].x + g[it + 1].y * g[it + 1].y);
 }
 
 __global__ void kry_init_kernel(KryDev K, const double2* __restrict__ nrm, const int* __restrict__ outer_act) {
@@ -151,7 +177,7 @@ __device__ __forceinline__ void coarse_row(const CoarseArgs<Z, R>& a, const Z* x
     out = acc;
 }
 
-struct CoarseSmem { size_t As, xn, Vs, ws, hc, h1, hcol, cs, sn, g, beta, live, kd, total; };
+struct CoarseSmem { size_t As, xn, Vs, ws, hc, h1, hr, hcol, cs, sn, g, beta, after, live, kd, again, total; };
 template <typename Z>
 __host__ __device__ inline CoarseSmem coarse_smem(int nrhs, int maxit, int E, int sps = 0, int nc = 0) {
     auto up = [](size_t v) { return (v + 15) & ~size_t(15); };
@@ -161,15 +187,18 @@ __host__ __device__ inline CoarseSmem coarse_smem(int nrhs, int maxit, int E, in
     L.xn = o;   o = up(o + sizeof(Z) * (size_t)nrhs * sps * 9 * nc);
     L.Vs = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 1) * nrhs * E);
     L.ws = o;   o = up(o + sizeof(Z) * (size_t)nrhs * E);
-    L.hc = o;   o = up(o + sizeof(double2) * (size_t)(maxit + 2) * nrhs);
-    L.h1 = o;   o = up(o + sizeof(double2) * (size_t)(maxit + 2) * nrhs);
-    L.hcol = o; o = up(o + sizeof(double2) * (size_t)(maxit + 1) * nrhs);
-    L.cs = o;   o = up(o + sizeof(double) * (size_t)nrhs * maxit);
-    L.sn = o;   o = up(o + sizeof(double2) * (size_t)nrhs * maxit);
-    L.g = o;    o = up(o + sizeof(double2) * (size_t)nrhs * (maxit + 1));
+    L.hc = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 2) * nrhs);
+    L.h1 = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 2) * nrhs);
+    L.hr = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 1) * nrhs);
+    L.hcol = o; o = up(o + sizeof(Z) * (size_t)(maxit + 1) * nrhs);
+    L.cs = o;   o = up(o + sizeof(Z) * (size_t)nrhs * maxit);
+    L.sn = o;   o = up(o + sizeof(Z) * (size_t)nrhs * maxit);
+    L.g = o;    o = up(o + sizeof(Z) * (size_t)nrhs * (maxit + 1));
     L.beta = o; o = up(o + sizeof(double) * nrhs);
+    L.after = o; o = up(o + sizeof(Z) * nrhs);
     L.live = o; o = up(o + sizeof(int) * nrhs);
     L.kd = o;   o = up(o + sizeof(int) * nrhs);
+    L.again = o; o = up(o + sizeof(int) * 4);
     L.total = o;
     return L;
 }
@@ -184,15 +213,20 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
     Z* xn = reinterpret_cast<Z*>(sraw + LY.xn);          // [nrhs][sps][9][nc] neighbour vectors
     Z* Vs = reinterpret_cast<Z*>(sraw + LY.Vs);          // [(maxit+1)][nrhs][E]
     Z* ws = reinterpret_cast<Z*>(sraw + LY.ws);          // [nrhs][E]
-    double2* hc = reinterpret_cast<double2*>(sraw + LY.hc);   // coefficients of the current pass
-    double2* h1s = reinterpret_cast<double2*>(sraw + LY.h1);  // pass-1 coefficients, kept for the Hessenberg column
-    double2* hcol = reinterpret_cast<double2*>(sraw + LY.hcol);   // [nrhs][maxit+1] column under rotation
-    double* cs = reinterpret_cast<double*>(sraw + LY.cs);
-    double2* sn = reinterpret_cast<double2*>(sraw + LY.sn);
-    double2* g = reinterpret_cast<double2*>(sraw + LY.g);
+    // the serial per-iteration bookkeeping runs in the working precision R:
+    // a dependent chain of FP64 operations is very slow on this part
+    Z* hc = reinterpret_cast<Z*>(sraw + LY.hc);          // coefficients of the current pass (+ norms)
+    Z* h1s = reinterpret_cast<Z*>(sraw + LY.h1);         // pass-1 coefficients, kept for the Hessenberg column
+    Z* hr = reinterpret_cast<Z*>(sraw + LY.hr);               // current-pass coefficients in the working precision
+    Z* hcol = reinterpret_cast<Z*>(sraw + LY.hcol);      // [nrhs][maxit+1] column under rotation
+    R* cs = reinterpret_cast<R*>(sraw + LY.cs);
+    Z* sn = reinterpret_cast<Z*>(sraw + LY.sn);
+    Z* g = reinterpret_cast<Z*>(sraw + LY.g);
     double* beta = reinterpret_cast<double*>(sraw + LY.beta);
     int* live = reinterpret_cast<int*>(sraw + LY.live);
     int* kd = reinterpret_cast<int*>(sraw + LY.kd);
+    R* after = reinterpret_cast<R*>(sraw + LY.after);   // [nrhs] ||w||^2 after pass 1
+    int* againf = reinterpret_cast<int*>(sraw + LY.again);
 
     const size_t nco = (size_t)a.gc.V * a.nc;
     const size_t lo = (size_t)blockIdx.x * E;
@@ -218,18 +252,20 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
             else { j = p - ni * nrhs; xa = Y + (size_t)j * E; }
             if (!live[j]) continue;
             const Z* ya = Y + (size_t)j * E;
-            double re = 0, im = 0;
+            // this CTA's share in the working precision R; only the cross-CTA
+            // totals are FP64 (FP64 throughput per SM is tiny on this part)
+            R re = 0, im = 0;
             for (int e = lane; e < len; e += 32) {
                 Z u = xa[e], v = ya[e];
-                re += (double)u.x * v.x + (double)u.y * v.y;
-                im += (double)u.x * v.y - (double)u.y * v.x;
+                re += u.x * v.x + u.y * v.y;
+                im += u.x * v.y - u.y * v.x;
             }
             re = warp_sum(re);
             im = warp_sum(im);
             const int slot = p < ni * nrhs ? p : (maxit + 1) * nrhs + j;
             if (lane == 0 && len > 0) {
-                atomicAdd(&tot[slot].x, re);
-                atomicAdd(&tot[slot].y, im);
+                atomicAdd(&tot[slot].x, (double)re);
+                atomicAdd(&tot[slot].y, (double)im);
             }
         }
     };
@@ -239,12 +275,7 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
             const int j = t / len, e = t % len;
             if (!live[j]) continue;
             Z acc = ws[(size_t)j * E + e];
-            for (int i = 0; i < ni; ++i) {
-                double2 h = hc[i * nrhs + j];
-                Z v = VS(i, j)[e];
-                acc.x -= (R)(h.x * v.x - h.y * v.y);
-                acc.y -= (R)(h.x * v.y + h.y * v.x);
-            }
+            for (int i = 0; i < ni; ++i) acc -= hr[i * nrhs + j] * VS(i, j)[e];
             ws[(size_t)j * E + e] = acc;
         }
     };
@@ -263,7 +294,7 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
         beta[j] = bb;
         if (!(bb > 0)) live[j] = 0;
         kd[j] = 0;
-        g[(size_t)j * (maxit + 1)] = make_double2(bb, 0);
+        g[(size_t)j * (maxit + 1)] = mk<R>((R)bb, R(0));
     }
     __syncthreads();
     for (int t = tid; t < nrhs * len; t += blockDim.x) {
@@ -334,36 +365,67 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
             }
         }
         __syncthreads();
-        // classical Gram-Schmidt, pass 1
-        dots(TOT(par, 0), it + 1, false, ws);
+        // classical Gram-Schmidt, pass 1, with ||w||^2 before the projection
+        dots(TOT(par, 0), it + 1, true, ws);
         grid.sync();
-        for (int t = tid; t < (it + 1) * nrhs; t += blockDim.x) hc[t] = h1s[t] = TOT(par, 0)[t];
+        for (int t = tid; t < (it + 1) * nrhs; t += blockDim.x) {
+            const double2 v = TOT(par, 0)[t];
+            hc[t] = h1s[t] = hr[t] = mk<R>((R)v.x, (R)v.y);
+        }
+        if (tid == 0) againf[0] = 0;
         __syncthreads();
+        // second pass only if some right-hand side lost more than half of its
+        // norm in the first ("twice is enough", Kahan-Parlett); every CTA takes
+        // the same decision from the same totals
+        if (tid < nrhs) {
+            const int j = tid;
+            const R before = (R)TOT(par, 0)[(maxit + 1) * nrhs + j].x;
+            R proj = 0;
+            for (int i = 0; i <= it; ++i) proj += h1s[i * nrhs + j].x * h1s[i * nrhs + j].x + h1s[i * nrhs + j].y * h1s[i * nrhs + j].y;
+            after[j] = before - proj;
+            if (live[j] && before - proj < R(0.49) * before) atomicOr(againf, 1);
+        }
+        __syncthreads();
+        const int again = againf[0];
         project(it + 1);
         __syncthreads();
-        // pass 2 and ||w||^2 before its update
-        dots(TOT(par, 1), it + 1, true, ws);
-        grid.sync();
-        for (int t = tid; t < (it + 1) * nrhs; t += blockDim.x) hc[t] = TOT(par, 1)[t];
-        for (int t = tid; t < nrhs; t += blockDim.x) hc[(maxit + 1) * nrhs + t] = TOT(par, 1)[(maxit + 1) * nrhs + t];
-        __syncthreads();
-        project(it + 1);
+        if (again) {
+            dots(TOT(par, 1), it + 1, true, ws);
+            grid.sync();
+            for (int t = tid; t < (it + 1) * nrhs; t += blockDim.x) {
+                const double2 v = TOT(par, 1)[t];
+                hc[t] = hr[t] = mk<R>((R)v.x, (R)v.y);
+            }
+            for (int t = tid; t < nrhs; t += blockDim.x) {
+                const double2 v = TOT(par, 1)[(maxit + 1) * nrhs + t];
+                hc[(maxit + 1) * nrhs + t] = mk<R>((R)v.x, (R)v.y);
+            }
+            __syncthreads();
+            project(it + 1);
+        } else {
+            // no second pass: its coefficients are zero, ||w||^2 by Pythagoras
+            for (int t = tid; t < (it + 1) * nrhs; t += blockDim.x) hc[t] = mk<R>(R(0), R(0));
+            for (int j = tid; j < nrhs; j += blockDim.x) hc[(maxit + 1) * nrhs + j] = mk<R>(after[j], R(0));
+            __syncthreads();
+        }
         if (tid < nrhs) {
             const int j = tid;
             if (live[j]) {
-                double2* h = hcol + (size_t)j * (maxit + 1);
-                double h2n = 0.0;
+                Z* h = hcol + (size_t)j * (maxit + 1);
+                R h2n = 0;
                 for (int i = 0; i <= it; ++i) {
-                    const double2 p2 = hc[i * nrhs + j];
+                    const Z p2 = hc[i * nrhs + j];
                     h[i] = h1s[i * nrhs + j] + p2;
-                    h2n += cabs2(p2);
+                    h2n += p2.x * p2.x + p2.y * p2.y;
                 }
-                const double hn = sqrt(fmax(hc[(maxit + 1) * nrhs + j].x - h2n, 0.0));
-                hc[(maxit + 1) * nrhs + j] = make_double2(hn, 0.0);
-                const double res = givens_column(h, hn, cs + (size_t)j * maxit, sn + (size_t)j * maxit,
-                                                 g + (size_t)j * (maxit + 1), it);
+                const R hn2 = hc[(maxit + 1) * nrhs + j].x - h2n;
+                const R hn = hn2 > R(0) ? sqrt(hn2) : R(0);
+                hc[(maxit + 1) * nrhs + j] = mk<R>(hn, R(0));
+                const double res = givens_column_t<R>(h, hn, cs + (size_t)j * maxit, sn + (size_t)j * maxit,
+                                                      g + (size_t)j * (maxit + 1), it);
                 if (blockIdx.x == 0) {
-                    for (int i = 0; i <= it; ++i) a.Rg[((size_t)j * maxit + i) * maxit + it] = h[i];
+                    Z* Rj = reinterpret_cast<Z*>(a.Rg) + (size_t)j * maxit * maxit;
+                    for (int i = 0; i <= it; ++i) Rj[(size_t)i * maxit + it] = h[i];
                     a.resid[j] = beta[j] > 0 ? res / beta[j] : 0.0;
                 }
                 kd[j] = it + 1;
@@ -375,8 +437,8 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
         for (int t = tid; t < nrhs * len; t += blockDim.x) {
             const int j = t / len, e = t % len;
             if (kd[j] != it + 1) continue;
-            const double hn = hc[(maxit + 1) * nrhs + j].x;
-            const R ih = hn > 0 ? (R)(1.0 / hn) : R(0);
+            const R hn = hc[(maxit + 1) * nrhs + j].x;
+            const R ih = hn > R(0) ? R(1) / hn : R(0);
             Z v = ws[(size_t)j * E + e];
             v.x *= ih; v.y *= ih;
             VS(it + 1, j)[e] = v;
@@ -389,15 +451,15 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
     // triangular solve (CTA 0) and x = V y
     if (blockIdx.x == 0 && tid < nrhs) {
         const int j = tid, k = kd[j];
-        const double2* Rj = a.Rg + (size_t)j * maxit * maxit;
-        const double2* gj = g + (size_t)j * (maxit + 1);
-        double2* y = a.yv + (size_t)j * maxit;
+        const Z* Rj = reinterpret_cast<const Z*>(a.Rg) + (size_t)j * maxit * maxit;
+        const Z* gj = g + (size_t)j * (maxit + 1);
+        Z* y = reinterpret_cast<Z*>(a.yv) + (size_t)j * maxit;
         for (int i = k - 1; i >= 0; --i) {
-            double2 sacc = gj[i];
+            Z sacc = gj[i];
             for (int l = i + 1; l < k; ++l) sacc -= Rj[(size_t)i * maxit + l] * y[l];
-            double2 d = Rj[(size_t)i * maxit + i];
-            double den = cabs2(d);
-            y[i] = den > 0 ? (1.0 / den) * cmulc(d, sacc) : make_double2(0, 0);
+            const Z d = Rj[(size_t)i * maxit + i];
+            const R den = d.x * d.x + d.y * d.y;
+            y[i] = den > R(0) ? (R(1) / den) * cmulc(d, sacc) : mk<R>(R(0), R(0));
         }
         a.iters[j] = k;
         if (a.counter != nullptr && (a.act == nullptr || a.act[j])) {
@@ -410,14 +472,9 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
         const int j = t / len, e = t % len;
         if (a.act != nullptr && !a.act[j]) continue;
         const int k = kd[j];
-        const double2* y = a.yv + (size_t)j * maxit;
-        double re = 0, im = 0;
-        for (int i = 0; i < k; ++i) {
-            Z v = VS(i, j)[e];
-            re += y[i].x * v.x - y[i].y * v.y;
-            im += y[i].x * v.y + y[i].y * v.x;
-        }
-        Z o; o.x = (R)re; o.y = (R)im;
+        const Z* y = reinterpret_cast<const Z*>(a.yv) + (size_t)j * maxit;
+        Z o; o.x = 0; o.y = 0;
+        for (int i = 0; i < k; ++i) o += y[i] * VS(i, j)[e];
         a.x[(size_t)j * nco + lo + e] = o;
     }
 }

@@ -464,18 +464,18 @@ __host__ __device__ inline SapSmemLayout sap_layout(int BS, int iters) {
     L.basis = o;  o = up(o + (size_t)(iters + 1) * BS * 12 * sizeof(cplx<R>));
     L.links = o;  o = up(o + (size_t)BS * 36 * sizeof(cplx<R>));
     L.clover = o; o = up(o + (size_t)BS * 72 * sizeof(R));
-    L.H = o;      o = up(o + (size_t)(iters + 1) * iters * sizeof(double2));
-    L.g = o;      o = up(o + (size_t)(iters + 1) * sizeof(double2));
-    L.sn = o;     o = up(o + (size_t)iters * sizeof(double2));
-    L.y = o;      o = up(o + (size_t)iters * sizeof(double2));
-    L.cs = o;     o = up(o + (size_t)iters * sizeof(double));
+    L.H = o;      o = up(o + (size_t)(iters + 1) * iters * sizeof(cplx<R>));
+    L.g = o;      o = up(o + (size_t)(iters + 1) * sizeof(cplx<R>));
+    L.sn = o;     o = up(o + (size_t)iters * sizeof(cplx<R>));
+    L.y = o;      o = up(o + (size_t)iters * sizeof(cplx<R>));
+    L.cs = o;     o = up(o + (size_t)iters * sizeof(R));
     L.flag = o;   o = up(o + 4 * sizeof(int));
     L.total = o;
     return L;
 }
 
-template <int BS>
-__device__ __forceinline__ double seg_sum(double v) {
+template <int BS, typename T>
+__device__ __forceinline__ T seg_sum(T v) {
 #pragma unroll
     for (int o = BS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -496,11 +496,13 @@ __global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const 
     cplx<R>* basis = reinterpret_cast<cplx<R>*>(base + LY.basis);
     cplx<R>* slink = reinterpret_cast<cplx<R>*>(base + LY.links);
     R* sclov = reinterpret_cast<R*>(base + LY.clover);
-    double2* H = reinterpret_cast<double2*>(base + LY.H);
-    double2* gv = reinterpret_cast<double2*>(base + LY.g);
-    double2* sn = reinterpret_cast<double2*>(base + LY.sn);
-    double2* yv = reinterpret_cast<double2*>(base + LY.y);
-    double* cs = reinterpret_cast<double*>(base + LY.cs);
+    // Hessenberg bookkeeping by lane 0 in the working precision (a dependent
+    // FP64 chain is very slow on this part)
+    cplx<R>* H = reinterpret_cast<cplx<R>*>(base + LY.H);
+    cplx<R>* gv = reinterpret_cast<cplx<R>*>(base + LY.g);
+    cplx<R>* sn = reinterpret_cast<cplx<R>*>(base + LY.sn);
+    cplx<R>* yv = reinterpret_cast<cplx<R>*>(base + LY.y);
+    R* cs = reinterpret_cast<R*>(base + LY.cs);
     int* flag = reinterpret_cast<int*>(base + LY.flag);
 
     const int j = blockIdx.y;
@@ -527,17 +529,17 @@ __global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const 
     for (int k = 0; k < 72; ++k) sclov[l * 72 + k] = __ldg(A + (size_t)y * 72 + k);
     Spinor<R> w;
     load_spinor<R>(r + (size_t)y * 12, w);
-    double nn = 0.0;
+    R nn = 0;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) nn += (double)w.c[k].x * w.c[k].x + (double)w.c[k].y * w.c[k].y;
+    for (int k = 0; k < 12; ++k) nn += w.c[k].x * w.c[k].x + w.c[k].y * w.c[k].y;
     nn = seg_sum<BS>(nn);
-    const double beta = valid ? sqrt(nn) : 0.0;
+    const R beta = valid ? sqrt(nn) : R(0);
     {
-        const R ib = beta > 0 ? (R)(1.0 / beta) : R(0);
+        const R ib = beta > R(0) ? R(1) / beta : R(0);
 #pragma unroll
         for (int k = 0; k < 12; ++k) basis[l * 12 + k] = ib * w.c[k];
     }
-    if (l == 0) { gv[0] = make_double2(beta, 0); flag[0] = beta > 0 ? 0 : 1; flag[1] = 0; }
+    if (l == 0) { gv[0] = mk<R>(beta, R(0)); flag[0] = beta > R(0) ? 0 : 1; flag[1] = 0; }
     __syncwarp();
     int lstride[4];
     lstride[3] = 1;
@@ -598,65 +600,65 @@ __global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const 
         // modified Gram-Schmidt against v_0 .. v_jj
         for (int i = 0; i <= jj; ++i) {
             const cplx<R>* vi = basis + (size_t)i * BS * 12 + l * 12;
-            double hr = 0.0, hi = 0.0;
+            R hr = 0, hi = 0;
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
                 cplx<R> a = vi[k];
-                hr += (double)a.x * acc.c[k].x + (double)a.y * acc.c[k].y;
-                hi += (double)a.x * acc.c[k].y - (double)a.y * acc.c[k].x;
+                hr += a.x * acc.c[k].x + a.y * acc.c[k].y;
+                hi += a.x * acc.c[k].y - a.y * acc.c[k].x;
             }
             hr = seg_sum<BS>(hr);
             hi = seg_sum<BS>(hi);
-            const cplx<R> h = mk<R>((R)hr, (R)hi);
+            const cplx<R> h = mk<R>(hr, hi);
 #pragma unroll
             for (int k = 0; k < 12; ++k) acc.c[k] -= h * vi[k];
-            if (l == 0 && active) H[i * iters + jj] = make_double2(hr, hi);
+            if (l == 0 && active) H[i * iters + jj] = mk<R>(hr, hi);
         }
-        double hn2 = 0.0;
+        R hn2 = 0;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) hn2 += (double)acc.c[k].x * acc.c[k].x + (double)acc.c[k].y * acc.c[k].y;
+        for (int k = 0; k < 12; ++k) hn2 += acc.c[k].x * acc.c[k].x + acc.c[k].y * acc.c[k].y;
         hn2 = seg_sum<BS>(hn2);
-        const double hn = sqrt(hn2);
+        const R hn = sqrt(hn2);
         {
-            const R ih = hn > 0 ? (R)(1.0 / hn) : R(0);
+            const R ih = hn > R(0) ? R(1) / hn : R(0);
             cplx<R>* vn = basis + (size_t)(jj + 1) * BS * 12 + l * 12;
 #pragma unroll
             for (int k = 0; k < 12; ++k) vn[k] = ih * acc.c[k];
         }
         if (l == 0 && active) {
-            H[(jj + 1) * iters + jj] = make_double2(hn, 0);
+            H[(jj + 1) * iters + jj] = mk<R>(hn, R(0));
             for (int i = 0; i < jj; ++i) {
-                double2 a = H[i * iters + jj], c = H[(i + 1) * iters + jj];
+                cplx<R> a = H[i * iters + jj], c = H[(i + 1) * iters + jj];
                 H[i * iters + jj] = cs[i] * a + sn[i] * c;
                 H[(i + 1) * iters + jj] = cs[i] * c - conj(sn[i]) * a;
             }
-            double2 a = H[jj * iters + jj];
-            double2 c = H[(jj + 1) * iters + jj];
-            double aa = sqrt(a.x * a.x + a.y * a.y), rr = sqrt(aa * aa + c.x * c.x + c.y * c.y);
-            if (aa > 0) {
+            cplx<R> a = H[jj * iters + jj];
+            cplx<R> c = H[(jj + 1) * iters + jj];
+            R aa = sqrt(a.x * a.x + a.y * a.y), rr = sqrt(aa * aa + c.x * c.x + c.y * c.y);
+            if (aa > R(0)) {
                 cs[jj] = aa / rr;
-                sn[jj] = (1.0 / rr) * ((1.0 / aa) * a * conj(c));
+                sn[jj] = (R(1) / rr) * ((R(1) / aa) * a * conj(c));
             } else {
-                cs[jj] = 0.0;
-                sn[jj] = make_double2(1, 0);
+                cs[jj] = R(0);
+                sn[jj] = mk<R>(R(1), R(0));
             }
             H[jj * iters + jj] = cs[jj] * a + sn[jj] * c;
-            gv[jj + 1] = -1.0 * (conj(sn[jj]) * gv[jj]);
+            gv[jj + 1] = R(-1) * (conj(sn[jj]) * gv[jj]);
             gv[jj] = cs[jj] * gv[jj];
-            const double res = sqrt(gv[jj + 1].x * gv[jj + 1].x + gv[jj + 1].y * gv[jj + 1].y);
+            const R res = sqrt(gv[jj + 1].x * gv[jj + 1].x + gv[jj + 1].y * gv[jj + 1].y);
             flag[1] = jj + 1;
-            if (tol >= 0.0 && res <= tol * beta) flag[0] = 1;
+            if (tol >= 0.0 && (double)res <= tol * (double)beta) flag[0] = 1;
         }
         __syncwarp();
     }
     const int kdim = flag[1];
     if (l == 0) {
         for (int i = kdim - 1; i >= 0; --i) {
-            double2 sacc = gv[i];
+            cplx<R> sacc = gv[i];
             for (int k = i + 1; k < kdim; ++k) sacc -= H[i * iters + k] * yv[k];
-            double2 dd = H[i * iters + i];
-            double den = dd.x * dd.x + dd.y * dd.y;
-            yv[i] = den > 0 ? (1.0 / den) * cmulc(dd, sacc) : make_double2(0, 0);
+            cplx<R> dd = H[i * iters + i];
+            R den = dd.x * dd.x + dd.y * dd.y;
+            yv[i] = den > R(0) ? (R(1) / den) * cmulc(dd, sacc) : mk<R>(R(0), R(0));
         }
     }
     __syncwarp();
@@ -664,7 +666,7 @@ __global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const 
     Spinor<R> e;
     load_spinor<R>(x + (size_t)y * 12, e);
     for (int i = 0; i < kdim; ++i) {
-        const cplx<R> yi = mk<R>((R)yv[i].x, (R)yv[i].y);
+        const cplx<R> yi = yv[i];
         const cplx<R>* vi = basis + (size_t)i * BS * 12 + l * 12;
 #pragma unroll
         for (int k = 0; k < 12; ++k) e.c[k] += yi * vi[k];
