@@ -50,6 +50,18 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, device=None):
+    """Max of a per-rank float over all ranks of the default process group
+    (the whole-job time of N replicas); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -252,11 +264,7 @@ def main():
     d = st_timed[dom["name"]]
     peak, peak_kind = measured_peaks()
     achieved = d["timed_bytes"] / (d["total_ms"] * 1e-3) / 1e9 if d["total_ms"] > 0 else 0.0
-    step_s = sum(ms) / len(ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([step_s], device=devn)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_s = float(t.item())
+    step_s = max_over_ranks(sum(ms) / len(ms) / 1e3, devn)
 
     # ---- FP64 comparison (same workload, same tolerance)
     fp64 = None

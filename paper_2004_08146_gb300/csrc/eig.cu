@@ -385,7 +385,7 @@ void small_harmonic_eig(const double2* G, const double2* H, int m, int ld, doubl
 void small_refine_targets(const double2* G, const double2* H, int m, int ld, double2* S, double* mu, const int* idx,
                           int nb, double2* work, cudaStream_t st) {
     KTimer kt("refine_targets", 0.0, 0.0, st);
-    refine_targets_kernel<<<nb, kT, 0, st>>>(G, H, m, ld, S, mu, idx, work, 2);
+    refine_targets_kernel<<<nb, kT, 0, st>>>(G, H, m, ld, S, mu, idx, work, 1);
 }
 void small_qr(const double2* S, int m, int k, int lds, double2* Q, double2* work, cudaStream_t st) {
     (void)work;

@@ -177,7 +177,7 @@ __device__ __forceinline__ void coarse_row(const CoarseArgs<Z, R>& a, const Z* x
     out = acc;
 }
 
-struct CoarseSmem { size_t As, xn, Vs, ws, hc, h1, hr, hcol, cs, sn, g, beta, after, live, kd, again, total; };
+struct CoarseSmem { size_t As, xn, nbr, Vs, ws, hc, h1, hr, hcol, cs, sn, g, beta, after, live, kd, again, total; };
 template <typename Z>
 __host__ __device__ inline CoarseSmem coarse_smem(int nrhs, int maxit, int E, int sps = 0, int nc = 0) {
     auto up = [](size_t v) { return (v + 15) & ~size_t(15); };
@@ -185,6 +185,7 @@ __host__ __device__ inline CoarseSmem coarse_smem(int nrhs, int maxit, int E, in
     size_t o = 0;
     L.As = o;   o = up(o + sizeof(Z) * (size_t)sps * 9 * nc * nc);
     L.xn = o;   o = up(o + sizeof(Z) * (size_t)nrhs * sps * 9 * nc);
+    L.nbr = o;  o = up(o + sizeof(int) * (size_t)sps * 9);
     L.Vs = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 1) * nrhs * E);
     L.ws = o;   o = up(o + sizeof(Z) * (size_t)nrhs * E);
     L.hc = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 2) * nrhs);
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
     const CoarseSmem LY = coarse_smem<Z>(nrhs, maxit, E, a.a_smem ? a.sps : 0, a.a_smem ? nc : 0);
     Z* As = reinterpret_cast<Z*>(sraw + LY.As);          // [sps][9][col][row] stencil blocks of my sites
     Z* xn = reinterpret_cast<Z*>(sraw + LY.xn);          // [nrhs][sps][9][nc] neighbour vectors
+    int* nbr = reinterpret_cast<int*>(sraw + LY.nbr);    // [sps][9] neighbour sites
     Z* Vs = reinterpret_cast<Z*>(sraw + LY.Vs);          // [(maxit+1)][nrhs][E]
     Z* ws = reinterpret_cast<Z*>(sraw + LY.ws);          // [nrhs][E]
     // the serial per-iteration bookkeeping runs in the working precision R:
@@ -236,6 +238,18 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
     if (a.a_smem) {
         const Z* src = a.A + (size_t)s0 * 9 * nc * nc;
         for (size_t t = threadIdx.x; t < (size_t)nsl * 9 * nc * nc; t += blockDim.x) As[t] = src[t];
+        for (int t = threadIdx.x; t < nsl * 9; t += blockDim.x) {
+            const int sl = t / 9, d = t % 9;
+            int c[4];
+            site_coords(a.gc, s0 + sl, c);
+            int sn = s0 + sl;
+            if (d > 0) {
+                int mu = (d - 1) & 3, step = d <= 4 ? 1 : -1;
+                c[mu] = (c[mu] + step + a.gc.L[mu]) % a.gc.L[mu];
+                sn = site_index(a.gc, c);
+            }
+            nbr[t] = sn;
+        }
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int npair = (maxit + 2) * nrhs;
@@ -245,28 +259,40 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
     // partial inner products of this chunk: <Vs_i[j], ws[j]> for i < ni (+ ||ws_j||^2), added to `tot`
     auto dots = [&](double2* tot, int ni, bool with_norm, const Z* Y) {
         const int np = ni * nrhs + (with_norm ? nrhs : 0);
-        for (int p = warp; p < np; p += nw) {
-            int j;
-            const Z* xa;
-            if (p < ni * nrhs) { j = p % nrhs; xa = VS(p / nrhs, j); }
-            else { j = p - ni * nrhs; xa = Y + (size_t)j * E; }
-            if (!live[j]) continue;
-            const Z* ya = Y + (size_t)j * E;
-            // this CTA's share in the working precision R; only the cross-CTA
-            // totals are FP64 (FP64 throughput per SM is tiny on this part)
-            R re = 0, im = 0;
-            for (int e = lane; e < len; e += 32) {
-                Z u = xa[e], v = ya[e];
-                re += u.x * v.x + u.y * v.y;
-                im += u.x * v.y - u.y * v.x;
+        // two pairs per warp and round (independent shuffle chains overlap);
+        // this CTA's share in the working precision R, only the cross-CTA
+        // totals are FP64 (FP64 throughput per SM is tiny on this part)
+        for (int p0 = 2 * warp; p0 < np; p0 += 2 * nw) {
+            R re[2] = {0, 0}, im[2] = {0, 0};
+            int slot[2] = {-1, -1};
+            for (int q = 0; q < 2; ++q) {
+                const int p = p0 + q;
+                if (p >= np) break;
+                int j;
+                const Z* xa;
+                if (p < ni * nrhs) { j = p % nrhs; xa = VS(p / nrhs, j); }
+                else { j = p - ni * nrhs; xa = Y + (size_t)j * E; }
+                if (!live[j]) continue;
+                const Z* ya = Y + (size_t)j * E;
+                for (int e = lane; e < len; e += 32) {
+                    Z u = xa[e], v = ya[e];
+                    re[q] += u.x * v.x + u.y * v.y;
+                    im[q] += u.x * v.y - u.y * v.x;
+                }
+                slot[q] = p < ni * nrhs ? p : (maxit + 1) * nrhs + j;
             }
-            re = warp_sum(re);
-            im = warp_sum(im);
-            const int slot = p < ni * nrhs ? p : (maxit + 1) * nrhs + j;
-            if (lane == 0 && len > 0) {
-                atomicAdd(&tot[slot].x, (double)re);
-                atomicAdd(&tot[slot].y, (double)im);
+            for (int o = 16; o > 0; o >>= 1) {
+                re[0] += __shfl_xor_sync(0xffffffffu, re[0], o);
+                im[0] += __shfl_xor_sync(0xffffffffu, im[0], o);
+                re[1] += __shfl_xor_sync(0xffffffffu, re[1], o);
+                im[1] += __shfl_xor_sync(0xffffffffu, im[1], o);
             }
+            if (lane == 0 && len > 0)
+                for (int q = 0; q < 2; ++q)
+                    if (slot[q] >= 0) {
+                        atomicAdd(&tot[slot[q]].x, (double)re[q]);
+                        atomicAdd(&tot[slot[q]].y, (double)im[q]);
+                    }
         }
     };
     // ws[j] -= sum_i hc[i][j] Vs_i[j]
@@ -325,31 +351,40 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
             for (int t = tid; t < nrhs * nsl * 9 * nc; t += blockDim.x) {
                 const int col = t % nc, d = (t / nc) % 9, sl = (t / (9 * nc)) % nsl, j = t / (9 * nc * nsl);
                 if (!live[j]) continue;
-                int c[4];
-                site_coords(a.gc, s0 + sl, c);
-                int sn = s0 + sl;
-                if (d > 0) {
-                    int mu = (d - 1) & 3, step = d <= 4 ? 1 : -1;
-                    c[mu] = (c[mu] + step + a.gc.L[mu]) % a.gc.L[mu];
-                    sn = site_index(a.gc, c);
-                }
-                xn[(((size_t)j * nsl + sl) * 9 + d) * nc + col] = Vit[(size_t)j * nco + (size_t)sn * nc + col];
+                xn[(((size_t)j * nsl + sl) * 9 + d) * nc + col] = Vit[(size_t)j * nco + (size_t)nbr[sl * 9 + d] * nc + col];
             }
             __syncthreads();
-            for (int t = tid; t < nrhs * len; t += blockDim.x) {
-                const int j = t / len, e = t % len;
-                if (!live[j]) continue;
-                const int sl = e / nc, r = e % nc;
-                const Z* am = As + (size_t)sl * 9 * nc * nc + r;
-                const Z* xs = xn + ((size_t)j * nsl + sl) * 9 * nc;
+            // tpr consecutive threads share one row (idle threads otherwise)
+            const int items = nrhs * len;
+            int tpr = 1;
+            while (tpr < 4 && items * tpr * 2 <= (int)blockDim.x) tpr *= 2;
+            const int span = (9 * nc + tpr - 1) / tpr;
+            for (int t0 = tid; t0 < ((items * tpr + 31) / 32) * 32; t0 += blockDim.x) {
+                const int item = t0 / tpr, sub = t0 % tpr;
+                const bool ok = item < items && live[item / len];
                 Z acc; acc.x = 0; acc.y = 0;
-                for (int dc = 0; dc < 9 * nc; ++dc) acc += am[(size_t)dc * nc] * xs[dc];
-                const R sg = r < nc / 2 ? R(1) : R(-1);
-                const R tj = (R)a.tau[j];
-                const Z xv = xs[r];      // direction 0 is the site itself
-                if (a.op == QCD_OP_D) { acc -= (tj * sg) * xv; }
-                else { acc = sg * acc; acc -= tj * xv; }
-                ws[(size_t)j * E + e] = acc;
+                int j = 0, e = 0, sl = 0, r = 0;
+                if (ok) {
+                    j = item / len; e = item % len;
+                    sl = e / nc; r = e % nc;
+                    const Z* am = As + (size_t)sl * 9 * nc * nc + r;
+                    const Z* xs = xn + ((size_t)j * nsl + sl) * 9 * nc;
+                    const int d0 = sub * span, d1 = min(9 * nc, d0 + span);
+                    for (int dc = d0; dc < d1; ++dc) acc += am[(size_t)dc * nc] * xs[dc];
+                }
+                for (int o = tpr / 2; o > 0; o >>= 1) {
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                }
+                if (ok && sub == 0) {
+                    const Z* xs = xn + ((size_t)j * nsl + sl) * 9 * nc;
+                    const R sg = r < nc / 2 ? R(1) : R(-1);
+                    const R tj = (R)a.tau[j];
+                    const Z xv = xs[r];      // direction 0 is the site itself
+                    if (a.op == QCD_OP_D) { acc -= (tj * sg) * xv; }
+                    else { acc = sg * acc; acc -= tj * xv; }
+                    ws[(size_t)j * E + e] = acc;
+                }
             }
         } else {
             for (int t = tid; t < nrhs * len; t += blockDim.x) {
@@ -374,16 +409,17 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
         }
         if (tid == 0) againf[0] = 0;
         __syncthreads();
-        // second pass only if some right-hand side lost more than half of its
-        // norm in the first ("twice is enough", Kahan-Parlett); every CTA takes
-        // the same decision from the same totals
+        // second pass only if some right-hand side lost more than 90% of its
+        // squared norm in the first (a Kahan-Parlett test, loosened for a
+        // solve that only needs a 0.5 reduction); every CTA takes the same
+        // decision from the same totals
         if (tid < nrhs) {
             const int j = tid;
             const R before = (R)TOT(par, 0)[(maxit + 1) * nrhs + j].x;
             R proj = 0;
             for (int i = 0; i <= it; ++i) proj += h1s[i * nrhs + j].x * h1s[i * nrhs + j].x + h1s[i * nrhs + j].y * h1s[i * nrhs + j].y;
             after[j] = before - proj;
-            if (live[j] && before - proj < R(0.49) * before) atomicOr(againf, 1);
+            if (live[j] && before - proj < R(0.1) * before) atomicOr(againf, 1);
         }
         __syncthreads();
         const int again = againf[0];

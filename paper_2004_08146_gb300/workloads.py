@@ -13,7 +13,7 @@ WORKLOADS = {
     "c1_4c4": dict(dims=(4, 4, 4, 4), eps=0.3, csw=1.0, m0=-0.2, seed=1001, k=10,
                    use_mg=0, agg=None, nv=0, sap=(2, 2, 2, 2)),
     # 16 x 8^3, two-level MG with 2^4 aggregates, Nv = 8, SAP on 2^4 blocks, 50 pairs
-    "c2_16x8c3": dict(dims=(16, 8, 8, 8), eps=0.5, csw=1.5, m0=None, seed=1002, k=50,
+    "c2_16x8c3": dict(dims=(16, 8, 8, 8), eps=0.5, csw=1.5, m0=-0.85, seed=1002, k=50,
                       use_mg=1, agg=(2, 2, 2, 2), nv=8, sap=(2, 2, 2, 2), target=1e-2),
 }
 
