@@ -208,6 +208,25 @@ int qcd_sap(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x,
 int qcd_mg_cycle(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x,
                  const double* tau);
 
+/* qcd_sap with no memory allocation (the paper has no counterpart: this
+ * serves callers that cannot allocate device memory while they run, e.g. an
+ * application that gives the library a fixed memory budget up front, or a
+ * plugin whose host owns every allocation).  Same arguments, layout and
+ * result as qcd_sap; all scratch (colour block lists, nrhs residual fields,
+ * block-GMRES vectors for blocks of more than 32 sites) comes from one 64 MiB
+ * file-scope device array that every GPU loading libqcd keeps until the
+ * process exits.  Needs lists + 12 * V * nrhs complex fields (+ Krylov
+ * vectors) <= 64 MiB, else EINVAL with a message.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) and must be
+ * made with that device current; make it before any stream capture.  The
+ * call allocates nothing (no cudaMalloc/cudaFree, no library allocator) and
+ * records no launch statistics; it clears nothing because every scratch word
+ * is written before it is read.  All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race.  Returns after the
+ * context's stream has synchronised. */
+int qcd_sap_static(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x,
+                   const double* tau, int sweeps, double block_tol);
+
 /* ---------------------------------------------------------------------
  * Launch accounting (process-wide, not part of the method): every libqcd
  * kernel launch is counted with its algorithmic bytes and flops; with

@@ -1321,3 +1321,106 @@ int qcd_eigs(qcd_ctx* ctx, int k, double tol, double* lambda, void* V, qcd_eig_i
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free SAP
+// qcd_sap_static: the SAP sweeps of qcd_sap for callers that cannot allocate
+// device memory (a host application that hands the library a fixed memory
+// budget up front, or a plugin whose host owns every allocation).  All
+// scratch -- the colour block lists, the residual fields and, for blocks of
+// more than 32 sites, the block-GMRES Krylov vectors -- lives in one
+// file-scope device array of kSapStaticBytes that every GPU loading the
+// library keeps until the process exits.
+namespace {
+
+constexpr size_t kSapStaticBytes = 64ull << 20;   // 64 MiB
+__device__ __align__(256) unsigned char g_sap_static[kSapStaticBytes];
+
+constexpr int kStaticMaxDevices = 64;
+void* g_sap_static_ptr[kStaticMaxDevices] = {};   // device address of g_sap_static, per device
+
+// block lists of the two colours: with an even block-grid extent in mu = 3
+// the blocks of each colour are exactly every second block, so block b goes
+// to position b / 2 of its colour's list (ascending, like the host-built lists)
+__global__ void sap_colour_lists_kernel(Blocking B, int* list0, int* list1) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B.nb) return;
+    int t = b;
+    const int c3 = t % B.cd[3]; t /= B.cd[3];
+    const int c2 = t % B.cd[2]; t /= B.cd[2];
+    const int c1 = t % B.cd[1], c0 = t / B.cd[1];
+    ((c0 + c1 + c2 + c3) % 2 ? list1 : list0)[b / 2] = b;
+}
+
+int static_fail(qcd_ctx* ctx, int code, const char* msg) {
+    ctx->err.assign(msg);
+    return code;
+}
+
+}  // namespace
+
+extern "C" int qcd_sap_static(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x, const double* tau,
+                              int sweeps, double block_tol) {
+    if (!ctx) return QCD_EINVAL;
+    if (!ctx->have_gauge) return static_fail(ctx, QCD_ENOTSETUP, "no gauge field: call qcd_set_gauge first");
+    if ((op != QCD_OP_D && op != QCD_OP_Q) || (prec != QCD_FP64 && prec != QCD_FP32) || nrhs < 1 ||
+        nrhs > kMaxRhs || !b || !x || !tau || sweeps < 0)
+        return static_fail(ctx, QCD_EINVAL, "qcd_sap_static: bad arguments");
+    if ((((uintptr_t)b) & 15) || (((uintptr_t)x) & 15))
+        return static_fail(ctx, QCD_EINVAL, "qcd_sap_static: b and x must be 16-byte aligned");
+    // the SAP blocking, as qcd_sap builds it
+    Blocking B;
+    B.bs = 1;
+    B.nb = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        const int e = ctx->p.sap_block[mu];
+        if (e < 1 || ctx->f.g.L[mu] % e) return static_fail(ctx, QCD_EINVAL, "qcd_sap_static: block must divide the lattice");
+        B.b[mu] = e;
+        B.cd[mu] = ctx->f.g.L[mu] / e;
+        if (B.cd[mu] % 2) return static_fail(ctx, QCD_EINVAL, "qcd_sap_static: SAP needs an even block count per direction");
+        B.bs *= e;
+        B.nb *= B.cd[mu];
+    }
+    if ((B.bs & (B.bs - 1)) || B.bs > 1024)
+        return static_fail(ctx, QCD_EINVAL, "qcd_sap_static: SAP block sites must be a power of two <= 1024");
+    // scratch layout in the static array: [lists][residual fields][Krylov vectors]
+    SapPlan plan;
+    plan.B = B;
+    plan.ncol[0] = plan.ncol[1] = B.nb / 2;
+    const size_t n = ctx->nfine();
+    const size_t lists = ((size_t)B.nb * sizeof(int) + 255) & ~size_t(255);
+    const size_t rbytes = ((n * nrhs * esz(prec)) + 255) & ~size_t(255);
+    const size_t kbytes = B.bs > 32 ? sap_scratch_bytes(plan, prec, nrhs, ctx->p.sap_block_iters) : 0;
+    if (lists + rbytes + kbytes > kSapStaticBytes)
+        return static_fail(ctx, QCD_EINVAL, "qcd_sap_static: problem needs more scratch than the 64 MiB static array");
+    // set-up, once per device, with that device current
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
+        return static_fail(ctx, QCD_ECUDA, "qcd_sap_static: no usable current device");
+    if (g_sap_static_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_sap_static) != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return static_fail(ctx, QCD_ECUDA, "qcd_sap_static: cudaGetSymbolAddress failed");
+        }
+        g_sap_static_ptr[dev] = p;
+    }
+    unsigned char* base = (unsigned char*)g_sap_static_ptr[dev];
+    plan.blocks_of_colour[0] = (int*)base;
+    plan.blocks_of_colour[1] = (int*)base + B.nb / 2;
+    void* r = base + lists;
+    void* scr = base + lists + rbytes;
+    QuietAccounting quiet;
+    sap_colour_lists_kernel<<<(B.nb + 255) / 256, 256, 0, ctx->st>>>(B, plan.blocks_of_colour[0],
+                                                                      plan.blocks_of_colour[1]);
+    for (int s = 0; s < sweeps; ++s) {
+        for (int colour = 0; colour < 2; ++colour) {
+            residual_op(ctx->f, prec, op, nrhs, b, x, r, tau, ctx->st);
+            sap_blocks(ctx->f, plan, colour, prec, op, nrhs, r, x, tau, ctx->p.sap_block_iters, block_tol, scr,
+                       ctx->st);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) return static_fail(ctx, QCD_ECUDA, "qcd_sap_static: kernel launch failed");
+    return QCD_OK;
+}

@@ -29,6 +29,16 @@ private:
     cudaEvent_t ea_ = nullptr, eb_ = nullptr;
 };
 
+// While one of these lives on a thread, KTimer records nothing (no host
+// allocation for the accounting map).
+class QuietAccounting {
+public:
+    QuietAccounting();
+    ~QuietAccounting();
+private:
+    bool prev_;
+};
+
 // ------------------------------------------------------------------ fine operator
 struct FineOp {
     Geom g{};

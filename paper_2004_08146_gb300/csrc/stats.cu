@@ -45,8 +45,14 @@ cudaEvent_t take_event(Stats& s) {
 }
 }  // namespace
 
+thread_local bool t_quiet = false;
+
+QuietAccounting::QuietAccounting() : prev_(t_quiet) { t_quiet = true; }
+QuietAccounting::~QuietAccounting() { t_quiet = prev_; }
+
 KTimer::KTimer(const char* name, double bytes, double flops, cudaStream_t st) : name_(name), st_(st), bytes_(bytes),
                                                                                 flops_(flops) {
+    if (t_quiet) return;   // launches of an allocation-free entry point are not recorded
     Stats& s = S();
     std::lock_guard<std::mutex> g(s.mu);
     Agg& a = s.agg[name_];

@@ -101,6 +101,7 @@ _SIGS = {
     "qcd_mg_get_coarse": (_I, [_P, _DP]),
     "qcd_sap": (_I, [_P, _I, _I, _I, _P, _P, _DP, _I, _D]),
     "qcd_mg_cycle": (_I, [_P, _I, _I, _I, _P, _P, _DP]),
+    "qcd_sap_static": (_I, [_P, _I, _I, _I, _P, _P, _DP, _I, _D]),
     "qcd_stats_reset": (_I, [_I, ctypes.c_char_p]),
     "qcd_stats_read": (_I, [ctypes.POINTER(qcd_kernel_stat), _I, _IP]),
 }
@@ -264,6 +265,11 @@ class Context:
     def qcd_sap(self, op, prec, nrhs, b, x, tau, sweeps, block_tol):
         t, tp = _dbl(tau)
         return self._check(_lib.qcd_sap(self.h, op, prec, nrhs, _ptr(b), _ptr(x), tp, int(sweeps), float(block_tol)))
+
+    def qcd_sap_static(self, op, prec, nrhs, b, x, tau, sweeps, block_tol):
+        t, tp = _dbl(tau)
+        return self._check(_lib.qcd_sap_static(self.h, op, prec, nrhs, _ptr(b), _ptr(x), tp, int(sweeps),
+                                               float(block_tol)))
 
     def qcd_mg_cycle(self, op, prec, nrhs, b, x, tau):
         t, tp = _dbl(tau)
