@@ -67,6 +67,8 @@ struct qcd_ctx {
     double2* test_vectors = nullptr;  // FP64 setup vectors [nv][V*12]
     int n_test = 0;
     bool no_coop = false;             // cooperative coarse launch unavailable: host-driven GMRES
+    unsigned* md_cnt = nullptr;       // zeroed dot-product completion counters (blas_multidot)
+    size_t md_cnt_n = 0;
 
     ~qcd_ctx() { release(); }
 
@@ -83,6 +85,9 @@ struct qcd_ctx {
         if (pinned) cudaFreeHost(pinned);
         pinned = nullptr;
         pinned_n = 0;
+        fr(md_cnt);
+        md_cnt = nullptr;
+        md_cnt_n = 0;
     }
     void drop_mg() {
         auto fr = [](void* q) { if (q) cudaFree(q); };
@@ -106,6 +111,25 @@ struct qcd_ctx {
             b.bytes = bytes;
         }
         return b.p;
+    }
+    // completion counters for dot products, zero between launches
+    unsigned* dot_counters(size_t n) {
+        if (md_cnt_n < n) {
+            n = std::max<size_t>(n, 4096);
+            if (md_cnt) {
+                CK(cudaStreamSynchronize(st));
+                CK(cudaFree(md_cnt));
+            }
+            md_cnt = nullptr;
+            md_cnt_n = 0;
+            if (cudaMalloc(&md_cnt, n * sizeof(unsigned)) != cudaSuccess) {
+                cudaGetLastError();
+                throw QcdError(QCD_ENOMEM, "device allocation of dot-product counters");
+            }
+            CK(cudaMemsetAsync(md_cnt, 0, n * sizeof(unsigned), st));
+            md_cnt_n = n;
+        }
+        return md_cnt;
     }
     double2* host(size_t n) {
         if (pinned_n < n) {
@@ -178,7 +202,7 @@ GmresResult gmres_batched(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn
     out.iters.assign(nrhs, 0);
     out.resest.assign(nrhs, 1.0);
     // beta_j = ||b_j||
-    blas_multidot(prec, b, 1, vs, b, nrhs, n, nr, part, st);
+    blas_multidot(prec, b, 1, vs, b, nrhs, n, nr, part, ctx->dot_counters(nrhs), st);
     const double2* hb = ctx->fetch(nr, nrhs);
     std::vector<double> beta(nrhs);
     std::vector<double2> scl(nrhs);
@@ -210,11 +234,11 @@ GmresResult gmres_batched(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn
         } else {
             A(vj, w, nullptr);
         }
-        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h1, part, st);
+        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h1, part, ctx->dot_counters((size_t)(it + 1) * nrhs), st);
         blas_multiaxpy(prec, Vk, it + 1, vs, h1, -1.0, w, nrhs, n, st);
-        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h2, part, st);
+        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h2, part, ctx->dot_counters((size_t)(it + 1) * nrhs), st);
         blas_multiaxpy(prec, Vk, it + 1, vs, h2, -1.0, w, nrhs, n, st);
-        blas_multidot(prec, w, 1, vs, w, nrhs, n, nr, part, st);
+        blas_multidot(prec, w, 1, vs, w, nrhs, n, nr, part, ctx->dot_counters(nrhs), st);
         check_launch("gmres iteration");
         const double2* hh = ctx->fetch(dd, (size_t)(2 * (maxit + 1) + 1) * nrhs);
         const double2* hh1 = hh;
@@ -303,7 +327,7 @@ DevGmresOut gmres_dev(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn& A,
     double2* nr = (double2*)ctx->buf(tag + ".nr", (size_t)nrhs * sizeof(double2));
     double2* part = (double2*)ctx->buf(tag + ".part", (size_t)(maxit + 2) * nrhs * 64 * sizeof(double2));
     KryDev K = kry_layout(ctx->buf(tag + ".K", kry_bytes(nrhs, maxit)), nrhs, maxit, tol);
-    blas_multidot(prec, b, 1, vs, b, nrhs, n, nr, part, st);
+    blas_multidot(prec, b, 1, vs, b, nrhs, n, nr, part, ctx->dot_counters(nrhs), st);
     kry_init(K, nr, outer_act, st);
     blas_zero(prec, x, vs, st);
     blas_scale_dev(prec, b, Vk, K.scale, nrhs, n, false, false, st, K.active);
@@ -316,11 +340,11 @@ DevGmresOut gmres_dev(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn& A,
         } else {
             A(vj, w, K.active);
         }
-        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h1, part, st, K.active);
+        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h1, part, ctx->dot_counters((size_t)(it + 1) * nrhs), st, K.active);
         blas_multiaxpy(prec, Vk, it + 1, vs, h1, -1.0, w, nrhs, n, st, K.active);
-        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h2, part, st, K.active);
+        blas_multidot(prec, Vk, it + 1, vs, w, nrhs, n, h2, part, ctx->dot_counters((size_t)(it + 1) * nrhs), st, K.active);
         blas_multiaxpy(prec, Vk, it + 1, vs, h2, -1.0, w, nrhs, n, st, K.active);
-        blas_multidot(prec, w, 1, vs, w, nrhs, n, nr, part, st, K.active);
+        blas_multidot(prec, w, 1, vs, w, nrhs, n, nr, part, ctx->dot_counters(nrhs), st, K.active);
         kry_step(K, it, h1, h2, nr, st);
         if (it + 1 < maxit) blas_scale_dev(prec, w, Vk + (size_t)(it + 1) * vs * eb, K.scale, nrhs, n, false, false, st,
                                            K.active);
@@ -474,7 +498,7 @@ void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void
 void normalize_set(qcd_ctx* ctx, double2* X, int nvec, size_t n) {
     double2* nr = (double2*)ctx->buf("nrm.d", nvec * sizeof(double2));
     double2* part = (double2*)ctx->buf("nrm.part", (size_t)nvec * 64 * sizeof(double2));
-    blas_multidot(QCD_FP64, X, 1, (size_t)nvec * n, X, nvec, n, nr, part, ctx->st);
+    blas_multidot(QCD_FP64, X, 1, (size_t)nvec * n, X, nvec, n, nr, part, ctx->dot_counters(nvec), ctx->st);
     const double2* h = ctx->fetch(nr, nvec);
     std::vector<double2> s(nvec);
     for (int i = 0; i < nvec; ++i) s[i] = make_double2(h[i].x > 0 ? 1.0 / std::sqrt(h[i].x) : 0.0, 0.0);
@@ -585,7 +609,7 @@ double shifted_solve_impl(qcd_ctx* ctx, int nrhs, const double2* b, double2* x, 
     void* tl = ctx->buf("ss.tl", n * nrhs * esz(prec));
     double2* nr = (double2*)ctx->buf("ss.nr", 2 * nrhs * sizeof(double2));
     double2* part = (double2*)ctx->buf("ss.part", (size_t)2 * nrhs * 64 * sizeof(double2));
-    blas_multidot(QCD_FP64, b, 1, n * nrhs, b, nrhs, n, nr, part, ctx->st);
+    blas_multidot(QCD_FP64, b, 1, n * nrhs, b, nrhs, n, nr, part, ctx->dot_counters(nrhs), ctx->st);
     std::vector<double> bn(nrhs);
     {
         const double2* h = ctx->fetch(nr, nrhs);
@@ -601,7 +625,7 @@ double shifted_solve_impl(qcd_ctx* ctx, int nrhs, const double2* b, double2* x, 
     std::vector<double> relres(nrhs, 1.0);
     for (; refine < max_refine; ++refine) {
         // current residuals
-        blas_multidot(QCD_FP64, r, 1, n * nrhs, r, nrhs, n, nr, part, ctx->st);
+        blas_multidot(QCD_FP64, r, 1, n * nrhs, r, nrhs, n, nr, part, ctx->dot_counters(nrhs), ctx->st);
         const double2* h = ctx->fetch(nr, nrhs);
         worst = 0.0;
         double maxr = 0.0;
@@ -662,28 +686,97 @@ void basis_transform(const double2* In, int m, const double2* C, int p, double2*
     KTimer kt("basis_transform", (double)(m + p) * n * 16, 8.0 * m * p * n, st);
     basis_transform_kernel<<<grid, 256, sm, st>>>(In, m, C, p, Out, n);
 }
-// G[i][m] = d1[i], G[m][i] = conj d1[i]; Hm[i][m] = d2[i]; Hm[m][i] = conj d3[i]  (ld = column stride)
-__global__ void gram_update_kernel(double2* G, double2* Hm, int ld, int m, const double2* d1, const double2* d2,
-                                   const double2* d3) {
+// G[i][m] = d1[i], G[m][i] = conj d1[i]; Hm[i][m] = d2[i]; Hm[m][i] = conj d2[i]  (ld = column stride).
+// H = W^H V = V^H Q V is Hermitian because Q is (Sec. 2), so its new row
+// is the conjugate of its new column.
+__global__ void gram_update_kernel(double2* G, double2* Hm, int ld, int m, const double2* d1, const double2* d2) {
     int i = threadIdx.x;
     if (i > m) return;
     G[(size_t)m * ld + i] = d1[i];
     G[(size_t)i * ld + m] = conj(d1[i]);
     Hm[(size_t)m * ld + i] = d2[i];
-    Hm[(size_t)i * ld + m] = conj(d3[i]);
+    Hm[(size_t)i * ld + m] = conj(d2[i]);
 }
 __global__ void gather_columns_kernel(const double2* S, int m, const int* idx, int p, double2* out) {
     for (int e = threadIdx.x; e < m * p; e += blockDim.x) out[e] = S[(size_t)idx[e / m] * m + e % m];
 }
-__global__ void normalize_vec_kernel(double2* s, int m) {
-    __shared__ double nn;
+// Deflation of a converged direction s (a column of S, m entries) by the
+// Householder reflector Hh = I - f w w^H that maps s/||s|| to a multiple of
+// e_0: w = s/||s|| + e^{i arg s_0} e_0, f = 2 / (w^H w).  Columns 1..m-1 of
+// Hh are orthonormal and orthogonal to s.  Writes w to hw[0..m) and f to
+// hw[m].x.
+__global__ void householder_vector_kernel(const double2* __restrict__ s, int m, double2* __restrict__ hw) {
+    __shared__ double nn, ww;
     if (threadIdx.x == 0) {
         double a = 0;
         for (int i = 0; i < m; ++i) a += s[i].x * s[i].x + s[i].y * s[i].y;
         nn = a > 0 ? 1.0 / sqrt(a) : 0.0;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = nn * s[i];
+    if (threadIdx.x == 0) {
+        const double2 s0 = nn * s[0];
+        const double a0 = sqrt(s0.x * s0.x + s0.y * s0.y);
+        const double2 ph = a0 > 0 ? (1.0 / a0) * s0 : make_double2(1, 0);
+        // w^H w = 2 (1 + |s_0|) for unit s
+        ww = 2.0 * (1.0 + a0);
+        hw[0] = s0 + ph;
+    }
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) hw[i] = nn * s[i];
+    __syncthreads();
+    if (threadIdx.x == 0) hw[m] = make_double2(2.0 / ww, 0.0);
+}
+// Out[:, j-1] = In[:, j] - f conj(w_j) (In w) for j = 1..m-1, i.e. In Hh
+// without its first column; the pair (V, W) is selected by blockIdx.y.
+// Row k of In w depends on row k of In only, so each thread finishes its
+// rows in place: it reads In[j][k] before it writes position j-1.
+__global__ void householder_deflate_kernel(double2* __restrict__ A0, double2* __restrict__ A1, int m, size_t n,
+                                           const double2* __restrict__ hw) {
+    __shared__ double2 w[kMaxKry + 1];
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) w[i] = hw[i];
+    __syncthreads();
+    double2* A = blockIdx.y ? A1 : A0;
+    const double f = w[m].x;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        double2 y = make_double2(0, 0);
+        for (int i = 0; i < m; ++i) y += w[i] * A[(size_t)i * n + k];
+        y = f * y;
+        for (int j = 1; j < m; ++j) A[(size_t)(j - 1) * n + k] = A[(size_t)j * n + k] - conj(w[j]) * y;
+    }
+}
+// out = Hh M Hh restricted to rows and columns 1..m-1 (M: G or H, ld = ld):
+//   out[i-1][j-1] = M_ij - f w_i conj(b_j) - f a_i conj(w_j) + f^2 g w_i conj(w_j)
+// with a = M w, b = M^H w, g = w^H M w.  blockIdx.x selects (G, Gt) or (H, Ht).
+__global__ void householder_gram_kernel(const double2* __restrict__ G, double2* __restrict__ Gt,
+                                        const double2* __restrict__ Hm, double2* __restrict__ Hmt, int m, int ld,
+                                        const double2* __restrict__ hw) {
+    __shared__ double2 w[kMaxKry + 1], a[kMaxKry], b[kMaxKry];
+    __shared__ double2 g;
+    const double2* M = blockIdx.x ? Hm : G;
+    double2* out = blockIdx.x ? Hmt : Gt;
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) w[i] = hw[i];
+    __syncthreads();
+    const double f = w[m].x;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double2 ai = make_double2(0, 0), bi = make_double2(0, 0);
+        for (int k = 0; k < m; ++k) {
+            ai += M[(size_t)k * ld + i] * w[k];
+            bi += conj(M[(size_t)i * ld + k]) * w[k];
+        }
+        a[i] = ai;
+        b[i] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 acc = make_double2(0, 0);
+        for (int i = 0; i < m; ++i) acc += conj(w[i]) * a[i];
+        g = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (m - 1) * (m - 1); e += blockDim.x) {
+        const int i = 1 + e % (m - 1), j = 1 + e / (m - 1);
+        out[(size_t)(j - 1) * ld + (i - 1)] = M[(size_t)j * ld + i] - f * (w[i] * conj(b[j])) -
+                                               f * (a[i] * conj(w[j])) + (f * f) * (g * (w[i] * conj(w[j])));
+    }
 }
 
 struct GD {
@@ -692,9 +785,12 @@ struct GD {
     int mcap, kcap;
     double2 *V, *W, *Vt, *Wt, *X, *G, *Hm, *Gt, *Hmt, *S, *work, *C, *dots, *part, *u, *Qu, *R, *T, *tmp;
     double* mu;
+    double* mu_ref;   // refined eigenvalues of the targets
     int* status;
     int* idx;
     int m = 0;        // current basis size
+    int m_fact = 0;   // leading rows of the factored pencil state still valid
+    double2* hstate = nullptr;   // L^-1, L^-1 H L^-H of the pencil (ld = mcap) and its FP32 eigenvectors
     int nlock = 0;
     std::vector<double> lam, lres;
 
@@ -712,46 +808,72 @@ struct GD {
         part = B("part", (size_t)(mcap + kcap + 8) * 64);
         u = B("u", n); Qu = B("Qu", n); R = B("R", (size_t)block * n); T = B("T", (size_t)block * n); tmp = B("tmp", n);
         mu = (double*)ctx->buf("gd.mu", mcap * sizeof(double));
+        mu_ref = (double*)ctx->buf("gd.mu_ref", mcap * sizeof(double));
         status = (int*)ctx->buf("gd.status", 4 * sizeof(int));
         idx = (int*)ctx->buf("gd.idx", mcap * sizeof(int));
+        hstate = B("hstate", (size_t)3 * mcap * mcap);
+        m_fact = 0;
         CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), ctx->st));
     }
     void applyQ(const double2* in, double2* out) {
         double z = 0.0;
         apply_op(ctx->f, QCD_FP64, QCD_OP_Q, 1, in, out, &z, ctx->st);
     }
-    // t orthogonalised against V and X (CGS twice), normalised into V[m]; W[m] = Q V[m]
-    bool add_vector(double2* t) {
+    // t orthogonalised against [V X] by classical Gram-Schmidt, normalised
+    // into V[m]; W[m] = Q V[m].  The second pass runs only when the first one
+    // removed more than half of |t|^2 (|t1| < |t| / sqrt 2, the Kahan-Parlett
+    // criterion); |t1|^2 = |t|^2 - |[V X]^H t|^2 otherwise gives the norm
+    // without another pass.
+    bool add_vector(const double2* t) {
         cudaStream_t st = ctx->st;
-        for (int pass = 0; pass < 2; ++pass) {
+        double2* v = V + (size_t)m * n;
+        double2* dx = dots + m + 1;
+        blas_copy(QCD_FP64, t, v, n, st);
+        blas_multidot(QCD_FP64, V, m + 1, n, v, 1, n, dots, part, ctx->dot_counters(m + 1), st);
+        if (nlock > 0) blas_multidot(QCD_FP64, X, nlock, n, v, 1, n, dx, part, ctx->dot_counters(nlock), st);
+        if (m > 0) blas_multiaxpy(QCD_FP64, V, m, n, dots, -1.0, v, 1, n, st);
+        if (nlock > 0) blas_multiaxpy(QCD_FP64, X, nlock, n, dx, -1.0, v, 1, n, st);
+        const double2* h = ctx->fetch(dots, m + 1 + nlock);
+        const double t0 = h[m].x;
+        double c2 = 0.0;
+        for (int i = 0; i < m + 1 + nlock; ++i)
+            if (i != m) c2 += h[i].x * h[i].x + h[i].y * h[i].y;
+        double nt2 = t0 - c2;
+        if (!(nt2 >= 0.5 * t0)) {
             if (m > 0) {
-                blas_multidot(QCD_FP64, V, m, n, t, 1, n, dots, part, st);
-                blas_multiaxpy(QCD_FP64, V, m, n, dots, -1.0, t, 1, n, st);
+                blas_multidot(QCD_FP64, V, m, n, v, 1, n, dots, part, ctx->dot_counters(m), st);
+                blas_multiaxpy(QCD_FP64, V, m, n, dots, -1.0, v, 1, n, st);
             }
             if (nlock > 0) {
-                blas_multidot(QCD_FP64, X, nlock, n, t, 1, n, dots, part, st);
-                blas_multiaxpy(QCD_FP64, X, nlock, n, dots, -1.0, t, 1, n, st);
+                blas_multidot(QCD_FP64, X, nlock, n, v, 1, n, dots, part, ctx->dot_counters(nlock), st);
+                blas_multiaxpy(QCD_FP64, X, nlock, n, dots, -1.0, v, 1, n, st);
             }
+            blas_multidot(QCD_FP64, v, 1, n, v, 1, n, dots, part, ctx->dot_counters(1), st);
+            nt2 = ctx->fetch(dots, 1)[0].x;
         }
-        blas_multidot(QCD_FP64, t, 1, n, t, 1, n, dots, part, st);
-        const double2* h = ctx->fetch(dots, 1);
-        double nt = std::sqrt(std::max(h[0].x, 0.0));
+        const double nt = std::sqrt(std::max(nt2, 0.0));
         if (!(nt > 1e-12) || !std::isfinite(nt)) return false;
-        blas_axpby(QCD_FP64, make_double2(1.0 / nt, 0), t, make_double2(0, 0), V + (size_t)m * n, n, st);
-        applyQ(V + (size_t)m * n, W + (size_t)m * n);
+        blas_axpby(QCD_FP64, make_double2(0, 0), v, make_double2(1.0 / nt, 0), v, n, st);
+        applyQ(v, W + (size_t)m * n);
         // new Gram column / row
-        blas_multidot(QCD_FP64, W, m + 1, n, W + (size_t)m * n, 1, n, dots, part, st);
-        blas_multidot(QCD_FP64, W, m + 1, n, V + (size_t)m * n, 1, n, dots + mcap, part, st);
-        blas_multidot(QCD_FP64, V, m + 1, n, W + (size_t)m * n, 1, n, dots + 2 * mcap, part, st);
+        blas_multidot(QCD_FP64, W, m + 1, n, W + (size_t)m * n, 1, n, dots, part, ctx->dot_counters(m + 1), st);
+        blas_multidot(QCD_FP64, W, m + 1, n, v, 1, n, dots + mcap, part, ctx->dot_counters(m + 1), st);
         KTimer kt("gram_update", 0.0, 0.0, st);
-        gram_update_kernel<<<1, 64, 0, st>>>(G, Hm, mcap, m, dots, dots + mcap, dots + 2 * mcap);
+        gram_update_kernel<<<1, 64, 0, st>>>(G, Hm, mcap, m, dots, dots + mcap);
         check_launch("add_vector");
         ++m;
         return true;
     }
+    // appends the converged unit vector u to X
+    void lock_vector(const double2* uv) {
+        blas_copy(QCD_FP64, uv, X + (size_t)nlock * n, n, ctx->st);
+        ++nlock;
+    }
     // harmonic Ritz pairs of the current basis; returns theta sorted by |theta| with the column index
     void harmonic(std::vector<double>& theta, std::vector<int>& col) {
-        small_harmonic_eig(G, Hm, m, mcap, mu, S, work, status, ctx->st);
+        if (m_fact > m) m_fact = 0;
+        small_harmonic_eig_inc(G, Hm, m, mcap, m_fact, mu, S, hstate, status, ctx->st);
+        m_fact = m;
         check_launch("harmonic eig");
         double* hm = (double*)ctx->host(m);
         CK(cudaMemcpyAsync(hm, mu, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
@@ -784,6 +906,29 @@ struct GD {
         std::swap(Hm, Hmt);
         check_launch("basis transform");
         m = p;
+        m_fact = 0;   // the pencil changed as a whole
+    }
+    // lock-time deflation V <- V Hh[:, 1:], W <- W Hh[:, 1:] and the Gram
+    // matrices accordingly, for the Householder reflector Hh of the column
+    // s (device, m entries): a rank-one update instead of an m x (m-1) product
+    void deflate(const double2* s) {
+        cudaStream_t st = ctx->st;
+        double2* hw = work;   // m + 1 entries
+        {
+            KTimer kt("householder", 0.0, 0.0, st);
+            householder_vector_kernel<<<1, 64, 0, st>>>(s, m, hw);
+            householder_gram_kernel<<<2, 256, 0, st>>>(G, Gt, Hm, Hmt, m, mcap, hw);
+        }
+        {
+            const int gx = (int)std::min<size_t>((n + 255) / 256, 1216);
+            KTimer kt("householder_deflate", (double)(4 * m - 2) * n * 16, 16.0 * m * n * 2, st);
+            householder_deflate_kernel<<<dim3(gx, 2), 256, 0, st>>>(V, W, m, n, hw);
+        }
+        std::swap(G, Gt);
+        std::swap(Hm, Hmt);
+        check_launch("deflate");
+        --m;
+        m_fact = 0;
     }
 };
 
@@ -863,11 +1008,11 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                 std::vector<int> cols(tg.size());
                 for (size_t q = 0; q < tg.size(); ++q) cols[q] = col[tg[q]];
                 CK(cudaMemcpyAsync(gd.idx, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-                small_refine_targets(gd.G, gd.Hm, gd.m, gd.mcap, gd.S, gd.mu, gd.idx, (int)cols.size(), gd.work, st);
-                double* hm = (double*)ctx->host(gd.m);
-                CK(cudaMemcpyAsync(hm, gd.mu, gd.m * sizeof(double), cudaMemcpyDeviceToHost, st));
+                small_refine_targets(gd.hstate, gd.m, gd.mcap, gd.S, gd.mu, gd.mu_ref, gd.idx, (int)cols.size(), st);
+                double* hm = (double*)ctx->host(cols.size());
+                CK(cudaMemcpyAsync(hm, gd.mu_ref, cols.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
-                for (size_t q = 0; q < tg.size(); ++q) theta[tg[q]] = hm[cols[q]] != 0.0 ? 1.0 / hm[cols[q]] : INFINITY;
+                for (size_t q = 0; q < tg.size(); ++q) theta[tg[q]] = hm[q] != 0.0 ? 1.0 / hm[q] : INFINITY;
             }
             bool locked = false;
             tsel.clear();
@@ -878,8 +1023,8 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                 blas_zero(QCD_FP64, gd.Qu, n, st);
                 blas_multiaxpy(QCD_FP64, gd.V, gd.m, n, s, 1.0, gd.u, 1, n, st);
                 blas_multiaxpy(QCD_FP64, gd.W, gd.m, n, s, 1.0, gd.Qu, 1, n, st);
-                blas_multidot(QCD_FP64, gd.u, 1, n, gd.u, 1, n, gd.dots, gd.part, st);
-                blas_multidot(QCD_FP64, gd.u, 1, n, gd.Qu, 1, n, gd.dots + 1, gd.part, st);
+                blas_multidot(QCD_FP64, gd.u, 1, n, gd.u, 1, n, gd.dots, gd.part, gd.ctx->dot_counters(1), st);
+                blas_multidot(QCD_FP64, gd.u, 1, n, gd.Qu, 1, n, gd.dots + 1, gd.part, gd.ctx->dot_counters(1), st);
                 const double2* h = ctx->fetch(gd.dots, 2);
                 const double uu = h[0].x;
                 const double rho = h[1].x / uu;
@@ -889,23 +1034,16 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                 blas_copy(QCD_FP64, gd.Qu, rj, n, st);
                 blas_axpby(QCD_FP64, make_double2(-rho * iu, 0), gd.u, make_double2(iu, 0), rj, n, st);
                 blas_axpby(QCD_FP64, make_double2(0, 0), gd.u, make_double2(iu, 0), gd.u, n, st);
-                blas_multidot(QCD_FP64, rj, 1, n, rj, 1, n, gd.dots, gd.part, st);
+                blas_multidot(QCD_FP64, rj, 1, n, rj, 1, n, gd.dots, gd.part, gd.ctx->dot_counters(1), st);
                 const double2* hr = ctx->fetch(gd.dots, 1);
                 const double rn = std::sqrt(std::max(hr[0].x, 0.0));
                 if (rn <= tol) {
                     if (gd.nlock >= gd.kcap) throw QcdError(QCD_EINVAL, "too many locked vectors");
-                    blas_copy(QCD_FP64, gd.u, gd.X + (size_t)gd.nlock * n, n, st);
+                    gd.lock_vector(gd.u);
                     gd.lam.push_back(rho);
                     gd.lres.push_back(rn);
-                    ++gd.nlock;
                     // deflate: V <- V C with C the complement of s/||s||
-                    CK(cudaMemcpyAsync(gd.work, s, gd.m * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-                    {
-                        KTimer kt("normalize_vec", 0.0, 0.0, st);
-                        normalize_vec_kernel<<<1, 64, 0, st>>>(gd.work, gd.m);
-                    }
-                    small_complement(gd.work, gd.m, gd.C, nullptr, st);
-                    gd.transform(gd.C, gd.m - 1);
+                    gd.deflate(s);
                     ++locks_since_update;
                     locked = true;
                     if (P.verbose)

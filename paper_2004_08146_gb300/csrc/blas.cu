@@ -31,6 +31,7 @@ __global__ void convert_kernel(const Zi* __restrict__ x, Zo* __restrict__ y, siz
 template <typename Z>
 __global__ void multidot_partial_kernel(const Z* __restrict__ X, size_t xstride_vec, const Z* __restrict__ w,
                                         int nrhs, size_t n, int nsplit, double2* __restrict__ partial,
+                                        unsigned* __restrict__ counters, double2* __restrict__ dots,
                                         const int* __restrict__ act) {
     const int v = blockIdx.y;            // v = i * nrhs + j
     const int i = v / nrhs, j = v % nrhs;
@@ -63,13 +64,28 @@ __global__ void multidot_partial_kernel(const Z* __restrict__ X, size_t xstride_
         im = warp_sum(im);
         if (lane == 0) partial[(size_t)v * nsplit + blockIdx.x] = make_double2(re, im);
     }
-}
-__global__ void multidot_final_kernel(const double2* __restrict__ partial, int nsplit, int nv, double2* dots) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    double2 s = make_double2(0, 0);
-    for (int k = 0; k < nsplit; ++k) s += partial[(size_t)v * nsplit + k];
-    dots[v] = s;
+    // the last CTA of dot v to finish adds the nsplit partials in a fixed
+    // order and re-arms counters[v] (zero between launches)
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&counters[v], 1u) == (unsigned)nsplit - 1;
+    }
+    __syncthreads();
+    if (!last || wid != 0) return;
+    __threadfence();
+    double sr = 0.0, si = 0.0;
+    for (int k = lane; k < nsplit; k += 32) {
+        const double2 q = __ldcg(&partial[(size_t)v * nsplit + k]);
+        sr += q.x;
+        si += q.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) {
+        dots[v] = make_double2(sr, si);
+        counters[v] = 0u;
+    }
 }
 
 constexpr int kAxpyCoef = 2048;   // coefficients staged per CTA (nvec * nrhs)
@@ -181,7 +197,7 @@ void blas_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, c
         convert_kernel<float2, double2><<<grid_for(n), kThreads, 0, st>>>((const float2*)x, (double2*)y, n);
 }
 void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const void* w, int nrhs, size_t n,
-                   double2* dots, double2* partial, cudaStream_t st, const int* act) {
+                   double2* dots, double2* partial, unsigned* counters, cudaStream_t st, const int* act) {
     if (nvec <= 0) return;
     // enough CTAs to fill the GPU (about 4 per SM), at least 2048 elements each
     int nsplit = 608 / (nvec * nrhs);
@@ -193,13 +209,10 @@ void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const 
               8.0 * nvec * nrhs * n, st);
     if (prec == QCD_FP64)
         multidot_partial_kernel<double2><<<grid, kThreads, 0, st>>>((const double2*)X, xstride_vec, (const double2*)w,
-                                                                   nrhs, n, nsplit, partial, act);
+                                                                   nrhs, n, nsplit, partial, counters, dots, act);
     else
         multidot_partial_kernel<float2><<<grid, kThreads, 0, st>>>((const float2*)X, xstride_vec, (const float2*)w,
-                                                                  nrhs, n, nsplit, partial, act);
-    int nv = nvec * nrhs;
-    KTimer kt2("multidot_final", 0.0, 0.0, st);
-    multidot_final_kernel<<<(nv + 127) / 128, 128, 0, st>>>(partial, nsplit, nv, dots);
+                                                                  nrhs, n, nsplit, partial, counters, dots, act);
 }
 void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const double2* c, double sign, void* w,
                     int nrhs, size_t n, cudaStream_t st, const int* act) {

@@ -100,9 +100,13 @@ void residual_op(const FineOp& f, int prec, int op, int nrhs, const void* b, con
 void blas_zero(int prec, void* x, size_t n, cudaStream_t st);
 void blas_copy(int prec, const void* x, void* y, size_t n, cudaStream_t st);
 void blas_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, cudaStream_t st);
-// dots[i*nrhs + j] = <X[i][j], w[j]> for i < nvec (FP64 results, device)
+// dots[i*nrhs + j] = <X[i][j], w[j]> for i < nvec (FP64 results, device).
+// partial: >= 64 * nvec * nrhs double2 of scratch; counters: >= nvec * nrhs
+// unsigned that are zero on entry and are left zero (one launch: the last
+// CTA of each dot adds the partial sums).
 void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const void* w, int nrhs,
-                   size_t n, double2* dots, double2* partial, cudaStream_t st, const int* act = nullptr);
+                   size_t n, double2* dots, double2* partial, unsigned* counters, cudaStream_t st,
+                   const int* act = nullptr);
 // w[j] += sign * sum_i c[i*nrhs + j] X[i][j]
 void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const double2* c, double sign,
                     void* w, int nrhs, size_t n, cudaStream_t st, const int* act = nullptr);
@@ -172,17 +176,19 @@ int coarse_gmres(const Coarse& c, int prec, int op, int nrhs, const void* b, voi
 // ------------------------------------------------------------------ kernels (eig.cu)
 // Harmonic Ritz pairs of the pencil G s = theta H s (G = W^H W, H = W^H V):
 // returns mu = 1/theta and S (column-major m x m) in device buffers.
-void small_harmonic_eig(const double2* G, const double2* H, int m, int ld, double* mu, double2* S,
-                        double2* work, int* status, cudaStream_t st);
-// FP64 refinement of the targeted pairs (columns idx[0..nb) of S, entries
-// of mu) by inverse iteration on the pencil; work >= nb * m * m double2.
-void small_refine_targets(const double2* G, const double2* H, int m, int ld, double2* S, double* mu, const int* idx,
-                          int nb, double2* work, cudaStream_t st);
+// L^-1 and L^-1 H L^-H (G = L L^H) are kept in `state` (3 * ld * ld double2:
+// those two and the FP32 eigenvectors of the latter) between calls: rows
+// m0..m-1 are appended, m0 = 0 recomputes.
+void small_harmonic_eig_inc(const double2* G, const double2* H, int m, int ld, int m0, double* mu, double2* S,
+                            double2* state, int* status, cudaStream_t st);
+// FP64 refinement of the targeted pairs (columns idx[0..nb) of S; their
+// eigenvalues go to mu_out[0..nb)) from the state left by
+// small_harmonic_eig_inc.
+void small_refine_targets(const double2* state, int m, int ld, double2* S, const double* mu, double* mu_out,
+                          const int* idx, int nb, cudaStream_t st);
 // Orthonormal Q (m x k, column-major, leading dim m) of the columns of S
 // (m x k, leading dimension lds) by modified Gram-Schmidt applied twice.
 void small_qr(const double2* S, int m, int k, int lds, double2* Q, double2* work, cudaStream_t st);
-// Orthonormal complement (m x (m-1)) of a unit vector s of length m.
-void small_complement(const double2* s, int m, double2* C, double2* work, cudaStream_t st);
 // C (m x p) = A^H B for small column-major matrices: used for Gram updates
 void small_gram_transform(const double2* M, int m, int ldm, const double2* C, int p, double2* out,
                           int ldo, double2* work, cudaStream_t st);

@@ -158,17 +158,48 @@ __device__ __forceinline__ void hop_dispatch(int mu, const Spinor<double>& psi, 
     }
 }
 
-__global__ void build_coarse_kernel(Geom g, Blocking B, int nv, const double2* __restrict__ U, const double* __restrict__ A,
-                                    const double2* __restrict__ P, double2* __restrict__ Ac) {
-    extern __shared__ double2 hsm[];   // [bs][12]
+// Sites of block blk that direction d draws from: all bs for d = 0, the
+// sites on the face towards block blk + d otherwise (none when the block grid
+// has extent 1 in that direction, whose hops wrap into d = 0).
+__device__ __forceinline__ bool coarse_active(const Blocking& B, int d, const int o[4]) {
+    if (d == 0) return true;
+    const bool fw = d <= 4;
+    const int mu = (d - 1) % 4;
+    return (fw ? o[mu] == B.b[mu] - 1 : o[mu] == 0) && B.cd[mu] > 1;
+}
+
+// Columns col0 .. col0+nch-1 at a time: every thread takes (column, active
+// site) tasks and leaves h in shared memory ([column][active site][12]);
+// then one warp per (column, row) entry forms P_blk[row]^H h over the active
+// sites only.
+__global__ void __launch_bounds__(256) build_coarse_kernel(Geom g, Blocking B, int nv, const double2* __restrict__ U,
+                                                          const double* __restrict__ A, const double2* __restrict__ P,
+                                                          double2* __restrict__ Ac, int chunk) {
+    extern __shared__ double2 hsm[];   // [chunk][na][12], then na ints
+    int* lst = reinterpret_cast<int*>(hsm + (size_t)chunk * B.bs * 12);
+    __shared__ int na_s;
     const int blk = blockIdx.x, d = blockIdx.y;
     const int nc = 2 * nv, nloc = B.bs * 6;
     int cb[4];
     block_coords(B, blk, cb);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    for (int col = 0; col < nc; ++col) {
-        const int chic = col / nv, ic = col % nv;
-        for (int l = threadIdx.x; l < B.bs; l += blockDim.x) {
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int l = 0; l < B.bs; ++l) {
+            int o[4];
+            local_coords(B, l, o);
+            if (coarse_active(B, d, o)) lst[c++] = l;
+        }
+        na_s = c;
+    }
+    __syncthreads();
+    const int na = na_s;
+    for (int col0 = 0; col0 < nc; col0 += chunk) {
+        const int nch = min(chunk, nc - col0);
+        for (int t = threadIdx.x; t < nch * na; t += blockDim.x) {
+            const int cc = t / na, a = t % na;
+            const int col = col0 + cc, l = lst[a];
+            const int chic = col / nv, ic = col % nv;
             int o[4], x[4];
             local_coords(B, l, o);
             for (int mu = 0; mu < 4; ++mu) x[mu] = cb[mu] * B.b[mu] + o[mu];
@@ -188,7 +219,7 @@ __global__ void build_coarse_kernel(Geom g, Blocking B, int nv, const double2* _
                     const int want = face ? (fw ? 1 + mu : 5 + mu) : 0;
                     if (want != d) continue;
                     int neg;
-                    int yn = fw ? nb_fwd(g, x, y, mu, neg) : nb_bwd(g, x, y, mu, neg);
+                    const int yn = fw ? nb_fwd(g, x, y, mu, neg) : nb_bwd(g, x, y, mu, neg);
                     int xn[4];
                     site_coords(g, yn, xn);
                     int cn[4], on[4];
@@ -201,23 +232,26 @@ __global__ void build_coarse_kernel(Geom g, Blocking B, int nv, const double2* _
                     else hop_dispatch<false>(mu, ps, u, neg ? -1.0 : 1.0, acc);
                 }
             }
+            double2* h = hsm + ((size_t)cc * na + a) * 12;
 #pragma unroll
-            for (int k = 0; k < 12; ++k) hsm[l * 12 + k] = acc.c[k];
+            for (int k = 0; k < 12; ++k) h[k] = acc.c[k];
         }
         __syncthreads();
-        for (int row = warp; row < nc; row += nwarps) {
+        for (int e = warp; e < nch * nc; e += nwarps) {
+            const int cc = e / nc, row = e % nc;
             const int chir = row / nv, ir = row % nv;
             const double2* pr = P + (((size_t)blk * 2 + chir) * nv + ir) * nloc;
+            const double2* h = hsm + (size_t)cc * na * 12 + 6 * chir;
             double re = 0, im = 0;
-            for (int e = lane; e < nloc; e += 32) {
-                int l = e / 6, sc = e % 6;
-                double2 a = pr[e], h = hsm[l * 12 + 6 * chir + sc];
-                re += a.x * h.x + a.y * h.y;
-                im += a.x * h.y - a.y * h.x;
+            for (int q = lane; q < na * 6; q += 32) {
+                const int a = q / 6, sc = q % 6;
+                const double2 pv = pr[lst[a] * 6 + sc], hv = h[a * 12 + sc];
+                re += pv.x * hv.x + pv.y * hv.y;
+                im += pv.x * hv.y - pv.y * hv.x;
             }
             re = warp_sum(re);
             im = warp_sum(im);
-            if (lane == 0) Ac[(((size_t)blk * 9 + d) * nc + col) * nc + row] = make_double2(re, im);
+            if (lane == 0) Ac[(((size_t)blk * 9 + d) * nc + col0 + cc) * nc + row] = make_double2(re, im);
         }
         __syncthreads();
     }
@@ -690,10 +724,13 @@ void mg_build_P(const FineOp& f, Coarse& c, const double2* vecs, int nvec, cudaS
 
 void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st) {
     dim3 grid(c.B.nb, 9);
-    size_t sm = (size_t)c.B.bs * 12 * sizeof(double2);
+    // columns per pass: h of a pass within about 96 KB of shared memory
+    const size_t per_col = (size_t)c.B.bs * 12 * sizeof(double2);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(c.nc, (96u << 10) / per_col));
+    const size_t sm = chunk * per_col + (size_t)c.B.bs * sizeof(int);
     if (sm > 48 * 1024) cudaFuncSetAttribute(build_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     KTimer kt("build_coarse", 0.0, 0.0, st);
-    build_coarse_kernel<<<grid, 256, sm, st>>>(f.g, c.B, c.nv, f.U64, f.A64, c.P64, c.A64);
+    build_coarse_kernel<<<grid, 256, sm, st>>>(f.g, c.B, c.nv, f.U64, f.A64, c.P64, c.A64, chunk);
     size_t n = (size_t)c.B.nb * 9 * c.nc * c.nc;
     KTimer kt2("narrow", (double)n * 24, 0.0, st);
     narrow_kernel<<<grid_for(n), 256, 0, st>>>(c.A64, c.A32, n);
