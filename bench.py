@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-stencil", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--k", type=int, default=None,
+                    help="eigenpairs per step instead of the workload's (short profiling runs)")
     return ap.parse_args()
 
 
@@ -60,6 +63,13 @@ def max_over_ranks(value, device=None):
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of each kernel as it stands now, for the roofline's "traffic";
+# profiles/sap_warp_f32_c2_16x8c3.md gives the capture.  A kernel that changes
+# is taken out of this table until it is captured again.
+NCU_TRAFFIC = {"sap_block_f32": 4780032}
 
 
 def measured_peaks():
@@ -161,6 +171,8 @@ def run_reference(args):
         return
     from paper_2004_08146_gb300 import workloads
     w = workloads.get(args.workload)
+    if args.k is not None:
+        w["k"] = args.k
     # outer-iteration count of the method on this workload (from a GPU run of
     # the same configuration); without one the paper's ~10 outer per pair
     outer = int(os.environ.get("QCD_REF_OUTER", str(10 * w["k"] // 2)))
@@ -195,6 +207,8 @@ def main():
     torch.cuda.set_device(local)
     devn = torch.device("cuda", local)
     w = workloads.get(args.workload)
+    if args.k is not None:
+        w["k"] = args.k
     dims = tuple(w["dims"])
     U = synth.gauge_field(dims, w["eps"], w["seed"])
     n = int(np.prod(dims)) * 12
@@ -226,15 +240,22 @@ def main():
         if ws > 1:
             dist.barrier()
         ms = []
-        for _ in range(K):
+        for i in range(K):
+            # the last timed step is the profiler range (ncu --profile-from-start off)
+            last = profile and i == K - 1
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)            # evict L2 between steps (outside the timed interval)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            if last:
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()
             e0.record(stream)
             lam, info = step(ctx)
             e1.record(stream)
             e1.synchronize()
+            if last:
+                torch.cuda.profiler.stop()
             ms.append(e0.elapsed_time(e1))
             infos.append(info)
         torch.cuda.synchronize()
@@ -253,7 +274,7 @@ def main():
     clocks = ClockSampler(local)
     qcd.qcd_stats_reset(2, dom["name"])
     clocks.start()
-    ms, infos, lam = timed_steps(ctx, args.steps, max(0, args.warmup - 2))
+    ms, infos, lam = timed_steps(ctx, args.steps, max(0, args.warmup - 2), profile=True)
     clk = clocks.stop()
     st_timed = {s["name"]: s for s in qcd.qcd_stats_read()}
     qcd.qcd_stats_reset(0)
@@ -276,22 +297,24 @@ def main():
         ctx64.close()
 
     # ---- end to end through the C ABI from host buffers
-    ctx_e = qcd.Context(params=qcd.default_params(precision=qcd.QCD_MIXED, use_mg=w["use_mg"], sap_block=w["sap"]),
-                        stream=sp)
-    Vh = torch.empty(w["k"] * n, dtype=torch.complex128).pin_memory()
-    e2e = []
-    for i in range(1 + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx_e.qcd_set_gauge(U, dims, w["m0"], w["csw"])
-        step(ctx_e)
-        Vh.copy_(V, non_blocking=True)
-        torch.cuda.current_stream(devn).synchronize()
-        stream.synchronize()
-        if i > 0:
-            e2e.append(time.perf_counter() - t0)
-    ctx_e.close()
-    e2e_s = float(np.mean(e2e))
+    e2e_s = None
+    if not args.no_e2e:
+        ctx_e = qcd.Context(params=qcd.default_params(precision=qcd.QCD_MIXED, use_mg=w["use_mg"], sap_block=w["sap"]),
+                            stream=sp)
+        Vh = torch.empty(w["k"] * n, dtype=torch.complex128).pin_memory()
+        e2e = []
+        for i in range(1 + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx_e.qcd_set_gauge(U, dims, w["m0"], w["csw"])
+            step(ctx_e)
+            Vh.copy_(V, non_blocking=True)
+            torch.cuda.current_stream(devn).synchronize()
+            stream.synchronize()
+            if i > 0:
+                e2e.append(time.perf_counter() - t0)
+        ctx_e.close()
+        e2e_s = float(np.mean(e2e))
 
     # ---- fine-stencil bandwidth, 64 x 32^3 (inputs far larger than L2)
     stencil = None
@@ -313,12 +336,12 @@ def main():
                        "precision": "FP32 inner / FP64 outer", "tol": 1e-8, "m0": w["m0"], "csw": w["csw"],
                        "eps": w["eps"], "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{ws}"},
-            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(U.nbytes),
-                    "d2h_bytes_per_step": int(V.numel() * 16 + 8 * w["k"])},
+            "e2e": None if e2e_s is None else {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(U.nbytes),
+                                               "d2h_bytes_per_step": int(V.numel() * 16 + 8 * w["k"])},
             "gpu_launches": launches_timed,
             "roofline": {"kernel": dom["name"], "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": None, "launches_timed": d["timed"],
+                         "traffic": NCU_TRAFFIC.get(dom["name"]), "launches_timed": d["timed"],
                          "avg_launch_us": d["total_ms"] * 1e3 / max(1, d["timed"]),
                          "share_of_step": d["total_ms"] / (sum(ms) * n_steps_in_window / args.steps)},
             "eig": {"outer": info.outer, "inner": info.inner, "locked": info.locked, "updates": info.updates,
