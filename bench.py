@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-stencil", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only-stencil", action="store_true",
+                    help="run and print only the fine-stencil bandwidth measurement")
     ap.add_argument("--k", type=int, default=None,
                     help="eigenpairs per step instead of the workload's (short profiling runs)")
     return ap.parse_args()
@@ -214,6 +216,10 @@ def main():
     n = int(np.prod(dims)) * 12
     stream = torch.cuda.Stream(devn)
     sp = stream.cuda_stream
+    if args.only_stencil:
+        peak, _ = measured_peaks()
+        print(json.dumps({"stencil": stencil_bench(qcd, synth, torch, devn, stream, peak)}), flush=True)
+        return
 
     def make(precision):
         p = qcd.default_params(precision=precision, use_mg=w["use_mg"], sap_block=w["sap"])

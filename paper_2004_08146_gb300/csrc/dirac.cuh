@@ -89,35 +89,13 @@ __device__ __forceinline__ void hop_accumulate(const Spinor<R>& psi, const Link<
     }
 }
 
-// y_chi = A_chi x_chi for the packed Hermitian 6x6 blocks (36 reals each).
+// y = A x for the two packed Hermitian 6x6 chirality blocks (diagonal reals,
+// then the upper triangle as (re, im) pairs in herm_off order)
 template <typename R>
-__device__ __forceinline__ void clover_apply(const R* __restrict__ A, const Spinor<R>& x, Spinor<R>& y) {
+__device__ __forceinline__ void clover_apply_regs(const R* a0, const Spinor<R>& x, Spinor<R>& y) {
 #pragma unroll
     for (int chi = 0; chi < 2; ++chi) {
-        const R* a = A + 36 * chi;
-        const cplx<R>* xs = x.c + 6 * chi;
-        cplx<R>* ys = y.c + 6 * chi;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) ys[i] = __ldg(a + i) * xs[i];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-#pragma unroll
-            for (int j = i + 1; j < 6; ++j) {
-                const int o = herm_off(i, j);
-                cplx<R> aij = mk<R>(__ldg(a + o), __ldg(a + o + 1));
-                ys[i] += aij * xs[j];
-                ys[j] += cmulc(aij, xs[i]);
-            }
-        }
-    }
-}
-
-// Same product with the packed blocks in shared memory.
-template <typename R>
-__device__ __forceinline__ void clover_apply_smem(const R* A, const Spinor<R>& x, Spinor<R>& y) {
-#pragma unroll
-    for (int chi = 0; chi < 2; ++chi) {
-        const R* a = A + 36 * chi;
+        const R* a = a0 + 36 * chi;
         const cplx<R>* xs = x.c + 6 * chi;
         cplx<R>* ys = y.c + 6 * chi;
 #pragma unroll
@@ -135,6 +113,50 @@ __device__ __forceinline__ void clover_apply_smem(const R* A, const Spinor<R>& x
     }
 }
 
+template <typename R>
+__device__ __forceinline__ void clover_apply(const R* __restrict__ A, const Spinor<R>& x, Spinor<R>& y) {
+    // the 72 reals of the site (288 B in FP32, 576 B in FP64; 16-byte aligned)
+    // in 16-byte loads
+    if constexpr (sizeof(R) == 4) {
+        R ar[72];
+        const float4* q = reinterpret_cast<const float4*>(A);
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+            const float4 v = __ldg(q + k);
+            ar[4 * k] = v.x; ar[4 * k + 1] = v.y; ar[4 * k + 2] = v.z; ar[4 * k + 3] = v.w;
+        }
+        clover_apply_regs<R>(ar, x, y);
+    } else {
+        // FP64: (re, im) pairs on demand (all pairs start at even offsets)
+#pragma unroll
+        for (int chi = 0; chi < 2; ++chi) {
+            const double2* q = reinterpret_cast<const double2*>(A + 36 * chi);
+            const cplx<R>* xs = x.c + 6 * chi;
+            cplx<R>* ys = y.c + 6 * chi;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double2 d = __ldg(q + i);
+                ys[2 * i] = d.x * xs[2 * i];
+                ys[2 * i + 1] = d.y * xs[2 * i + 1];
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+#pragma unroll
+                for (int j = i + 1; j < 6; ++j) {
+                    const double2 aij = __ldg(q + herm_off(i, j) / 2);
+                    ys[i] += aij * xs[j];
+                    ys[j] += cmulc(aij, xs[i]);
+                }
+            }
+        }
+    }
+}
+
+// Same product with the packed blocks in shared memory.
+template <typename R>
+__device__ __forceinline__ void clover_apply_smem(const R* A, const Spinor<R>& x, Spinor<R>& y) {
+    clover_apply_regs<R>(A, x, y);
+}
 // neighbour site and boundary sign
 __device__ __forceinline__ int nb_fwd(const Geom& g, const int x[4], int s, int mu, int& sgn_neg) {
     int y[4] = {x[0], x[1], x[2], x[3]};
