@@ -452,8 +452,11 @@ void smooth(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, co
 }
 
 // two-level cycle x = M b (Eq. 2.8, post-smoothing only)
+void ensure_coarse64(qcd_ctx* ctx);
+
 void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau,
                    const int* act = nullptr) {
+    if (prec == QCD_FP64) ensure_coarse64(ctx);
     const Coarse& c = ctx->c;
     const size_t nco = (size_t)c.gc.V * c.nc;
     void* rc = ctx->buf("cyc.rc", nco * nrhs * esz(prec));
@@ -508,6 +511,14 @@ void normalize_set(qcd_ctx* ctx, double2* X, int nvec, size_t n) {
     CK(cudaStreamSynchronize(ctx->st));
 }
 
+// the FP64 coarse operator, rebuilt if only the FP32 one is current
+void ensure_coarse64(qcd_ctx* ctx) {
+    if (ctx->c.a64_stale) {
+        mg_build_coarse(ctx->f, ctx->c, ctx->st, false);
+        check_launch("coarse rebuild");
+    }
+}
+
 void build_from_vectors(qcd_ctx* ctx, const double2* V, int nvec, const int block[4]) {
     Coarse& c = ctx->c;
     Blocking B = make_blocking(ctx->f.g, block);
@@ -532,7 +543,9 @@ void build_from_vectors(qcd_ctx* ctx, const double2* V, int nvec, const int bloc
         CK(cudaMalloc(&c.A32, na * sizeof(float2)));
     }
     mg_build_P(ctx->f, c, V, nvec, ctx->st);
-    mg_build_coarse(ctx->f, c, ctx->st);
+    // a mixed-precision context runs its cycles in FP32: build only that
+    // operator; FP64 users rebuild the FP64 one on demand (ensure_coarse64)
+    mg_build_coarse(ctx->f, c, ctx->st, ctx->p.precision != QCD_FP64);
     check_launch("mg build");
     c.ready = true;
 }
@@ -1361,6 +1374,7 @@ int qcd_coarse_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* x, vo
     return guarded(ctx, [&]() {
         require_mg(ctx);
         if (nrhs < 1 || nrhs > kMaxRhs || !x || !y || !tau) throw QcdError(QCD_EINVAL, "bad arguments");
+        if (prec == QCD_FP64) ensure_coarse64(ctx);
         coarse_apply(ctx->c, prec, op, nrhs, x, y, tau, ctx->st);
         check_launch("coarse apply");
         return QCD_OK;
@@ -1380,6 +1394,7 @@ int qcd_mg_get_P(qcd_ctx* ctx, double* P_host) {
 int qcd_mg_get_coarse(qcd_ctx* ctx, double* A_host) {
     return guarded(ctx, [&]() {
         require_mg(ctx);
+        ensure_coarse64(ctx);
         const int nc = ctx->c.nc;
         size_t na = (size_t)ctx->c.B.nb * 9 * nc * nc;
         std::vector<double2> tmp(na);

@@ -339,36 +339,44 @@ __global__ void __launch_bounds__(64) refine_targets_kernel(const double2* __res
     if (tid == 0) mu_out[blockIdx.x] = rho;
 }
 
-// Q = orthonormal basis of the columns of S (m x k): modified Gram-Schmidt, twice.
+// Q = orthonormal basis of the columns of S (m x k <= 64): column by column,
+// classical Gram-Schmidt twice against the previous columns (all inner
+// products of a pass at once, one warp each), then normalisation.
 __global__ void __launch_bounds__(kT) small_qr_kernel(const double2* __restrict__ S, int m, int k, int lds,
                                                       double2* __restrict__ Q) {
     __shared__ double red[33];
-    __shared__ double2 hsh;
-    const int tid = threadIdx.x;
+    __shared__ double2 h[64];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     for (int e = tid; e < m * k; e += blockDim.x) Q[e] = S[(e / m) * lds + e % m];
     __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int j = 0; j < k; ++j) {
-            double2* qj = Q + (size_t)j * m;
-            for (int i = 0; i < j; ++i) {
+    for (int j = 0; j < k; ++j) {
+        double2* qj = Q + (size_t)j * m;
+        for (int pass = 0; pass < 2 && j > 0; ++pass) {
+            // h_i = q_i^H q_j for all i < j at once, one warp per i
+            for (int i = warp; i < j; i += nwarp) {
                 const double2* qi = Q + (size_t)i * m;
-                double hr = 0, hi = 0;
-                for (int r = tid; r < m; r += blockDim.x) { double2 t = cmulc(qi[r], qj[r]); hr += t.x; hi += t.y; }
-                hr = block_reduce_sum(hr, red);
-                hi = block_reduce_sum(hi, red);
-                if (tid == 0) hsh = make_double2(hr, hi);
-                __syncthreads();
-                double2 h = hsh;
-                for (int r = tid; r < m; r += blockDim.x) qj[r] -= h * qi[r];
-                __syncthreads();
+                double2 acc = make_double2(0, 0);
+                for (int r = lane; r < m; r += 32) acc += cmulc(qi[r], qj[r]);
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                }
+                if (lane == 0) h[i] = acc;
             }
-            double nn = 0;
-            for (int r = tid; r < m; r += blockDim.x) nn += cabs2(qj[r]);
-            nn = block_reduce_sum(nn, red);
-            double inv = nn > 0 ? 1.0 / sqrt(nn) : 0.0;
-            for (int r = tid; r < m; r += blockDim.x) qj[r] = inv * qj[r];
+            __syncthreads();
+            for (int r = tid; r < m; r += blockDim.x) {
+                double2 v = qj[r];
+                for (int i = 0; i < j; ++i) v -= h[i] * Q[(size_t)i * m + r];
+                qj[r] = v;
+            }
             __syncthreads();
         }
+        double nn = 0;
+        for (int r = tid; r < m; r += blockDim.x) nn += cabs2(qj[r]);
+        nn = block_reduce_sum(nn, red);
+        const double inv = nn > 0 ? 1.0 / sqrt(nn) : 0.0;
+        for (int r = tid; r < m; r += blockDim.x) qj[r] = inv * qj[r];
+        __syncthreads();
     }
 }
 

@@ -82,6 +82,7 @@ struct Coarse {
     float2* P32 = nullptr;
     double2* A64 = nullptr;   // [Vc][9][col][row]  (column-major blocks)
     float2* A32 = nullptr;
+    bool a64_stale = false;   // A32 was built in FP32 and A64 is out of date
     bool ready = false;
 };
 
@@ -120,7 +121,7 @@ void blas_axpby(int prec, double2 a, const void* x, double2 b, void* y, size_t n
 
 // ------------------------------------------------------------------ kernels (mg.cu)
 void mg_build_P(const FineOp& f, Coarse& c, const double2* vecs, int nvec, cudaStream_t st);
-void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st);
+void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st, bool fp32_only = false);
 void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st,
                  const int* act = nullptr);
 void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* xc, void* x, bool accumulate,

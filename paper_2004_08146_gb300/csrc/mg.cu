@@ -138,23 +138,23 @@ __global__ void prolong_kernel(Geom g, Blocking B, int nv, const Z* __restrict__
 // CTA (coarse site blk, direction d): column by column, h(l) = the part of
 // (D P e_col)(y_l) that D couples from block blk + d (d = 0: site-diagonal and
 // in-block hops), then A[blk][d][col][row] = P_blk[row]^H h.
-__device__ __forceinline__ void P_spinor(const double2* __restrict__ P, int nv, int nloc, int blk, int chi, int i, int l,
-                                         Spinor<double>& s) {
+template <typename R>
+__device__ __forceinline__ void P_spinor(const cplx<R>* __restrict__ P, int nv, int nloc, int blk, int chi, int i, int l,
+                                         Spinor<R>& s) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) s.c[k] = make_double2(0, 0);
-    const double2* p = P + (((size_t)blk * 2 + chi) * nv + i) * nloc + (size_t)l * 6;
+    for (int k = 0; k < 12; ++k) s.c[k] = czero<R>();
+    const cplx<R>* p = P + (((size_t)blk * 2 + chi) * nv + i) * nloc + (size_t)l * 6;
 #pragma unroll
     for (int k = 0; k < 6; ++k) s.c[6 * chi + k] = p[k];
 }
 
-template <bool fwd>
-__device__ __forceinline__ void hop_dispatch(int mu, const Spinor<double>& psi, const Link<double>& u, double sg,
-                                             Spinor<double>& acc) {
+template <bool fwd, typename R>
+__device__ __forceinline__ void hop_dispatch(int mu, const Spinor<R>& psi, const Link<R>& u, R sg, Spinor<R>& acc) {
     switch (mu) {
-        case 0: hop_accumulate<double, 0, fwd>(psi, u, sg, acc); break;
-        case 1: hop_accumulate<double, 1, fwd>(psi, u, sg, acc); break;
-        case 2: hop_accumulate<double, 2, fwd>(psi, u, sg, acc); break;
-        default: hop_accumulate<double, 3, fwd>(psi, u, sg, acc); break;
+        case 0: hop_accumulate<R, 0, fwd>(psi, u, sg, acc); break;
+        case 1: hop_accumulate<R, 1, fwd>(psi, u, sg, acc); break;
+        case 2: hop_accumulate<R, 2, fwd>(psi, u, sg, acc); break;
+        default: hop_accumulate<R, 3, fwd>(psi, u, sg, acc); break;
     }
 }
 
@@ -172,10 +172,12 @@ __device__ __forceinline__ bool coarse_active(const Blocking& B, int d, const in
 // site) tasks and leaves h in shared memory ([column][active site][12]);
 // then one warp per (column, row) entry forms P_blk[row]^H h over the active
 // sites only.
-__global__ void __launch_bounds__(256) build_coarse_kernel(Geom g, Blocking B, int nv, const double2* __restrict__ U,
-                                                          const double* __restrict__ A, const double2* __restrict__ P,
-                                                          double2* __restrict__ Ac, int chunk) {
-    extern __shared__ double2 hsm[];   // [chunk][na][12], then na ints
+template <typename R>
+__global__ void __launch_bounds__(256) build_coarse_kernel(Geom g, Blocking B, int nv, const cplx<R>* __restrict__ U,
+                                                          const R* __restrict__ A, const cplx<R>* __restrict__ P,
+                                                          cplx<R>* __restrict__ Ac, int chunk) {
+    extern __shared__ __align__(16) unsigned char hraw[];
+    cplx<R>* hsm = reinterpret_cast<cplx<R>*>(hraw);   // [chunk][na][12], then na ints
     int* lst = reinterpret_cast<int*>(hsm + (size_t)chunk * B.bs * 12);
     __shared__ int na_s;
     const int blk = blockIdx.x, d = blockIdx.y;
@@ -204,13 +206,13 @@ __global__ void __launch_bounds__(256) build_coarse_kernel(Geom g, Blocking B, i
             local_coords(B, l, o);
             for (int mu = 0; mu < 4; ++mu) x[mu] = cb[mu] * B.b[mu] + o[mu];
             const int y = site_index(g, x);
-            Spinor<double> acc;
+            Spinor<R> acc;
 #pragma unroll
-            for (int k = 0; k < 12; ++k) acc.c[k] = make_double2(0, 0);
+            for (int k = 0; k < 12; ++k) acc.c[k] = czero<R>();
             if (d == 0) {
-                Spinor<double> ps;
-                P_spinor(P, nv, nloc, blk, chic, ic, l, ps);
-                clover_apply<double>(A + (size_t)y * 72, ps, acc);
+                Spinor<R> ps;
+                P_spinor<R>(P, nv, nloc, blk, chic, ic, l, ps);
+                clover_apply<R>(A + (size_t)y * 72, ps, acc);
             }
             for (int mu = 0; mu < 4; ++mu) {
                 for (int dir = 0; dir < 2; ++dir) {
@@ -224,15 +226,15 @@ __global__ void __launch_bounds__(256) build_coarse_kernel(Geom g, Blocking B, i
                     site_coords(g, yn, xn);
                     int cn[4], on[4];
                     for (int k = 0; k < 4; ++k) { cn[k] = xn[k] / B.b[k]; on[k] = xn[k] % B.b[k]; }
-                    Spinor<double> ps;
-                    P_spinor(P, nv, nloc, coarse_index(B, cn), chic, ic, local_index(B, on), ps);
-                    Link<double> u;
-                    load_link<double>(U + ((size_t)(fw ? y : yn) * 4 + mu) * 9, u);
-                    if (fw) hop_dispatch<true>(mu, ps, u, neg ? -1.0 : 1.0, acc);
-                    else hop_dispatch<false>(mu, ps, u, neg ? -1.0 : 1.0, acc);
+                    Spinor<R> ps;
+                    P_spinor<R>(P, nv, nloc, coarse_index(B, cn), chic, ic, local_index(B, on), ps);
+                    Link<R> u;
+                    load_link<R>(U + ((size_t)(fw ? y : yn) * 4 + mu) * 9, u);
+                    if (fw) hop_dispatch<true, R>(mu, ps, u, neg ? R(-1) : R(1), acc);
+                    else hop_dispatch<false, R>(mu, ps, u, neg ? R(-1) : R(1), acc);
                 }
             }
-            double2* h = hsm + ((size_t)cc * na + a) * 12;
+            cplx<R>* h = hsm + ((size_t)cc * na + a) * 12;
 #pragma unroll
             for (int k = 0; k < 12; ++k) h[k] = acc.c[k];
         }
@@ -240,18 +242,18 @@ __global__ void __launch_bounds__(256) build_coarse_kernel(Geom g, Blocking B, i
         for (int e = warp; e < nch * nc; e += nwarps) {
             const int cc = e / nc, row = e % nc;
             const int chir = row / nv, ir = row % nv;
-            const double2* pr = P + (((size_t)blk * 2 + chir) * nv + ir) * nloc;
-            const double2* h = hsm + (size_t)cc * na * 12 + 6 * chir;
-            double re = 0, im = 0;
+            const cplx<R>* pr = P + (((size_t)blk * 2 + chir) * nv + ir) * nloc;
+            const cplx<R>* h = hsm + (size_t)cc * na * 12 + 6 * chir;
+            R re = 0, im = 0;
             for (int q = lane; q < na * 6; q += 32) {
                 const int a = q / 6, sc = q % 6;
-                const double2 pv = pr[lst[a] * 6 + sc], hv = h[a * 12 + sc];
+                const cplx<R> pv = pr[lst[a] * 6 + sc], hv = h[a * 12 + sc];
                 re += pv.x * hv.x + pv.y * hv.y;
                 im += pv.x * hv.y - pv.y * hv.x;
             }
             re = warp_sum(re);
             im = warp_sum(im);
-            if (lane == 0) Ac[(((size_t)blk * 9 + d) * nc + col0 + cc) * nc + row] = make_double2(re, im);
+            if (lane == 0) Ac[(((size_t)blk * 9 + d) * nc + col0 + cc) * nc + row] = mk<R>(re, im);
         }
         __syncthreads();
     }
@@ -722,18 +724,31 @@ void mg_build_P(const FineOp& f, Coarse& c, const double2* vecs, int nvec, cudaS
     build_P_kernel<<<grid, 256, 256 * sizeof(double2), st>>>(f.g, c.B, nvec, vecs, c.P64, c.P32);
 }
 
-void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st) {
+void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st, bool fp32_only) {
     dim3 grid(c.B.nb, 9);
     // columns per pass: h of a pass within about 96 KB of shared memory
-    const size_t per_col = (size_t)c.B.bs * 12 * sizeof(double2);
+    const size_t es = fp32_only ? sizeof(float2) : sizeof(double2);
+    const size_t per_col = (size_t)c.B.bs * 12 * es;
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>(c.nc, (96u << 10) / per_col));
     const size_t sm = chunk * per_col + (size_t)c.B.bs * sizeof(int);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(build_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (fp32_only) {
+        // the FP32 operator straight from P32, U32 and the FP32 clover; the
+        // FP64 one is rebuilt on demand (Coarse::a64_stale)
+        if (sm > 48 * 1024)
+            cudaFuncSetAttribute(build_coarse_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        KTimer kt("build_coarse_f32", 0.0, 0.0, st);
+        build_coarse_kernel<float><<<grid, 256, sm, st>>>(f.g, c.B, c.nv, f.U32, f.A32, c.P32, c.A32, chunk);
+        c.a64_stale = true;
+        return;
+    }
+    if (sm > 48 * 1024)
+        cudaFuncSetAttribute(build_coarse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     KTimer kt("build_coarse", 0.0, 0.0, st);
-    build_coarse_kernel<<<grid, 256, sm, st>>>(f.g, c.B, c.nv, f.U64, f.A64, c.P64, c.A64, chunk);
+    build_coarse_kernel<double><<<grid, 256, sm, st>>>(f.g, c.B, c.nv, f.U64, f.A64, c.P64, c.A64, chunk);
     size_t n = (size_t)c.B.nb * 9 * c.nc * c.nc;
     KTimer kt2("narrow", (double)n * 24, 0.0, st);
     narrow_kernel<<<grid_for(n), 256, 0, st>>>(c.A64, c.A32, n);
+    c.a64_stale = false;
 }
 
 void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st,
