@@ -89,6 +89,55 @@ __device__ __forceinline__ void hop_accumulate(const Spinor<R>& psi, const Link<
     }
 }
 
+// The same hop with the direction chosen at run time (fwd: U_mu(x) and
+// 1 - gamma_mu; otherwise U_mu(x-mu)^H and 1 + gamma_mu), so that lanes with
+// neighbours on different sides share one instruction stream.
+template <typename R, int mu>
+__device__ __forceinline__ void hop_accumulate_dir(const Spinor<R>& psi, const Link<R>& u, R sgn, bool fwd,
+                                                   Spinor<R>& acc) {
+    constexpr SpinMono B = kB(mu);
+    constexpr SpinMono BH = kBH(mu);
+    const R pm = fwd ? R(-1) : R(1);
+    cplx<R> h[6], o[6];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const cplx<R> bd = mul_ipow(psi.c[(2 + B.perm[s]) * 3 + a], B.ph[s]);
+            h[s * 3 + a] = psi.c[s * 3 + a] + pm * bd;
+        }
+    }
+    cplx<R> e[9];   // U or U^H
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const cplx<R> d = u.e[a * 3 + b], t = u.e[b * 3 + a];
+            e[a * 3 + b] = fwd ? d : conj(t);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cplx<R> accv = czero<R>();
+#pragma unroll
+            for (int b = 0; b < 3; ++b) accv += e[a * 3 + b] * h[s * 3 + b];
+            o[s * 3 + a] = accv;
+        }
+    }
+    const R half = R(-0.5) * sgn;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            acc.c[s * 3 + a] += half * o[s * 3 + a];
+            const cplx<R> bo = mul_ipow(o[BH.perm[s] * 3 + a], BH.ph[s]);
+            acc.c[(2 + s) * 3 + a] += (pm * half) * bo;
+        }
+    }
+}
+
 // y = A x for the two packed Hermitian 6x6 chirality blocks (diagonal reals,
 // then the upper triangle as (re, im) pairs in herm_off order)
 template <typename R>

@@ -591,24 +591,31 @@ __global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const 
 #pragma unroll
         for (int k = 0; k < 12; ++k) psi.c[k] = vj[l * 12 + k];
         clover_apply_smem<R>(sclov + l * 72, psi, acc);
+        // Dirichlet block: per mu one neighbour inside the block on the
+        // forward side if there is one, else on the backward side (a 2-site
+        // extent has exactly one), taken by all lanes together; interior
+        // sites of wider blocks add their backward neighbour afterwards
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
             Spinor<R> nb;
             Link<R> u;
-            if (o[mu] < B.b[mu] - 1) {
-                const int ln = l + lstride[mu];
+            const bool fw = o[mu] < B.b[mu] - 1;
+            if (fw || o[mu] > 0) {
+                const int ln = fw ? l + lstride[mu] : l - lstride[mu];
 #pragma unroll
                 for (int k = 0; k < 12; ++k) nb.c[k] = vj[ln * 12 + k];
+                const cplx<R>* lk = slink + (fw ? l : ln) * 36 + mu * 9;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) u.e[k] = slink[l * 36 + mu * 9 + k];
+                for (int k = 0; k < 9; ++k) u.e[k] = lk[k];
                 switch (mu) {
-                    case 0: hop_accumulate<R, 0, true>(nb, u, R(1), acc); break;
-                    case 1: hop_accumulate<R, 1, true>(nb, u, R(1), acc); break;
-                    case 2: hop_accumulate<R, 2, true>(nb, u, R(1), acc); break;
-                    default: hop_accumulate<R, 3, true>(nb, u, R(1), acc); break;
+                    case 0: hop_accumulate_dir<R, 0>(nb, u, R(1), fw, acc); break;
+                    case 1: hop_accumulate_dir<R, 1>(nb, u, R(1), fw, acc); break;
+                    case 2: hop_accumulate_dir<R, 2>(nb, u, R(1), fw, acc); break;
+                    default: hop_accumulate_dir<R, 3>(nb, u, R(1), fw, acc); break;
                 }
             }
-            if (o[mu] > 0) {
+            const bool both = fw && o[mu] > 0;
+            if (__any_sync(0xffffffffu, both) && both) {
                 const int ln = l - lstride[mu];
 #pragma unroll
                 for (int k = 0; k < 12; ++k) nb.c[k] = vj[ln * 12 + k];
