@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-stencil", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="no nvidia-smi clock sampling (profiling runs under ncu)")
     ap.add_argument("--only-stencil", action="store_true",
                     help="run and print only the fine-stencil bandwidth measurement")
     ap.add_argument("--k", type=int, default=None,
@@ -88,12 +90,15 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, enabled=True):
         self.idx = gpu_index
+        self.enabled = enabled
         self.proc = None
         self.file = None
 
     def start(self):
+        if not self.enabled:
+            return
         try:
             self.file = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
@@ -277,7 +282,7 @@ def main():
     st = qcd.qcd_stats_read()
     dom = max(st, key=lambda s: s["total_ms"])
     # ---- timed region: launch counts for all kernels, events on the dominant one
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
     qcd.qcd_stats_reset(2, dom["name"])
     clocks.start()
     ms, infos, lam = timed_steps(ctx, args.steps, max(0, args.warmup - 2), profile=True)

@@ -717,6 +717,230 @@ __global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const 
     store_spinor<R>(x + (size_t)y * 12, e);
 }
 
+// SAP block solve for 16-site blocks with two lanes per site: lane
+// chi * 16 + l holds chirality half chi (spins 2chi, 2chi+1) of site l, so one
+// warp solves one block.  The clover term is block diagonal in chirality; in a
+// hop each lane forms the projected half-spinor h_s for s = chi, multiplies it
+// by the link (9 complex products instead of 18) and takes the other s from
+// the partner lane (lane ^ 16) before it reconstructs its own half.  Same
+// GMRES as sap_warp_kernel (modified Gram-Schmidt, Givens by lane 0).
+template <typename R>
+__global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const cplx<R>* __restrict__ U,
+                                                     const R* __restrict__ A, const int* __restrict__ blocks, int ncol,
+                                                     int op, Shifts tau, const cplx<R>* __restrict__ r,
+                                                     cplx<R>* __restrict__ x, int iters, double tol,
+                                                     const int* __restrict__ act) {
+    constexpr int BS = 16;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x;
+    const int chi = lane >> 4, l = lane & 15;
+    const SapSmemLayout LY = sap_layout<R>(BS, iters);
+    unsigned char* base = smraw;
+    cplx<R>* basis = reinterpret_cast<cplx<R>*>(base + LY.basis);
+    cplx<R>* slink = reinterpret_cast<cplx<R>*>(base + LY.links);
+    R* sclov = reinterpret_cast<R*>(base + LY.clover);
+    cplx<R>* H = reinterpret_cast<cplx<R>*>(base + LY.H);
+    cplx<R>* gv = reinterpret_cast<cplx<R>*>(base + LY.g);
+    cplx<R>* sn = reinterpret_cast<cplx<R>*>(base + LY.sn);
+    cplx<R>* yv = reinterpret_cast<cplx<R>*>(base + LY.y);
+    R* cs = reinterpret_cast<R*>(base + LY.cs);
+    int* flag = reinterpret_cast<int*>(base + LY.flag);
+
+    const int j = blockIdx.y;
+    if (act != nullptr && !act[j]) return;
+    const int blk = blocks[blockIdx.x];
+    const size_t fstride = (size_t)g.V * 12;
+    r += j * fstride;
+    x += j * fstride;
+    const R t = (R)tau.t[j];
+    int o[4];
+    {
+        int tt = l;
+        o[3] = tt % B.b[3]; tt /= B.b[3];
+        o[2] = tt % B.b[2]; tt /= B.b[2];
+        o[1] = tt % B.b[1]; o[0] = tt / B.b[1];
+    }
+    const int y = block_fine_site(g, B, blk, l);
+    // stage links and clover of the 16 sites (both lanes of a site share the work)
+    for (int k = chi; k < 36; k += 2) slink[l * 36 + k] = __ldg(U + (size_t)y * 36 + k);
+    for (int k = chi; k < 72; k += 2) sclov[l * 72 + k] = __ldg(A + (size_t)y * 72 + k);
+    cplx<R> w[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = __ldg(r + (size_t)y * 12 + 6 * chi + k);
+    R nn = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) nn += w[k].x * w[k].x + w[k].y * w[k].y;
+    nn = warp_sum(nn);
+    const R beta = sqrt(nn);
+    {
+        const R ib = beta > R(0) ? R(1) / beta : R(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) basis[l * 12 + 6 * chi + k] = ib * w[k];
+    }
+    if (lane == 0) { gv[0] = mk<R>(beta, R(0)); flag[0] = beta > R(0) ? 0 : 1; flag[1] = 0; }
+    __syncwarp();
+    int lstride[4];
+    lstride[3] = 1;
+    lstride[2] = B.b[3];
+    lstride[1] = B.b[3] * B.b[2];
+    lstride[0] = B.b[3] * B.b[2] * B.b[1];
+    for (int jj = 0; jj < iters; ++jj) {
+        const bool active = flag[0] == 0;
+        if (!active) break;   // flag is shared by the whole warp
+        const cplx<R>* vj = basis + (size_t)jj * BS * 12;
+        cplx<R> psi[6], acc[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) psi[k] = vj[l * 12 + 6 * chi + k];
+        // clover block chi of site l
+        {
+            const R* a = sclov + l * 72 + 36 * chi;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) acc[i] = a[i] * psi[i];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+#pragma unroll
+                for (int jc = i + 1; jc < 6; ++jc) {
+                    const int oo = herm_off(i, jc);
+                    const cplx<R> aij = mk<R>(a[oo], a[oo + 1]);
+                    acc[i] += aij * psi[jc];
+                    acc[jc] += cmulc(aij, psi[i]);
+                }
+            }
+        }
+        // hops inside the block (Dirichlet): per mu the forward neighbour if it
+        // is inside, else the backward one; interior sites of wider blocks
+        // add their backward neighbour in a second round
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const SpinMono Bm = kB(mu), BHm = kBH(mu);
+            for (int round = 0; round < 2; ++round) {
+                const bool fw = round == 0 ? (o[mu] < B.b[mu] - 1) : false;
+                const bool has = round == 0 ? (fw || o[mu] > 0) : (o[mu] < B.b[mu] - 1 && o[mu] > 0);
+                if (round == 1 && !__any_sync(0xffffffffu, has)) break;
+                const int ln = has ? (fw ? l + lstride[mu] : l - lstride[mu]) : l;
+                const cplx<R>* nb = vj + ln * 12;
+                const R pm = fw ? R(-1) : R(1);
+                // h_s for s = chi: up_s + pm i^{ph_s} dn_{perm_s}
+                const int sp = Bm.perm[chi], ph = Bm.ph[chi];
+                cplx<R> h[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) h[a] = nb[chi * 3 + a] + pm * mul_ipow(nb[(2 + sp) * 3 + a], ph);
+                const cplx<R>* lk = slink + (fw ? l : ln) * 36 + mu * 9;
+                cplx<R> os[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cplx<R> v = czero<R>();
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) v += (fw ? lk[a * 3 + b] : conj(lk[b * 3 + a])) * h[b];
+                    os[a] = has ? v : czero<R>();
+                }
+                cplx<R> ot[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    ot[a].x = __shfl_xor_sync(0xffffffffu, os[a].x, 16);
+                    ot[a].y = __shfl_xor_sync(0xffffffffu, os[a].y, 16);
+                }
+                // o[0], o[1] of the site; reconstruct this lane's half
+                const R half = R(-0.5);
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const int src = chi ? BHm.perm[s2] : s2;
+                    const int php = chi ? BHm.ph[s2] : 0;
+                    const R c = chi ? pm * half : half;
+                    const bool mine = src == chi;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) acc[s2 * 3 + a] += c * mul_ipow(mine ? os[a] : ot[a], php);
+                }
+            }
+        }
+        // shift: D - tau Gamma5 (op D) or Gamma5 D - tau (op Q)
+        {
+            const R g5 = chi ? R(-1) : R(1);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                if (op == QCD_OP_D) acc[k] -= (t * g5) * psi[k];
+                else acc[k] = g5 * acc[k] - t * psi[k];
+            }
+        }
+        // modified Gram-Schmidt against v_0 .. v_jj
+        for (int i = 0; i <= jj; ++i) {
+            const cplx<R>* vi = basis + (size_t)i * BS * 12 + l * 12 + 6 * chi;
+            R hr = 0, hi = 0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const cplx<R> a = vi[k];
+                hr += a.x * acc[k].x + a.y * acc[k].y;
+                hi += a.x * acc[k].y - a.y * acc[k].x;
+            }
+            hr = warp_sum(hr);
+            hi = warp_sum(hi);
+            const cplx<R> h = mk<R>(hr, hi);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[k] -= h * vi[k];
+            if (lane == 0) H[i * iters + jj] = h;
+        }
+        R hn2 = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) hn2 += acc[k].x * acc[k].x + acc[k].y * acc[k].y;
+        hn2 = warp_sum(hn2);
+        const R hn = sqrt(hn2);
+        {
+            const R ih = hn > R(0) ? R(1) / hn : R(0);
+            cplx<R>* vn = basis + (size_t)(jj + 1) * BS * 12 + l * 12 + 6 * chi;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) vn[k] = ih * acc[k];
+        }
+        if (lane == 0) {
+            H[(jj + 1) * iters + jj] = mk<R>(hn, R(0));
+            for (int i = 0; i < jj; ++i) {
+                cplx<R> a = H[i * iters + jj], c = H[(i + 1) * iters + jj];
+                H[i * iters + jj] = cs[i] * a + sn[i] * c;
+                H[(i + 1) * iters + jj] = cs[i] * c - conj(sn[i]) * a;
+            }
+            cplx<R> a = H[jj * iters + jj];
+            cplx<R> c = H[(jj + 1) * iters + jj];
+            R aa = sqrt(a.x * a.x + a.y * a.y), rr = sqrt(aa * aa + c.x * c.x + c.y * c.y);
+            if (aa > R(0)) {
+                cs[jj] = aa / rr;
+                sn[jj] = (R(1) / rr) * ((R(1) / aa) * a * conj(c));
+            } else {
+                cs[jj] = R(0);
+                sn[jj] = mk<R>(R(1), R(0));
+            }
+            H[jj * iters + jj] = cs[jj] * a + sn[jj] * c;
+            gv[jj + 1] = R(-1) * (conj(sn[jj]) * gv[jj]);
+            gv[jj] = cs[jj] * gv[jj];
+            const R res = sqrt(gv[jj + 1].x * gv[jj + 1].x + gv[jj + 1].y * gv[jj + 1].y);
+            flag[1] = jj + 1;
+            if (tol >= 0.0 && (double)res <= tol * (double)beta) flag[0] = 1;
+        }
+        __syncwarp();
+    }
+    const int kdim = flag[1];
+    if (lane == 0) {
+        for (int i = kdim - 1; i >= 0; --i) {
+            cplx<R> sacc = gv[i];
+            for (int k = i + 1; k < kdim; ++k) sacc -= H[i * iters + k] * yv[k];
+            cplx<R> dd = H[i * iters + i];
+            R den = dd.x * dd.x + dd.y * dd.y;
+            yv[i] = den > R(0) ? (R(1) / den) * cmulc(dd, sacc) : mk<R>(R(0), R(0));
+        }
+    }
+    __syncwarp();
+    if (kdim == 0) return;
+    cplx<R> e[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) e[k] = x[(size_t)y * 12 + 6 * chi + k];
+    for (int i = 0; i < kdim; ++i) {
+        const cplx<R> yi = yv[i];
+        const cplx<R>* vi = basis + (size_t)i * BS * 12 + l * 12 + 6 * chi;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) e[k] += yi * vi[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) x[(size_t)y * 12 + 6 * chi + k] = e[k];
+}
+
 inline int grid_for(size_t n, int th = 256) {
     size_t gsz = (n + th - 1) / th;
     return (int)(gsz > 1048576 ? 1048576 : (gsz == 0 ? 1 : gsz));
@@ -820,7 +1044,22 @@ void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op
     const double sites = (double)sp.ncol[colour] * bs;
     KTimer kt(prec == QCD_FP64 ? "sap_block_f64" : "sap_block_f32", rs * sites * (nrhs * 72.0 + 144.0),
               1824.0 * sites * nrhs * iters, st);
-    if (bs == 16 || bs == 32) {
+    if (bs == 16) {
+        dim3 grid(sp.ncol[colour], nrhs);
+        if (prec == QCD_FP64) {
+            const size_t sm = sap_layout<double>(16, iters).total;
+            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            sap_chi_kernel<double><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
+                sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
+        } else {
+            const size_t sm = sap_layout<float>(16, iters).total;
+            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            sap_chi_kernel<float><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
+                sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
+        }
+        return;
+    }
+    if (bs == 32) {
         const int spw = 32 / bs;
         dim3 grid((sp.ncol[colour] + spw - 1) / spw, nrhs);
         if (prec == QCD_FP64) {
