@@ -69,11 +69,12 @@ def max_over_ranks(value, device=None):
     return float(t.item())
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of each kernel as it stands now, for the roofline's "traffic";
-# profiles/sap_warp_f32_c2_16x8c3.md gives the capture.  A kernel that changes
-# is taken out of this table until it is captured again.
-NCU_TRAFFIC = {"sap_block_f32": 4780032}
+# DRAM bytes per launch (dram__bytes.sum.per_second x gpu__time_duration.sum,
+# i.e. read + write) from one ncu capture of each kernel as it stands now, for
+# the roofline's "traffic"; profiles/sap_chi_f32_c2_16x8c3.md gives the
+# capture.  A kernel that changes is taken out of this table until it is
+# captured again.
+NCU_TRAFFIC = {"sap_block_f32": 4782000}
 
 
 def measured_peaks():
