@@ -76,8 +76,8 @@ struct qcd_ctx {
         for (auto& kv : ws) if (kv.second.p) cudaFree(kv.second.p);
         ws.clear();
         auto fr = [](void* q) { if (q) cudaFree(q); };
-        fr(f.U64); fr(f.U32); fr(f.A64); fr(f.A32);
-        f.U64 = nullptr; f.U32 = nullptr; f.A64 = nullptr; f.A32 = nullptr;
+        fr(f.U64); fr(f.U32); fr(f.U32s); fr(f.A64); fr(f.A32); fr(f.A32s);
+        f.U64 = nullptr; f.U32 = nullptr; f.U32s = nullptr; f.A64 = nullptr; f.A32 = nullptr; f.A32s = nullptr;
         drop_mg();
         fr(sap.blocks_of_colour[0]); fr(sap.blocks_of_colour[1]);
         sap.blocks_of_colour[0] = sap.blocks_of_colour[1] = nullptr;
@@ -1278,6 +1278,8 @@ int qcd_set_gauge(qcd_ctx* ctx, const double* U, const int dims[4], double m0, d
         CK(cudaMalloc(&f.U32, nl * sizeof(float2)));
         CK(cudaMalloc(&f.A64, (size_t)V * 72 * sizeof(double)));
         CK(cudaMalloc(&f.A32, (size_t)V * 72 * sizeof(float)));
+        CK(cudaMalloc(&f.U32s, nl * sizeof(float2)));
+        CK(cudaMalloc(&f.A32s, (size_t)V * 18 * sizeof(float4)));
         CK(cudaMemcpyAsync(f.U64, U, nl * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
         blas_convert(QCD_FP64, f.U64, QCD_FP32, f.U32, nl, ctx->st);
         launch_clover_build(f, ctx->st);

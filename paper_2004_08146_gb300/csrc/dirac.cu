@@ -183,11 +183,108 @@ __global__ void __launch_bounds__(128) wilson_clover_kernel(
     store_spinor<R>(out + (size_t)s * 12, acc);
 }
 
+// FP32 stencil with links and clover blocks in site-fastest (SoA) copies:
+// Us[(mu * 9 + k) * V + site] (float2) and As[q * V + site] (float4, q < 18),
+// so a warp's link and clover loads are contiguous; spinors keep the ABI
+// layout.  Same arithmetic as wilson_clover_kernel<float>.
+__global__ void __launch_bounds__(128) wilson_clover_soa_kernel(
+    float2* __restrict__ out, const float2* __restrict__ in, const float2* __restrict__ b,
+    const float2* __restrict__ Us, const float4* __restrict__ As, Geom g, int op, Shifts tau, size_t stride,
+    const int* __restrict__ act) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    const int j = blockIdx.y;
+    if (act != nullptr && !act[j]) return;
+    in += j * stride;
+    out += j * stride;
+    const size_t V = (size_t)g.V;
+    int x[4];
+    site_coords(g, s, x);
+    Spinor<float> psi, acc;
+    load_spinor<float>(in + (size_t)s * 12, psi);
+    {
+        float ar[72];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) {
+            const float4 v = __ldg(As + (size_t)q * V + s);
+            ar[4 * q] = v.x; ar[4 * q + 1] = v.y; ar[4 * q + 2] = v.z; ar[4 * q + 3] = v.w;
+        }
+        clover_apply_regs<float>(ar, psi, acc);
+    }
+    auto link = [&](int site, int mu, Link<float>& u) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) u.e[k] = __ldg(Us + (size_t)(mu * 9 + k) * V + site);
+    };
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        int neg;
+        Spinor<float> nb;
+        Link<float> u;
+        int sf = nb_fwd(g, x, s, mu, neg);
+        load_spinor<float>(in + (size_t)sf * 12, nb);
+        link(s, mu, u);
+        float sg = neg ? -1.f : 1.f;
+        switch (mu) {
+            case 0: hop_accumulate<float, 0, true>(nb, u, sg, acc); break;
+            case 1: hop_accumulate<float, 1, true>(nb, u, sg, acc); break;
+            case 2: hop_accumulate<float, 2, true>(nb, u, sg, acc); break;
+            default: hop_accumulate<float, 3, true>(nb, u, sg, acc); break;
+        }
+        int sb = nb_bwd(g, x, s, mu, neg);
+        load_spinor<float>(in + (size_t)sb * 12, nb);
+        link(sb, mu, u);
+        sg = neg ? -1.f : 1.f;
+        switch (mu) {
+            case 0: hop_accumulate<float, 0, false>(nb, u, sg, acc); break;
+            case 1: hop_accumulate<float, 1, false>(nb, u, sg, acc); break;
+            case 2: hop_accumulate<float, 2, false>(nb, u, sg, acc); break;
+            default: hop_accumulate<float, 3, false>(nb, u, sg, acc); break;
+        }
+    }
+    const float t = (float)tau.t[j];
+    if (op == QCD_OP_D) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc.c[k] -= t * psi.c[k];
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc.c[k] += t * psi.c[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc.c[k] -= t * psi.c[k];
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc.c[k] = -acc.c[k] - t * psi.c[k];
+    }
+    if (b != nullptr) {
+        Spinor<float> bb;
+        load_spinor<float>(b + j * stride + (size_t)s * 12, bb);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc.c[k] = bb.c[k] - acc.c[k];
+    }
+    store_spinor<float>(out + (size_t)s * 12, acc);
+}
+
+// site-fastest copies of the FP32 links and clover blocks
+__global__ void soa_copies_kernel(const float2* __restrict__ U, const float* __restrict__ A, float2* __restrict__ Us,
+                                  float4* __restrict__ As, int V) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)V * 36; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t site = e % V;
+        const int r = (int)(e / V);   // mu * 9 + k
+        Us[e] = U[site * 36 + r];
+    }
+    const float4* A4 = reinterpret_cast<const float4*>(A);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)V * 18; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t site = e % V;
+        const int q = (int)(e / V);
+        As[e] = A4[site * 18 + q];
+    }
+}
+
 // ------------------------------------------------------------------ host launchers
 void launch_clover_build(const FineOp& f, cudaStream_t st) {
     int th = 128;
     KTimer kt("clover_build", 0.0, 0.0, st);
     clover_build_kernel<<<(f.g.V + th - 1) / th, th, 0, st>>>(f.U64, f.g, f.m0, f.csw, f.A64, f.A32);
+    if (f.U32s != nullptr && f.A32s != nullptr)
+        soa_copies_kernel<<<1216, 256, 0, st>>>(f.U32, f.A32, f.U32s, f.A32s, f.g.V);
 }
 
 template <typename R>
@@ -201,6 +298,11 @@ void launch_dirac(const FineOp& f, int op, int nrhs, const void* in, void* out, 
     const double bytes = (double)f.g.V * (nrhs * (b ? 72.0 : 48.0) + 144.0) * sizeof(R);
     KTimer kt(std::is_same<R, double>::value ? "wilson_clover_f64" : "wilson_clover_f32", bytes,
               1824.0 * f.g.V * nrhs, st);
+    if (!std::is_same<R, double>::value && f.U32s != nullptr && f.A32s != nullptr) {
+        wilson_clover_soa_kernel<<<grid, 128, 0, st>>>((float2*)out, (const float2*)in, (const float2*)b, f.U32s,
+                                                       f.A32s, f.g, op, sh, (size_t)f.g.V * 12, act);
+        return;
+    }
     wilson_clover_kernel<R><<<grid, 128, 0, st>>>((cplx<R>*)out, (const cplx<R>*)in, (const cplx<R>*)b,
                                                   U, A, f.g, op, sh, (size_t)f.g.V * 12, act);
 }

@@ -44,8 +44,10 @@ struct FineOp {
     Geom g{};
     double2* U64 = nullptr;   // [V][4][3][3]
     float2* U32 = nullptr;
+    float2* U32s = nullptr;   // FP32 links site-fastest: [(mu * 9 + k) * V + site]
     double* A64 = nullptr;    // [V][2][36]: (m0 + 4) + clover, packed Hermitian 6x6
     float* A32 = nullptr;
+    float4* A32s = nullptr;   // FP32 clover site-fastest: [q * V + site], q < 18 (16-byte pieces)
     double m0 = 0, csw = 0;
 };
 
