@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true",
                     help="no nvidia-smi clock sampling (profiling runs under ncu)")
+    ap.add_argument("--smoother-sweep", action="store_true",
+                    help="shifted-solve iterations and time vs tau for SAP / GMRES smoothing and the "
+                         "D - tau Gamma5 / Q - tau forms on an 8^4 field, then exit")
     ap.add_argument("--only-stencil", action="store_true",
                     help="run and print only the fine-stencil bandwidth measurement")
     ap.add_argument("--k", type=int, default=None,
@@ -222,6 +225,9 @@ def main():
     n = int(np.prod(dims)) * 12
     stream = torch.cuda.Stream(devn)
     sp = stream.cuda_stream
+    if args.smoother_sweep:
+        print(json.dumps({"smoother_sweep": smoother_sweep(qcd, synth, torch, devn, stream)}), flush=True)
+        return
     if args.only_stencil:
         peak, _ = measured_peaks()
         print(json.dumps({"stencil": stencil_bench(qcd, synth, torch, devn, stream, peak)}), flush=True)
@@ -369,6 +375,41 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def smoother_sweep(qcd, synth, torch, devn, stream):
+    """Iterations and time of one shifted solve (Q - tau) x = b to 1e-8 relative
+    residual against the shift tau, for the SAP and the GMRES smoother and for
+    the two forms of the correction equation (Sec. 2 last paragraph, Sec. 3):
+    8^4 field with the 16x8^3 workload's eps, csw and m0, two-level MG with 2^4
+    aggregates, Nv = 8, SAP on 2^4 blocks."""
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_field(dims, 0.5, 1005)
+    m0, csw = -0.85, 1.5
+    b = torch.from_numpy(synth.spinor(dims, 1006).reshape(-1)).to(devn)
+    rows = []
+    for sm_name, sm in (("sap", qcd.QCD_SMOOTHER_SAP), ("gmres", qcd.QCD_SMOOTHER_GMRES)):
+        for form_name, form in (("D-tau*G5", qcd.QCD_OP_D), ("Q-tau", qcd.QCD_OP_Q)):
+            p = qcd.default_params(smoother=sm, correction_form=form, sap_block=(2, 2, 2, 2))
+            ctx = qcd.Context(params=p, stream=stream.cuda_stream)
+            ctx.qcd_set_gauge(U, dims, m0, csw)
+            ctx.qcd_mg_setup(8, (2, 2, 2, 2))
+            x = torch.zeros_like(b)
+            ctx.qcd_shifted_solve(b, x, 0.0, 1e-8)            # warm-up
+            # shifts across the wanted part of the spectrum (the 50 smallest
+            # |lambda| of the 16x8^3 workload reach 0.25); beyond it the
+            # two-level solver stops converging for every smoother and form
+            for tau in (0.0, 0.05, 0.1, 0.15, 0.2, 0.25):
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, info = ctx.qcd_shifted_solve(b, x, tau, 1e-8)
+                torch.cuda.synchronize()
+                rows.append({"smoother": sm_name, "form": form_name, "tau": tau, "converged": rc == qcd.QCD_OK,
+                             "fgmres_iterations": info.iterations, "refinements": info.refinements,
+                             "residual": info.residual, "ms": (time.perf_counter() - t0) * 1e3})
+            ctx.close()
+    return {"lattice": "8^4", "eps": 0.5, "csw": csw, "m0": m0, "tol": 1e-8, "rows": rows}
 
 
 def stencil_bench(qcd, synth, torch, devn, stream, peak):

@@ -60,3 +60,22 @@ def test_gd_lambda_amg_c1(c1, precision):
     assert rc == qcd.QCD_OK and info.converged
     assert info.updates >= 1
     _check(op, ev, lam, host(V).reshape(k, -1), k)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gd_other_seeds_complete_c1(c1, precision):
+    """Runs with other seeds (other setup and start vectors) find the same k
+    smallest |lambda|: a guard against eigenvalues the search skips (locking,
+    restart and the completion rule all take part)."""
+    from paper_2004_08146_gb300 import qcd
+    torch = torch_cuda()
+    U, op, ev = c1
+    k = 10
+    for seed in (1001, 1002, 1003, 1004):
+        ctx = make_ctx(U, DIMS, -0.2, 1.0, precision=precision, seed=seed)
+        ctx.qcd_mg_setup(8, (2, 2, 2, 2))
+        V = torch.zeros(k * op.n, dtype=torch.complex128, device="cuda")
+        rc, lam, info = ctx.qcd_eigs(k, 1e-8, V)
+        assert rc == qcd.QCD_OK and info.converged
+        assert np.max(np.abs(lam - ev[:k]) / np.abs(ev[:k])) < 1e-10, seed
+        ctx.close()

@@ -140,3 +140,25 @@ def test_shifted_solve_residual(setting, precision):
         xh = host(xs[j]).reshape(DIMS + (4, 3))
         res = np.linalg.norm(b[j] - op.Q_shift(xh, taus[j])) / np.linalg.norm(b[j])
         assert res < 2e-10
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_two_level_cycle_gmres_smoother(setting, prec, tol):
+    """The cycle with the GMRES smoother (Sec. 2, last paragraph) in both forms
+    of the shifted operator, D - tau Gamma5 (Eq. 3.7) and Q - tau (Eq. 3.6)."""
+    from paper_2004_08146_gb300 import qcd
+    op = setting["op"]
+    dt = np.complex128 if prec == 0 else np.complex64
+    ctx = make_ctx(setting["U"], DIMS, setting["m0"], setting["csw"], sap_block=BLOCK, smoother=1,
+                   gmres_smooth_iters=3, nu=2, coarse_tol=0.0, coarse_maxiter=8, precision=0)
+    ctx.qcd_mg_update_from_eigvecs(dev(setting["vecs"]), NV)
+    b = synth.spinor(DIMS, 61, nvec=1)
+    tau = [0.11]
+    for form, oform in ((qcd.QCD_OP_D, 'g5'), (qcd.QCD_OP_Q, 'Q')):
+        h = mg.TwoLevelMG(op, BLOCK, BLOCK, NV, nu=2, coarse_tol=0.0, coarse_maxiter=8, smoother='gmres',
+                          smooth_iters=3, form=oform)
+        h.set_vectors(setting["vecs"])
+        ref = h.cycle(b[0], tau[0])
+        x = dev(b, dt)
+        ctx.qcd_mg_cycle(form, prec, 1, dev(b, dt), x, tau)
+        assert relerr(host(x), ref) < tol, form
