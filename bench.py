@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--smoother-sweep", action="store_true",
                     help="shifted-solve iterations and time vs tau for SAP / GMRES smoothing and the "
                          "D - tau Gamma5 / Q - tau forms on an 8^4 field, then exit")
+    ap.add_argument("--ablation", action="store_true",
+                    help="GD-lambda-AMG variants on the workload (k = 20): default, no interpolation "
+                         "updates, Rayleigh-Ritz extraction; then exit")
     ap.add_argument("--only-stencil", action="store_true",
                     help="run and print only the fine-stencil bandwidth measurement")
     ap.add_argument("--k", type=int, default=None,
@@ -225,6 +228,9 @@ def main():
     n = int(np.prod(dims)) * 12
     stream = torch.cuda.Stream(devn)
     sp = stream.cuda_stream
+    if args.ablation:
+        print(json.dumps({"ablation": ablation(qcd, synth, torch, devn, stream, w, U, dims, n)}), flush=True)
+        return
     if args.smoother_sweep:
         print(json.dumps({"smoother_sweep": smoother_sweep(qcd, synth, torch, devn, stream)}), flush=True)
         return
@@ -375,6 +381,30 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def ablation(qcd, synth, torch, devn, stream, w, U, dims, n):
+    """The variants of Sec. 4 on the workload: harmonic Ritz extraction with
+    interpolation updates after every lock (the method), without updates, and
+    with Rayleigh-Ritz extraction; 20 eigenpairs, at most 600 outer iterations."""
+    k = 20
+    rows = []
+    for name, kw in (("harmonic+updates", {}), ("harmonic, no updates", {"update_every": 0}),
+                     ("rayleigh-ritz+updates", {"extraction": qcd.QCD_EXTRACT_RITZ})):
+        p = qcd.default_params(use_mg=w["use_mg"], sap_block=w["sap"], max_outer=600, **kw)
+        ctx = qcd.Context(params=p, stream=stream.cuda_stream)
+        ctx.qcd_set_gauge(U, dims, w["m0"], w["csw"])
+        V = torch.zeros(k * n, dtype=torch.complex128, device=devn)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.qcd_mg_setup(w["nv"], w["agg"])
+        rc, lam, info = ctx.qcd_eigs(k, 1e-8, V)
+        torch.cuda.synchronize()
+        rows.append({"variant": name, "converged": bool(info.converged), "locked": info.locked,
+                     "outer": info.outer, "inner": info.inner, "updates": info.updates,
+                     "coarse_iterations": info.coarse_iterations, "s": time.perf_counter() - t0})
+        ctx.close()
+    return {"workload": "c2_16x8c3", "k": k, "rows": rows}
 
 
 def smoother_sweep(qcd, synth, torch, devn, stream):

@@ -51,6 +51,9 @@ extern "C" {
 #define QCD_SMOOTHER_SAP   0
 #define QCD_SMOOTHER_GMRES 1
 
+#define QCD_EXTRACT_HARMONIC 0
+#define QCD_EXTRACT_RITZ     1
+
 typedef struct qcd_ctx qcd_ctx;
 
 /* Parameters; defaults (qcd_default_params) are Table 2 of the paper. */
@@ -78,7 +81,11 @@ typedef struct qcd_params {
     int    n_init;           /* random start vectors when use_mg = 0 (default 8) */
     int    shift_rho;        /* 1: correction-equation shift = Rayleigh quotient rho of the
                                 target vector (default); 0: its harmonic Ritz value theta */
-    int    update_every;     /* interpolation rebuild every k locks (default 1) */
+    int    update_every;     /* interpolation rebuild every k locks (default 1; 0: never,
+                                the no-update variant of Sec. 4) */
+    int    extraction;       /* QCD_EXTRACT_HARMONIC: harmonic Ritz pairs (Theorem 1,
+                                default); QCD_EXTRACT_RITZ: Rayleigh-Ritz pairs of
+                                V^H Q V (the Ritz-Galerkin condition of Sec. 3) */
     int    max_outer;        /* outer iteration cap (default 100000) */
     unsigned long long seed; /* counter-based RNG seed for setup / start vectors */
     int    verbose;          /* 1: per-lock progress on stderr */

@@ -66,6 +66,20 @@ def harmonic_ritz(V, W):
     return theta[order], S[:, order]
 
 
+def rayleigh_ritz(V, W):
+    """All Ritz pairs of Q w.r.t. span(V) for orthonormal V, given W = Q V:
+    the Ritz-Galerkin condition Q u - theta u orthogonal to span(V) (Sec. 3)
+    reduces to the Hermitian eigenproblem (V^H Q V) s = theta s.
+
+    Returns ``(theta, S)`` in the order of ``harmonic_ritz``.
+    """
+    Hm = V.conj().T @ W
+    Hm = 0.5 * (Hm + Hm.conj().T)
+    theta, S = np.linalg.eigh(Hm)
+    order = np.lexsort((theta, np.abs(theta)))
+    return theta[order], S[:, order]
+
+
 def _orth_complement(s):
     """Orthonormal basis of the complement of unit vector s in C^m."""
     m = s.shape[0]
@@ -111,7 +125,7 @@ def select_targets(theta, b, candidates=None):
 
 def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
                   n_tv=None, on_update=None, update_every=1, max_outer=100000,
-                  random_vector=None, n_guard=0, block=1, shift='rho'):
+                  random_vector=None, n_guard=0, block=1, shift='rho', extraction='harmonic'):
     """Algorithm 2 (GD-lambda-AMG) on flat complex vectors.
 
     Q            : callable, v (N,) -> Q v
@@ -131,7 +145,10 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
     shift        : 'rho' shifts the correction equation by the Rayleigh
                    quotient of the target vector, 'theta' by its harmonic
                    Ritz value (Algorithm 2 as printed)
+    extraction   : 'harmonic' (Theorem 1, the method's default) or 'rr' for
+                   the Rayleigh-Ritz pairs (the comparison of Sec. 4)
     """
+    extract = harmonic_ritz if extraction == 'harmonic' else rayleigh_ritz
     n_want = n
     n = n + int(n_guard)
     V0 = np.asarray(V0, dtype=np.complex128)
@@ -170,7 +187,7 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
             continue
         finished = False
         while True:
-            theta, S = harmonic_ritz(V, W)
+            theta, S = extract(V, W)
             cand = None
             if len(lam) >= n:
                 lim = np.sort(np.abs(lam))[n - 1]
@@ -204,7 +221,7 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
             if V.shape[1] == 0:
                 break
             if on_update is not None and X.shape[1] >= n_tv and locks_since_update >= update_every:
-                theta2, _ = harmonic_ritz(V, W)
+                theta2, _ = extract(V, W)
                 target = theta2[0]
                 dist = np.abs(np.asarray(lam) - target)
                 pick = np.lexsort((np.arange(len(lam)), dist))[:n_tv]
@@ -221,7 +238,7 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
             T[:, j] = t
             inner += int(it)
         if V.shape[1] + T.shape[1] > m_max:
-            theta, S = harmonic_ritz(V, W)
+            theta, S = extract(V, W)
             Qs, _ = np.linalg.qr(S[:, :m_min])
             V = V @ Qs
             W = W @ Qs

@@ -160,6 +160,9 @@ void validate_params(const qcd_params& p) {
     if (p.m_min < 1 || p.m_max < p.m_min + 1 || p.m_max > 64)
         throw QcdError(QCD_EINVAL, "need 1 <= m_min < m_max <= 64");
     if (p.block < 1 || p.block > 16) throw QcdError(QCD_EINVAL, "block must be in [1, 16]");
+    if (p.update_every < 0) throw QcdError(QCD_EINVAL, "update_every must be >= 0");
+    if (p.extraction != QCD_EXTRACT_HARMONIC && p.extraction != QCD_EXTRACT_RITZ)
+        throw QcdError(QCD_EINVAL, "bad extraction");
     if (p.m_max + p.block > 64) throw QcdError(QCD_EINVAL, "need m_max + block <= 64");
     if (p.nu < 0 || p.sap_block_iters < 1 || p.sap_block_iters > 32) throw QcdError(QCD_EINVAL, "bad smoother params");
     if (p.inner_maxiter < 1 || p.inner_maxiter > 64 || p.coarse_maxiter < 1 || p.coarse_maxiter > 200 ||
@@ -804,6 +807,8 @@ struct GD {
     int m = 0;        // current basis size
     int m_fact = 0;   // leading rows of the factored pencil state still valid
     double2* hstate = nullptr;   // L^-1, L^-1 H L^-H of the pencil (ld = mcap) and its FP32 eigenvectors
+    bool ritz = false;           // Rayleigh-Ritz extraction: the pencil with the identity for W^H W
+    double2* Iden = nullptr;     // mcap x mcap identity (Rayleigh-Ritz only)
     int nlock = 0;
     std::vector<double> lam, lres;
 
@@ -825,6 +830,14 @@ struct GD {
         status = (int*)ctx->buf("gd.status", 4 * sizeof(int));
         idx = (int*)ctx->buf("gd.idx", mcap * sizeof(int));
         hstate = B("hstate", (size_t)3 * mcap * mcap);
+        if (ritz) {
+            // V is orthonormal, so V^H Q V s = theta s is the pencil with W^H W -> I
+            Iden = B("Iden", (size_t)mcap * mcap);
+            std::vector<double2> id((size_t)mcap * mcap, make_double2(0, 0));
+            for (int i = 0; i < mcap; ++i) id[(size_t)i * mcap + i] = make_double2(1, 0);
+            CK(cudaMemcpyAsync(Iden, id.data(), id.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+        }
         m_fact = 0;
         CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), ctx->st));
     }
@@ -885,7 +898,7 @@ struct GD {
     // harmonic Ritz pairs of the current basis; returns theta sorted by |theta| with the column index
     void harmonic(std::vector<double>& theta, std::vector<int>& col) {
         if (m_fact > m) m_fact = 0;
-        small_harmonic_eig_inc(G, Hm, m, mcap, m_fact, mu, S, hstate, status, ctx->st);
+        small_harmonic_eig_inc(ritz ? Iden : G, Hm, m, mcap, m_fact, mu, S, hstate, status, ctx->st);
         m_fact = m;
         check_launch("harmonic eig");
         double* hm = (double*)ctx->host(m);
@@ -894,7 +907,7 @@ struct GD {
         theta.resize(m);
         col.resize(m);
         for (int i = 0; i < m; ++i) {
-            theta[i] = hm[i] != 0.0 ? 1.0 / hm[i] : INFINITY;
+            theta[i] = ritz ? hm[i] : (hm[i] != 0.0 ? 1.0 / hm[i] : INFINITY);
             col[i] = i;
         }
         std::sort(col.begin(), col.end(), [&](int a, int b) {
@@ -973,6 +986,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
     GD gd{};
     gd.ctx = ctx;
     gd.n = n;
+    gd.ritz = P.extraction == QCD_EXTRACT_RITZ;
     const int n0 = P.use_mg ? ctx->n_test : P.n_init;
     if (n0 + block > P.m_max) throw QcdError(QCD_EINVAL, "m_max too small for the start basis");
     gd.alloc(P.m_max + block, k + P.m_max + 2 * block + 8, block);
@@ -1025,7 +1039,8 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                 double* hm = (double*)ctx->host(cols.size());
                 CK(cudaMemcpyAsync(hm, gd.mu_ref, cols.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
-                for (size_t q = 0; q < tg.size(); ++q) theta[tg[q]] = hm[q] != 0.0 ? 1.0 / hm[q] : INFINITY;
+                for (size_t q = 0; q < tg.size(); ++q)
+                    theta[tg[q]] = gd.ritz ? hm[q] : (hm[q] != 0.0 ? 1.0 / hm[q] : INFINITY);
             }
             bool locked = false;
             tsel.clear();
@@ -1072,7 +1087,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
             }
             if (!locked) break;
             if (gd.m == 0) break;
-            if (P.use_mg && gd.nlock >= ctx->n_test && locks_since_update >= P.update_every) {
+            if (P.use_mg && P.update_every > 0 && gd.nlock >= ctx->n_test && locks_since_update >= P.update_every) {
                 std::vector<double> th2;
                 std::vector<int> c2;
                 gd.harmonic(th2, c2);
@@ -1206,6 +1221,7 @@ void qcd_default_params(qcd_params* p) {
     p->n_init = 8;
     p->shift_rho = 1;
     p->update_every = 1;
+    p->extraction = QCD_EXTRACT_HARMONIC;
     p->max_outer = 100000;
     p->seed = 20200417ull;
     p->verbose = 0;

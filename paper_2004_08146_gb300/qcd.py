@@ -18,6 +18,7 @@ QCD_OP_D, QCD_OP_Q = 0, 1
 QCD_FP64, QCD_FP32 = 0, 1
 QCD_MIXED = 1
 QCD_SMOOTHER_SAP, QCD_SMOOTHER_GMRES = 0, 1
+QCD_EXTRACT_HARMONIC, QCD_EXTRACT_RITZ = 0, 1
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libqcd.so not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -48,6 +49,7 @@ class qcd_params(ctypes.Structure):
         ("n_init", ctypes.c_int),
         ("shift_rho", ctypes.c_int),
         ("update_every", ctypes.c_int),
+        ("extraction", ctypes.c_int),
         ("max_outer", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
         ("verbose", ctypes.c_int),

@@ -79,3 +79,19 @@ def test_gd_other_seeds_complete_c1(c1, precision):
         assert rc == qcd.QCD_OK and info.converged
         assert np.max(np.abs(lam - ev[:k]) / np.abs(ev[:k])) < 1e-10, seed
         ctx.close()
+
+
+def test_gd_without_interpolation_updates_c1(c1):
+    """update_every = 0 keeps the setup interpolation for the whole run (the
+    no-update variant of Sec. 4): no rebuilds, same eigenpairs."""
+    from paper_2004_08146_gb300 import qcd
+    torch = torch_cuda()
+    U, op, ev = c1
+    ctx = make_ctx(U, DIMS, -0.2, 1.0, precision=1, update_every=0)
+    ctx.qcd_mg_setup(8, (2, 2, 2, 2))
+    k = 12
+    V = torch.zeros(k * op.n, dtype=torch.complex128, device="cuda")
+    rc, lam, info = ctx.qcd_eigs(k, 1e-8, V)
+    assert rc == qcd.QCD_OK and info.converged
+    assert info.updates == 0
+    _check(op, ev, lam, host(V).reshape(k, -1), k)

@@ -84,3 +84,20 @@ def test_gd_c1_matches_dense_eig():
         u = res.X[:, j]
         assert abs(np.linalg.norm(u) - 1) < 1e-12
         assert np.linalg.norm(Q(u) - res.lam[j] * u) <= 1e-8
+
+
+def test_rayleigh_ritz_galerkin_condition():
+    """Rayleigh-Ritz pairs (Sec. 3): A u - theta u is orthogonal to span(V)
+    for u = V s, and an invariant subspace gives exact eigenpairs."""
+    n, m = 60, 8
+    A = _herm(n, 3)
+    V, _ = np.linalg.qr(synth.complex_gaussian((n, m), 4))
+    theta, S = gd.rayleigh_ritz(V, A @ V)
+    assert np.all(np.diff(np.abs(theta)) >= 0)
+    for k in range(m):
+        u = V @ S[:, k]
+        assert np.linalg.norm(V.conj().T @ (A @ u - theta[k] * u)) < 1e-12 * np.linalg.norm(A)
+    w, Y = np.linalg.eigh(A)
+    theta2, S2 = gd.rayleigh_ritz(Y[:, 10:18], A @ Y[:, 10:18])
+    assert np.max(np.abs(np.sort(theta2) - np.sort(w[10:18]))) < 1e-12 * np.max(np.abs(w))
+
