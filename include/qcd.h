@@ -198,6 +198,14 @@ int qcd_mg_prolong(qcd_ctx* ctx, int prec, int nrhs, const void* xc, void* x);
 int qcd_coarse_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* x, void* y,
                      const double* tau);
 
+/* Local coherence lc(v) = ||Pi v|| / ||v|| (Sec. 3, the local coherence
+ * measure) of nvec FP64 fine vectors V (DEVICE, complex128 [nvec][V*12],
+ * 16-byte aligned) with respect to the current interpolation P; Pi = P P^H is
+ * the orthogonal projection on range(P) (P has orthonormal columns, so
+ * lc(v) = ||P^H v|| / ||v||).  out: HOST array of nvec doubles (0 for v = 0).
+ * Needs qcd_mg_setup or qcd_mg_update_from_eigvecs first (QCD_ENOTSETUP). */
+int qcd_local_coherence(qcd_ctx* ctx, int nvec, const void* V, double* out);
+
 /* Copy P (HOST complex128 [coarse site][chi][i][block site][spin 2][colour 3])
  * and the coarse stencil (HOST complex128 [coarse site][9][row][col];
  * direction 0 = self, 1+mu = +mu, 5+mu = -mu) out of the library. */

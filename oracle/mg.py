@@ -271,6 +271,16 @@ class Interpolation:
         return M
 
 
+def local_coherence(interp, v):
+    """Local coherence measure lc(v) = ||Pi v|| / ||v|| (Sec. 3), with Pi the
+    orthogonal projection on the range of P: Pi v = P (P^H v), P having
+    orthonormal columns (per aggregate and chirality, by construction)."""
+    v = np.asarray(v).reshape(interp.dims + (4, 3))
+    pv = interp.prolong(interp.restrict(v))
+    nv = np.linalg.norm(v)
+    return float(np.linalg.norm(pv) / nv) if nv > 0 else 0.0
+
+
 def gamma5_coarse(nv):
     """Gamma5^c per coarse site: diag(+1 x nv, -1 x nv) (Sec. 2, above Eq. 2.9)."""
     return np.concatenate([np.ones(nv), -np.ones(nv)])

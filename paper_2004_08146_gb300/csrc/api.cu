@@ -1378,6 +1378,35 @@ int qcd_mg_restrict(qcd_ctx* ctx, int prec, int nrhs, const void* r, void* xc) {
     });
 }
 
+int qcd_local_coherence(qcd_ctx* ctx, int nvec, const void* V, double* out) {
+    return guarded(ctx, [&]() {
+        require_mg(ctx);
+        if (nvec < 0 || (nvec > 0 && (!V || !out))) throw QcdError(QCD_EINVAL, "bad arguments");
+        check_align(V, "V");
+        const size_t n = ctx->nfine();
+        const Coarse& c = ctx->c;
+        const size_t nco = (size_t)c.gc.V * c.nc;
+        const int chunk = kMaxRhs;
+        double2* xc = (double2*)ctx->buf("lc.xc", (size_t)chunk * nco * sizeof(double2));
+        double2* dots = (double2*)ctx->buf("lc.dots", (size_t)2 * chunk * sizeof(double2));
+        double2* part = (double2*)ctx->buf("lc.part", (size_t)chunk * 64 * sizeof(double2));
+        for (int j0 = 0; j0 < nvec; j0 += chunk) {
+            const int nb = std::min(chunk, nvec - j0);
+            const double2* v = (const double2*)V + (size_t)j0 * n;
+            mg_restrict(ctx->f, c, QCD_FP64, nb, v, xc, ctx->st);
+            blas_multidot(QCD_FP64, xc, 1, nco, xc, nb, nco, dots, part, ctx->dot_counters(nb), ctx->st);
+            blas_multidot(QCD_FP64, v, 1, n, v, nb, n, dots + chunk, part, ctx->dot_counters(nb), ctx->st);
+            const double2* h = ctx->fetch(dots, 2 * chunk);
+            for (int j = 0; j < nb; ++j) {
+                const double pv = h[j].x, vv = h[chunk + j].x;
+                out[j0 + j] = vv > 0 ? std::sqrt(std::max(pv, 0.0) / vv) : 0.0;
+            }
+        }
+        check_launch("local coherence");
+        return QCD_OK;
+    });
+}
+
 int qcd_mg_prolong(qcd_ctx* ctx, int prec, int nrhs, const void* xc, void* x) {
     return guarded(ctx, [&]() {
         require_mg(ctx);

@@ -162,3 +162,25 @@ def test_two_level_cycle_gmres_smoother(setting, prec, tol):
         x = dev(b, dt)
         ctx.qcd_mg_cycle(form, prec, 1, dev(b, dt), x, tau)
         assert relerr(host(x), ref) < tol, form
+
+
+def test_local_coherence_matches_oracle():
+    """lc(v) = ||Pi v|| / ||v|| (Sec. 3) through the C ABI against the oracle's
+    projection P (P^H v): eigenvectors of the 4^4 Q, with P built from the 24
+    eigenvectors closest to zero (2^4 aggregates, as in the paper's 4^4 study)."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, 1001)
+    op = WilsonClover(U, -0.2, 1.0)
+    w, Y = np.linalg.eigh(op.dense('Q'))
+    near = np.argsort(np.abs(w))[:24]
+    vecs = Y[:, near].T.reshape((24,) + dims + (4, 3))
+    ctx = make_ctx(U, dims, -0.2, 1.0, sap_block=(2, 2, 2, 2), precision=0)
+    ctx.qcd_mg_update_from_eigvecs(dev(vecs), 24)
+    interp = mg.Interpolation(dims, (2, 2, 2, 2), vecs)
+    pick = np.arange(0, 3072, 16)
+    sample = Y[:, pick].T.copy()
+    got = ctx.qcd_local_coherence(len(pick), dev(sample))
+    ref = np.array([mg.local_coherence(interp, sample[j]) for j in range(len(pick))])
+    assert np.max(np.abs(got - ref)) < 1e-12
+    own = ctx.qcd_local_coherence(24, dev(vecs))
+    assert np.max(np.abs(own - 1.0)) < 1e-12

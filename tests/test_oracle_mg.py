@@ -247,3 +247,23 @@ def test_two_level_cycle_exact_coarse(setting):
     Dc = P.conj().T @ D @ P
     ref = P @ np.linalg.solve(Dc, P.conj().T @ b.reshape(-1))
     assert np.linalg.norm(got - ref) < 1e-10 * np.linalg.norm(ref)
+
+
+def test_local_coherence_measure():
+    """lc(v) = ||Pi v|| / ||v|| (Sec. 3): 1 on the test vectors and on the range
+    of P, P^H P = I (so Pi is an orthogonal projection), and for random
+    vectors lc^2 averages to rank(P) / N = 768 / 3072 (the no-coherence value
+    the paper quotes for this 4^4 setting with 24 vectors and 2^4 aggregates)."""
+    dims = (4, 4, 4, 4)
+    vecs = synth.spinor(dims, 71, nvec=24)
+    interp = mg.Interpolation(dims, (2, 2, 2, 2), vecs)
+    Pd = interp.dense()
+    assert Pd.shape == (3072, 768)
+    assert np.max(np.abs(Pd.conj().T @ Pd - np.eye(768))) < 1e-12
+    for j in range(0, 24, 5):
+        assert abs(mg.local_coherence(interp, vecs[j]) - 1.0) < 1e-12
+    xc = synth.complex_gaussian((16, 2, 24), 72)
+    assert abs(mg.local_coherence(interp, interp.prolong(xc)) - 1.0) < 1e-12
+    rnd = synth.spinor(dims, 73, nvec=32)
+    lc2 = np.array([mg.local_coherence(interp, rnd[j]) ** 2 for j in range(32)])
+    assert abs(lc2.mean() - 0.25) < 0.02
