@@ -70,3 +70,22 @@ def test_calls_without_gauge_fail_cleanly():
         ctx.qcd_mg_setup(0, (2, 2, 2, 2))
     assert e.value.code == qcd.QCD_EINVAL
     ctx.close()
+
+
+@pytest.mark.parametrize("bad", [dict(extraction=2), dict(update_every=-1), dict(block=0),
+                                 dict(m_max=60, block=8), dict(sap_block_iters=0)])
+def test_create_rejects_each_bad_field(bad):
+    """Parameter validation happens in qcd_create, on the host, before any GPU work."""
+    from paper_2004_08146_gb300 import qcd
+    with pytest.raises(qcd.QcdError) as e:
+        qcd.Context(params=qcd.default_params(**bad))
+    assert e.value.code == qcd.QCD_EINVAL
+
+
+def test_default_params_method_variants():
+    """Defaults: harmonic Ritz extraction, interpolation update after every lock
+    (Algorithm 2), Rayleigh-quotient shift, two targets per outer iteration."""
+    from paper_2004_08146_gb300 import qcd
+    p = qcd.default_params()
+    assert p.extraction == qcd.QCD_EXTRACT_HARMONIC and p.update_every == 1
+    assert p.shift_rho == 1 and p.block == 2
