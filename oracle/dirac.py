@@ -230,3 +230,95 @@ def clover_blocks(C):
     out[..., 0, :, :] = C[..., :6, :6]
     out[..., 1, :, :] = C[..., 6:, 6:]
     return out
+
+
+# ---------------------------------------------------------------- derivative along a link direction
+# The eigenvalue derivative of the differentiation workload: links move as
+# U_mu(x) -> exp(i eps X_mu(x)) U_mu(x) with X traceless Hermitian, so
+# dU/deps at eps = 0 is i X U.  The operator of Eq. 2.5 plus the clover term is
+# linear in each link of the hop terms and a sum of four-link products in the
+# clover leaves; its derivative follows by the product rule.  For a simple
+# eigenvalue lambda of the Hermitian Q with unit eigenvector v,
+# d lambda / d eps = v^H (dQ/d eps) v (Hellmann-Feynman).
+
+def _dag_pair(p):
+    return _dag(p[0]), _dag(p[1])
+
+
+def _shift_pair(p, mu, sign):
+    return shift_field(p[0], mu, sign), shift_field(p[1], mu, sign)
+
+
+def _product_rule(pairs):
+    """(A1 A2 ... Ak, d(A1 A2 ... Ak)) from (Ai, dAi) pairs."""
+    P, dP = pairs[0]
+    for M, dM in pairs[1:]:
+        dP = dP @ M + P @ dM
+        P = P @ M
+    return P, dP
+
+
+def plaquette_leaves_tangent(U, dU, mu, nu):
+    """d Q_{mu nu}(x) along dU: the four leaves of ``plaquette_leaves``
+    differentiated factor by factor."""
+    Umu = (U[..., mu, :, :], dU[..., mu, :, :])
+    Unu = (U[..., nu, :, :], dU[..., nu, :, :])
+    S = _shift_pair
+    D = _dag_pair
+    Umu_m = S(Umu, mu, -1)
+    Unu_m = S(Unu, nu, -1)
+    leaves = [
+        [Umu, S(Unu, mu, +1), D(S(Umu, nu, +1)), D(Unu)],
+        [Unu, D(S(S(Umu, nu, +1), mu, -1)), D(S(Unu, mu, -1)), Umu_m],
+        [D(Umu_m), D(S(S(Unu, mu, -1), nu, -1)), S(S(Umu, mu, -1), nu, -1), Unu_m],
+        [D(Unu_m), S(Umu, nu, -1), S(S(Unu, mu, +1), nu, -1), D(Umu)],
+    ]
+    return sum(_product_rule(l)[1] for l in leaves)
+
+
+def clover_field_tangent(U, dU, csw):
+    """dC/deps of ``clover_field`` along dU (dims + (12, 12))."""
+    dims = U.shape[:4]
+    dC = np.zeros(dims + (12, 12), dtype=np.complex128)
+    if csw == 0.0:
+        return dC
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            dQ = plaquette_leaves_tangent(U, dU, mu, nu)
+            dF = (dQ - _dag(dQ)) / 8.0
+            dC += np.einsum('st,...ab->...satb', sigma_munu(mu, nu), dF).reshape(dims + (12, 12))
+    return dC * (csw * 0.5j)
+
+
+def link_tangent(U, X):
+    """dU/deps = i X U for U_mu(x) -> exp(i eps X_mu(x)) U_mu(x)."""
+    return 1j * np.einsum('...ab,...bc->...ac', X, U)
+
+
+def operator_tangent(op, X):
+    """Callable psi -> (dD/deps) psi for the WilsonClover ``op`` along X: the
+    hop terms of Eq. 2.5 with dU in place of U (the (m0 + 4) term is constant)
+    plus the clover derivative."""
+    dU = link_tangent(op.U, X)
+    dC = clover_field_tangent(op.U, dU, op.csw)
+    dUb = [shift_field(dU[..., mu, :, :], mu, -1) for mu in range(4)]
+
+    def apply(psi):
+        out = np.einsum('...ij,...j->...i', dC, psi.reshape(psi.shape[:-2] + (12,))).reshape(psi.shape)
+        for mu in range(4):
+            nb = hop_spinor(psi, mu, +1, op.antiperiodic_t)
+            Up = _cmul(dU[..., mu, :, :], nb)
+            out = out - 0.5 * (Up - _smul(GAMMA[mu], Up))
+            nb = hop_spinor(psi, mu, -1, op.antiperiodic_t)
+            Up = _cmul(_dag(dUb[mu]), nb)
+            out = out - 0.5 * (Up + _smul(GAMMA[mu], Up))
+        return out
+    return apply
+
+
+def eigenvalue_derivative(op, X, v):
+    """Hellmann-Feynman d lambda / d eps = Re v^H Gamma5 (dD/deps) v for a unit
+    eigenvector v of Q = Gamma5 D with a simple eigenvalue."""
+    v = np.asarray(v).reshape(op.dims + (4, 3))
+    dv = operator_tangent(op, X)(v)
+    return float(np.real(np.vdot(v, WilsonClover.g5(dv))) / np.real(np.vdot(v, v)))

@@ -218,3 +218,50 @@ def test_clover_constant_abelian_field():
     C = clover_field(U, csw)
     ref = 0.5 * csw * np.kron(sigma_munu(1, 2), np.diag([np.sin(B), -np.sin(B), 0.0]))
     assert np.max(np.abs(C - ref)) < 1e-14
+
+
+def _moved_links(U, X, eps):
+    """U_mu(x) -> exp(i eps X_mu(x)) U_mu(x), the exponential through numpy's
+    Hermitian eigendecomposition."""
+    w, Y = np.linalg.eigh(X)
+    E = np.einsum('...ab,...b,...cb->...ac', Y, np.exp(1j * eps * w), np.conj(Y))
+    return np.einsum('...ab,...bc->...ac', E, U)
+
+
+def test_operator_tangent_matches_central_difference():
+    """dD/deps along a random su(3) direction field (product rule through the
+    hop terms and every clover leaf) against a central difference of the whole
+    operator rebuilt at U(+h) and U(-h), antiperiodic time, csw = 1.5."""
+    from oracle.dirac import operator_tangent
+    dims = (4, 4, 2, 2)
+    U = synth.gauge_field(dims, 0.5, 81)
+    X = synth.su3_directions(dims, 82, 1)[0]
+    psi = synth.spinor(dims, 83)
+    op = WilsonClover(U, -0.3, 1.5)
+    got = operator_tangent(op, X)(psi)
+    h = 1e-4
+    Dp = WilsonClover(_moved_links(U, X, h), -0.3, 1.5).D(psi)
+    Dm = WilsonClover(_moved_links(U, X, -h), -0.3, 1.5).D(psi)
+    fd = (Dp - Dm) / (2 * h)
+    assert np.linalg.norm(got - fd) < 1e-7 * np.linalg.norm(fd)
+
+
+def test_hellmann_feynman_matches_eigenvalue_difference():
+    """d lambda_k / d eps (Hellmann-Feynman with the operator tangent) against a
+    central difference of the dense eigenvalues of Q at U(+-h), for the five
+    eigenvalues of smallest modulus (simple for this random field)."""
+    from oracle.dirac import eigenvalue_derivative
+    dims = (4, 4, 2, 2)
+    U = synth.gauge_field(dims, 0.5, 91)
+    X = synth.su3_directions(dims, 92, 1)[0]
+    op = WilsonClover(U, -0.3, 1.5)
+    w, Y = np.linalg.eigh(op.dense('Q'))
+    order = np.argsort(np.abs(w))[:5]
+    h = 1e-5
+    wp = np.linalg.eigvalsh(WilsonClover(_moved_links(U, X, h), -0.3, 1.5).dense('Q'))
+    wm = np.linalg.eigvalsh(WilsonClover(_moved_links(U, X, -h), -0.3, 1.5).dense('Q'))
+    for k in order:
+        assert np.min(np.abs(np.delete(w, k) - w[k])) > 1e-6          # simple eigenvalue
+        fd = (wp[k] - wm[k]) / (2 * h)                                  # eigvalsh keeps the ascending order
+        hf = eigenvalue_derivative(op, X, Y[:, k])
+        assert abs(hf - fd) <= 1e-6 * max(abs(fd), 1e-3)
