@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--local-coherence", action="store_true",
                     help="lc(v) of all 3072 eigenvectors of the 4^4 Q for the 128 interpolation sets "
                          "of 24 consecutive eigenpairs (block averages), then exit")
+    ap.add_argument("--gradient", action="store_true",
+                    help="eigenvalue derivatives of the 20 smallest |lambda| on a 16^4 field along 16 su(3) "
+                         "directions, checked by central differences of Rayleigh quotients; then exit")
     ap.add_argument("--only-stencil", action="store_true",
                     help="run and print only the fine-stencil bandwidth measurement")
     ap.add_argument("--k", type=int, default=None,
@@ -231,6 +234,9 @@ def main():
     n = int(np.prod(dims)) * 12
     stream = torch.cuda.Stream(devn)
     sp = stream.cuda_stream
+    if args.gradient:
+        print(json.dumps({"gradient": gradient_study(qcd, synth, torch, devn, stream)}), flush=True)
+        return
     if args.local_coherence:
         print(json.dumps({"local_coherence": local_coherence_study(qcd, synth, torch, devn, stream)}), flush=True)
         return
@@ -387,6 +393,60 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def gradient_study(qcd, synth, torch, devn, stream):
+    """Differentiation workload: 16^4 field (eps 0.5, csw 1.5; m0 = -0.85 as in
+    the 16x8^3 workload, not retuned), the 20 smallest-|lambda| eigenpairs from
+    the GPU eigensolver (two-level MG, 4^4 aggregates, Nv = 8), then d lambda_k / d eps along 16 random su(3)
+    directions X (U -> exp(i eps X) U).  Each derivative is checked against
+    the central difference (h = 1e-6) of the Rayleigh quotient v_k^H Q(U(+-h)) v_k,
+    whose derivative at eps = 0 is the same Hellmann-Feynman expression."""
+    dims = (16, 16, 16, 16)
+    k, ndir, h = 20, 16, 1e-6
+    U = synth.gauge_field(dims, 0.5, 1007)
+    n = 12 * int(np.prod(dims))
+    p = qcd.default_params(sap_block=(2, 2, 2, 2))
+    ctx = qcd.Context(params=p, stream=stream.cuda_stream)
+    ctx.qcd_set_gauge(U, dims, -0.85, 1.5)
+    V = torch.zeros(k * n, dtype=torch.complex128, device=devn)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.qcd_mg_setup(8, (4, 4, 4, 4))        # 4^4 aggregates: a 4^4 coarse lattice
+    rc, lam, info = ctx.qcd_eigs(k, 1e-8, V)
+    torch.cuda.synchronize()
+    t_eigs = time.perf_counter() - t0
+    Vm = V.view(k, n)
+    ctx_fd = qcd.Context(params=qcd.default_params(precision=qcd.QCD_FP64), stream=stream.cuda_stream)
+    QV = torch.empty_like(Vm)
+    worst, t_der = 0.0, 0.0
+
+    def moved(X, eps):   # exp(i eps X) U to O(eps^3) ~ 1e-18 for eps = 1e-6
+        X2 = np.einsum('...ab,...bc->...ac', X, X)
+        E = np.eye(3) + 1j * eps * X - 0.5 * eps * eps * X2
+        return np.einsum('...ab,...bc->...ac', E, U)
+
+    def rayleigh(Um):
+        ctx_fd.qcd_set_gauge(Um, dims, -0.85, 1.5)
+        rq = []
+        for j in range(k):
+            ctx_fd.qcd_apply_Q(Vm[j], QV[j], 0.0)
+            rq.append(torch.vdot(Vm[j], QV[j]).real.item() / torch.vdot(Vm[j], Vm[j]).real.item())
+        return np.array(rq)
+
+    for d in range(ndir):
+        X = synth.su3_directions(dims, 2000 + d, 1)[0]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        der = ctx.qcd_eig_derivative(X, k, V)
+        t_der += time.perf_counter() - t1
+        fd = (rayleigh(moved(X, h)) - rayleigh(moved(X, -h))) / (2 * h)
+        worst = max(worst, float(np.max(np.abs(der - fd) / np.maximum(np.abs(fd), 1e-3))))
+    ctx.close()
+    ctx_fd.close()
+    return {"lattice": "16^4", "k": k, "directions": ndir, "eigs_s": t_eigs, "converged": bool(info.converged),
+            "min_abs_lambda": float(np.min(np.abs(lam))), "derivative_s_per_direction": t_der / ndir,
+            "max_rel_dev_from_central_difference": worst, "h": h}
 
 
 def local_coherence_study(qcd, synth, torch, devn, stream):

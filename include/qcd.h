@@ -198,6 +198,17 @@ int qcd_mg_prolong(qcd_ctx* ctx, int prec, int nrhs, const void* xc, void* x);
 int qcd_coarse_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* x, void* y,
                      const double* tau);
 
+/* Eigenvalue derivatives along a link direction (no counterpart in the paper;
+ * the differentiation form of the eigensolver's operator, Eq. 2.5 plus the
+ * clover term): for links moved as U_mu(x) -> exp(i eps X_mu(x)) U_mu(x),
+ * out[k] = d lambda_k / d eps = v_k^H Gamma5 (dD/d eps) v_k / v_k^H v_k
+ * (Hellmann-Feynman; valid for simple eigenvalues and eigenvectors v_k of Q).
+ * X: HOST complex128 [site][mu][3][3] traceless Hermitian; V: DEVICE
+ * complex128 [nvec][V*12] eigenvectors (16-byte aligned); out: HOST nvec
+ * doubles.  FP64 throughout; dD/d eps is the stencil with dU = i X U and the
+ * product-rule derivative of every clover leaf. */
+int qcd_eig_derivative(qcd_ctx* ctx, const double* X, int nvec, const void* V, double* out);
+
 /* Local coherence lc(v) = ||Pi v|| / ||v|| (Sec. 3, the local coherence
  * measure) of nvec FP64 fine vectors V (DEVICE, complex128 [nvec][V*12],
  * 16-byte aligned) with respect to the current interpolation P; Pi = P P^H is

@@ -1407,6 +1407,39 @@ int qcd_local_coherence(qcd_ctx* ctx, int nvec, const void* V, double* out) {
     });
 }
 
+int qcd_eig_derivative(qcd_ctx* ctx, const double* X, int nvec, const void* V, double* out) {
+    return guarded(ctx, [&]() {
+        require_gauge(ctx);
+        if (nvec < 0 || (nvec > 0 && (!X || !V || !out))) throw QcdError(QCD_EINVAL, "bad arguments");
+        if (nvec == 0) return QCD_OK;
+        check_align(V, "V");
+        const FineOp& f = ctx->f;
+        const size_t n = ctx->nfine(), nl = (size_t)f.g.V * 36;
+        double2* Xd = (double2*)ctx->buf("der.X", nl * sizeof(double2));
+        double2* dU = (double2*)ctx->buf("der.dU", nl * sizeof(double2));
+        double* dA = (double*)ctx->buf("der.dA", (size_t)f.g.V * 72 * sizeof(double));
+        CK(cudaMemcpyAsync(Xd, X, nl * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+        tangent_fields(f, Xd, dU, dA, ctx->st);
+        const int chunk = kMaxRhs;
+        double2* w = (double2*)ctx->buf("der.w", (size_t)chunk * n * sizeof(double2));
+        double2* g5v = (double2*)ctx->buf("der.g5v", (size_t)chunk * n * sizeof(double2));
+        double2* dots = (double2*)ctx->buf("der.dots", (size_t)2 * chunk * sizeof(double2));
+        double2* part = (double2*)ctx->buf("der.part", (size_t)chunk * 64 * sizeof(double2));
+        for (int j0 = 0; j0 < nvec; j0 += chunk) {
+            const int nb = std::min(chunk, nvec - j0);
+            const double2* v = (const double2*)V + (size_t)j0 * n;
+            apply_tangent(f, dU, dA, nb, v, w, ctx->st);
+            blas_gamma5(QCD_FP64, v, g5v, (size_t)f.g.V * nb, ctx->st);
+            blas_multidot(QCD_FP64, g5v, 1, n, w, nb, n, dots, part, ctx->dot_counters(nb), ctx->st);
+            blas_multidot(QCD_FP64, v, 1, n, v, nb, n, dots + chunk, part, ctx->dot_counters(nb), ctx->st);
+            const double2* h = ctx->fetch(dots, 2 * chunk);
+            for (int j = 0; j < nb; ++j) out[j0 + j] = h[chunk + j].x > 0 ? h[j].x / h[chunk + j].x : 0.0;
+        }
+        check_launch("eig derivative");
+        return QCD_OK;
+    });
+}
+
 int qcd_mg_prolong(qcd_ctx* ctx, int prec, int nrhs, const void* xc, void* x) {
     return guarded(ctx, [&]() {
         require_mg(ctx);

@@ -117,6 +117,92 @@ __global__ void clover_build_kernel(const double2* __restrict__ U, Geom g, doubl
     }
 }
 
+// ------------------------------------------------------------------ derivative along a link direction
+// Links move as U_mu(x) -> exp(i eps X_mu(x)) U_mu(x) (X traceless Hermitian),
+// so dU/deps = i X U.  The operator is linear in the links of its hop terms, so
+// their derivative is the stencil with dU; the clover leaves are four-link
+// products, differentiated factor by factor below.
+__global__ void link_tangent_kernel(const double2* __restrict__ U, const double2* __restrict__ X,
+                                    double2* __restrict__ dU, int V) {
+    const size_t nl = (size_t)V * 4;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nl; e += (size_t)gridDim.x * blockDim.x) {
+        const double2* u = U + e * 9;
+        const double2* x = X + e * 9;
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+                double2 acc = make_double2(0, 0);
+                for (int b = 0; b < 3; ++b) acc += x[a * 3 + b] * u[b * 3 + c];
+                dU[e * 9 + a * 3 + c] = make_double2(-acc.y, acc.x);   // i * acc
+            }
+    }
+}
+
+struct M3T { M3<double> m, d; };   // a matrix and its derivative
+__device__ __forceinline__ M3T m3t_mul(const M3T& x, const M3T& y) {
+    M3T r;
+    r.m = m3_mul(x.m, y.m);
+    const M3<double> a = m3_mul(x.d, y.m), b = m3_mul(x.m, y.d);
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) r.d.e[i][j] = a.e[i][j] + b.e[i][j];
+    return r;
+}
+__device__ __forceinline__ M3T m3t_dag(const M3T& x) { return M3T{m3_dag(x.m), m3_dag(x.d)}; }
+
+// Packed derivative of the clover blocks (no constant diagonal), same layout
+// and conventions as clover_build_kernel.
+__global__ void clover_tangent_kernel(const double2* __restrict__ U, const double2* __restrict__ dU, Geom g,
+                                      double csw, double* __restrict__ dA) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    int x[4];
+    site_coords(g, s, x);
+    double2 C[2][6][6];
+    for (int chi = 0; chi < 2; ++chi)
+        for (int i = 0; i < 6; ++i) for (int j = 0; j < 6; ++j) C[chi][i][j] = make_double2(0, 0);
+    if (csw != 0.0) {
+        for (int mu = 0; mu < 4; ++mu) {
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                auto L = [&](int site, int d) {
+                    return M3T{m3_load(U + ((size_t)site * 4 + d) * 9), m3_load(dU + ((size_t)site * 4 + d) * 9)};
+                };
+                const M3T Umu = L(s, mu), Unu = L(s, nu);
+                const M3T Umu_m = L(shifted(g, x, mu, -1, nu, 0), mu);
+                const M3T Unu_m = L(shifted(g, x, mu, 0, nu, -1), nu);
+                const M3T l1 = m3t_mul(m3t_mul(Umu, L(shifted(g, x, mu, 1, nu, 0), nu)),
+                                       m3t_mul(m3t_dag(L(shifted(g, x, mu, 0, nu, 1), mu)), m3t_dag(Unu)));
+                const M3T l2 = m3t_mul(m3t_mul(Unu, m3t_dag(L(shifted(g, x, mu, -1, nu, 1), mu))),
+                                       m3t_mul(m3t_dag(L(shifted(g, x, mu, -1, nu, 0), nu)), Umu_m));
+                const M3T l3 = m3t_mul(m3t_mul(m3t_dag(Umu_m), m3t_dag(L(shifted(g, x, mu, -1, nu, -1), nu))),
+                                       m3t_mul(L(shifted(g, x, mu, -1, nu, -1), mu), Unu_m));
+                const M3T l4 = m3t_mul(m3t_mul(m3t_dag(Unu_m), L(shifted(g, x, mu, 0, nu, -1), mu)),
+                                       m3t_mul(L(shifted(g, x, mu, 1, nu, -1), nu), m3t_dag(Umu)));
+                double2 F[3][3];
+                for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+                    const double2 q = l1.d.e[a][b] + l2.d.e[a][b] + l3.d.e[a][b] + l4.d.e[a][b];
+                    const double2 qh = conj(l1.d.e[b][a] + l2.d.e[b][a] + l3.d.e[b][a] + l4.d.e[b][a]);
+                    F[a][b] = 0.125 * (q - qh);
+                }
+                for (int chi = 0; chi < 2; ++chi) {
+                    double2 S[2][2];
+                    sigma_block(mu, nu, chi, S);
+                    for (int si = 0; si < 2; ++si) for (int sj = 0; sj < 2; ++sj)
+                        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b)
+                            C[chi][si * 3 + a][sj * 3 + b] += S[si][sj] * F[a][b];
+                }
+            }
+        }
+    }
+    for (int chi = 0; chi < 2; ++chi) {
+        double* out = dA + (size_t)s * 72 + 36 * chi;
+        for (int i = 0; i < 6; ++i) out[i] = mul_ipow(0.5 * csw * C[chi][i][i], 1).x;
+        for (int i = 0; i < 6; ++i) for (int j = i + 1; j < 6; ++j) {
+            const double2 v = mul_ipow(0.5 * csw * C[chi][i][j], 1);
+            const int o = herm_off(i, j);
+            out[o] = v.x;
+            out[o + 1] = v.y;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ stencil
 // out_j = op(tau_j) in_j, or out_j = b_j - op(tau_j) in_j when b != nullptr.
 // op = QCD_OP_D: D - tau Gamma5 ; op = QCD_OP_Q: Gamma5 D - tau.
@@ -305,6 +391,26 @@ void launch_dirac(const FineOp& f, int op, int nrhs, const void* in, void* out, 
     }
     wilson_clover_kernel<R><<<grid, 128, 0, st>>>((cplx<R>*)out, (const cplx<R>*)in, (const cplx<R>*)b,
                                                   U, A, f.g, op, sh, (size_t)f.g.V * 12, act);
+}
+
+void tangent_fields(const FineOp& f, const double2* X, double2* dU, double* dA, cudaStream_t st) {
+    {
+        KTimer kt("link_tangent", 0.0, 0.0, st);
+        link_tangent_kernel<<<1216, 256, 0, st>>>(f.U64, X, dU, f.g.V);
+    }
+    KTimer kt("clover_tangent", 0.0, 0.0, st);
+    clover_tangent_kernel<<<(f.g.V + 127) / 128, 128, 0, st>>>(f.U64, dU, f.g, f.csw, dA);
+}
+
+void apply_tangent(const FineOp& f, const double2* dU, const double* dA, int nrhs, const double2* in, double2* out,
+                   cudaStream_t st) {
+    // the hop terms with dU and the clover derivative: the stencil with these
+    // fields in place of U and (m0 + 4) + C, shift 0
+    Shifts sh{};
+    dim3 grid((f.g.V + 127) / 128, nrhs);
+    KTimer kt("wilson_tangent_f64", 0.0, 1824.0 * f.g.V * nrhs, st);
+    wilson_clover_kernel<double><<<grid, 128, 0, st>>>(out, in, nullptr, dU, dA, f.g, QCD_OP_D, sh,
+                                                       (size_t)f.g.V * 12, nullptr);
 }
 
 void apply_op(const FineOp& f, int prec, int op, int nrhs, const void* in, void* out,

@@ -92,6 +92,12 @@ struct Coarse {
 void launch_clover_build(const FineOp& f, cudaStream_t st);
 // `act` (device, per right-hand side, may be null): skip right-hand sides
 // whose flag is 0 (converged systems of a batched Krylov solve).
+// dU = i X U (V*36 double2) and the packed clover derivative dA (V*72 double)
+// for U -> exp(i eps X) U (X: device FP64 traceless Hermitian [V][4][3][3]);
+// then out_j = (dD/deps) in_j, FP64.
+void tangent_fields(const FineOp& f, const double2* X, double2* dU, double* dA, cudaStream_t st);
+void apply_tangent(const FineOp& f, const double2* dU, const double* dA, int nrhs, const double2* in, double2* out,
+                   cudaStream_t st);
 void apply_op(const FineOp& f, int prec, int op, int nrhs, const void* in, void* out,
               const double* tau, cudaStream_t st, const int* act = nullptr);
 void residual_op(const FineOp& f, int prec, int op, int nrhs, const void* b, const void* x, void* r,

@@ -99,6 +99,7 @@ _SIGS = {
     "qcd_mg_restrict": (_I, [_P, _I, _I, _P, _P]),
     "qcd_mg_prolong": (_I, [_P, _I, _I, _P, _P]),
     "qcd_local_coherence": (_I, [_P, _I, _P, _DP]),
+    "qcd_eig_derivative": (_I, [_P, _DP, _I, _P, _DP]),
     "qcd_coarse_apply": (_I, [_P, _I, _I, _I, _P, _P, _DP]),
     "qcd_mg_get_P": (_I, [_P, _DP]),
     "qcd_mg_get_coarse": (_I, [_P, _DP]),
@@ -243,6 +244,13 @@ class Context:
 
     def qcd_mg_restrict(self, prec, nrhs, r, xc):
         return self._check(_lib.qcd_mg_restrict(self.h, prec, nrhs, _ptr(r), _ptr(xc)))
+
+    def qcd_eig_derivative(self, X, nvec, V):
+        Xh = np.ascontiguousarray(np.asarray(X, dtype=np.complex128)).view(np.float64)
+        out = np.zeros(int(nvec), dtype=np.float64)
+        self._check(_lib.qcd_eig_derivative(self.h, Xh.ctypes.data_as(_DP), int(nvec), _ptr(V),
+                                            out.ctypes.data_as(_DP)))
+        return out
 
     def qcd_local_coherence(self, nvec, V):
         out = np.zeros(int(nvec), dtype=np.float64)
