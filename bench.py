@@ -428,11 +428,11 @@ def gradient_study(qcd, synth, torch, devn, stream):
 
     def rayleigh(Um):
         ctx_fd.qcd_set_gauge(Um, dims, -0.85, 1.5)
-        rq = []
         for j in range(k):
             ctx_fd.qcd_apply_Q(Vm[j], QV[j], 0.0)
-            rq.append(torch.vdot(Vm[j], QV[j]).real.item() / torch.vdot(Vm[j], Vm[j]).real.item())
-        return np.array(rq)
+        torch.cuda.synchronize()      # the library's stream is not torch's
+        return np.array([torch.vdot(Vm[j], QV[j]).real.item() / torch.vdot(Vm[j], Vm[j]).real.item()
+                         for j in range(k)])
 
     for d in range(ndir):
         X = synth.su3_directions(dims, 2000 + d, 1)[0]
@@ -472,6 +472,7 @@ def local_coherence_study(qcd, synth, torch, devn, stream):
         E.zero_()
         for j in range(16):
             E[j * N + c0 + j] = 1.0
+        torch.cuda.synchronize()      # E is written on torch's stream, read on the library's
         ctx.qcd_apply(qcd.QCD_OP_Q, qcd.QCD_FP64, 16, E, out, [0.0] * 16)
         torch.cuda.synchronize()
         Qd[:, c0:c0 + 16] = out.cpu().numpy().reshape(16, N).T
@@ -544,6 +545,7 @@ def smoother_sweep(qcd, synth, torch, devn, stream):
             ctx.qcd_set_gauge(U, dims, m0, csw)
             ctx.qcd_mg_setup(8, (2, 2, 2, 2))
             x = torch.zeros_like(b)
+            torch.cuda.synchronize()
             ctx.qcd_shifted_solve(b, x, 0.0, 1e-8)            # warm-up
             # shifts across the wanted part of the spectrum (the 50 smallest
             # |lambda| of the 16x8^3 workload reach 0.25); beyond it the
