@@ -9,16 +9,16 @@ package imports nothing from the product package.
 
 Modules
 -------
-dirac   Wilson-clover operator D, Gamma5, Q = Gamma5 D (Sec. 2, Eq. 2.4, 2.5, 2.7)
+dirac   Wilson-clover operator D, Gamma5, Q = Gamma5 D (Sec. 2, Eq. 2.4, 2.5, 2.7);
+        its derivative along su(3) link directions and the Hellmann-Feynman
+        eigenvalue derivative (pinned by central differences)
 mg      aggregation interpolation P, restriction P^H, Galerkin coarse operator
-        D_c = P^H D P, SAP smoother, GMRES/FGMRES and the two-level cycle
-        E_2g (Sec. 2, Eq. 2.8-2.11, Prop. 1)
-gd      generalized Davidson with harmonic Ritz extraction, thick restart,
-        locking and interpolation updates (Sec. 3, Algorithm 1, Algorithm 2,
-        Theorem 1, Eq. 3.4-3.6)
-grad    Hellmann-Feynman eigenvalue gradients dlambda/dU (derivative of the
-        operator of Eq. 2.4 plus the clover term) -- parity unpinned only for
-        the clover-force convention, see the module header.
+        D_c = P^H D P, SAP smoother, GMRES/FGMRES, the two-level cycle
+        E_2g (Sec. 2, Eq. 2.8-2.11, Prop. 1) and the local coherence measure
+        (Sec. 3)
+gd      generalized Davidson with harmonic (or Rayleigh-Ritz) extraction,
+        thick restart, locking and interpolation updates (Sec. 3,
+        Algorithm 1, Algorithm 2, Theorem 1, Eq. 3.4-3.6)
 
 Every function cites the passage it restates.  Readings taken where the paper
 is silent are stated in the function docstrings.
