@@ -401,7 +401,9 @@ def gradient_study(qcd, synth, torch, devn, stream):
     the GPU eigensolver (two-level MG, 4^4 aggregates, Nv = 8), then d lambda_k / d eps along 16 random su(3)
     directions X (U -> exp(i eps X) U).  Each derivative is checked against
     the central difference (h = 1e-6) of the Rayleigh quotient v_k^H Q(U(+-h)) v_k,
-    whose derivative at eps = 0 is the same Hellmann-Feynman expression."""
+    whose derivative at eps = 0 is the same Hellmann-Feynman expression.  The
+    per-link forces of all 20 eigenvalues are timed once and contracted with
+    every direction against the directional derivatives."""
     dims = (16, 16, 16, 16)
     k, ndir, h = 20, 16, 1e-6
     U = synth.gauge_field(dims, 0.5, 1007)
@@ -434,6 +436,17 @@ def gradient_study(qcd, synth, torch, devn, stream):
         return np.array([torch.vdot(Vm[j], QV[j]).real.item() / torch.vdot(Vm[j], Vm[j]).real.item()
                          for j in range(k)])
 
+    # per-link forces of all k eigenvalues (gauge-field layout per eigenvector)
+    nl = 36 * int(np.prod(dims))
+    F = torch.empty(k * nl, dtype=torch.complex128, device=devn)
+    ctx.qcd_eig_force(k, V, F)                  # warm-up (buffers)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ctx.qcd_eig_force(k, V, F)
+    torch.cuda.synchronize()
+    t_force = time.perf_counter() - t1
+    Fm = F.view(k, -1, 3, 3)
+    worst_force = 0.0
     for d in range(ndir):
         X = synth.su3_directions(dims, 2000 + d, 1)[0]
         torch.cuda.synchronize()
@@ -442,11 +455,17 @@ def gradient_study(qcd, synth, torch, devn, stream):
         t_der += time.perf_counter() - t1
         fd = (rayleigh(moved(X, h)) - rayleigh(moved(X, -h))) / (2 * h)
         worst = max(worst, float(np.max(np.abs(der - fd) / np.maximum(np.abs(fd), 1e-3))))
+        # sum_{x,mu} tr(X F_k) must reproduce the directional derivative
+        Xt = torch.from_numpy(np.ascontiguousarray(X).reshape(-1, 3, 3)).to(devn)
+        con = (Xt.unsqueeze(0) * Fm.transpose(-1, -2)).sum(dim=(1, 2, 3)).real.cpu().numpy()
+        worst_force = max(worst_force, float(np.max(np.abs(con - der) / np.maximum(np.abs(der), 1e-3))))
     ctx.close()
     ctx_fd.close()
     return {"lattice": "16^4", "k": k, "directions": ndir, "eigs_s": t_eigs, "converged": bool(info.converged),
             "min_abs_lambda": float(np.min(np.abs(lam))), "derivative_s_per_direction": t_der / ndir,
-            "max_rel_dev_from_central_difference": worst, "h": h}
+            "max_rel_dev_from_central_difference": worst, "h": h,
+            "force_s_per_eigenvector": t_force / k,
+            "max_rel_dev_force_contraction_vs_derivative": worst_force}
 
 
 def local_coherence_study(qcd, synth, torch, devn, stream):

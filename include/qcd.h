@@ -209,6 +209,17 @@ int qcd_coarse_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* x, vo
  * product-rule derivative of every clover leaf. */
 int qcd_eig_derivative(qcd_ctx* ctx, const double* X, int nvec, const void* V, double* out);
 
+/* The same derivative resolved per link (the force of each eigenvalue):
+ * F[k] = the traceless Hermitian 3x3 fields F_mu(x) with
+ * d lambda_k / d eps = sum_{x,mu} tr(X_mu(x) F_mu(x)) for every traceless
+ * Hermitian X, normalised by v_k^H v_k.  Hop terms contribute the colour
+ * outer product of v_k(x + mu) and Gamma5 v_k(x) through the spin projector;
+ * the clover term the plaquettes above and below each link with the clover
+ * insertion at each corner.  V: DEVICE complex128 [nvec][V*12]; F: DEVICE
+ * complex128 [nvec][site][mu][3][3] (gauge-field layout), caller-owned and
+ * overwritten; both 16-byte aligned.  FP64 throughout. */
+int qcd_eig_force(qcd_ctx* ctx, int nvec, const void* V, void* F);
+
 /* Local coherence lc(v) = ||Pi v|| / ||v|| (Sec. 3, the local coherence
  * measure) of nvec FP64 fine vectors V (DEVICE, complex128 [nvec][V*12],
  * 16-byte aligned) with respect to the current interpolation P; Pi = P P^H is

@@ -322,3 +322,73 @@ def eigenvalue_derivative(op, X, v):
     v = np.asarray(v).reshape(op.dims + (4, 3))
     dv = operator_tangent(op, X)(v)
     return float(np.real(np.vdot(v, WilsonClover.g5(dv))) / np.real(np.vdot(v, v)))
+
+
+# ---------------------------------------------------------------- force: the derivative per link
+# The same derivative resolved link by link: a traceless Hermitian 3x3 matrix
+# F_mu(x) per link with d lambda / d eps = sum_{x, mu} tr(X_mu(x) F_mu(x)) for
+# every traceless Hermitian direction field X.  With w = Gamma5 v:
+#
+# * hop terms of Eq. 2.5: the backward hop is the complex conjugate of the
+#   forward one (Q is Hermitian), so both together give -Re tr(dU_mu(x) A_mu(x))
+#   with the colour outer product A = sum_{st} (I - gamma_mu)_{st}
+#   v_t(x + mu) w_s(x)^H (boundary phase included in v(x + mu));
+# * clover term: v^H Gamma5 C v is real, so its derivative is
+#   Re[i c_sw / 16 * sum_x sum_{(rho, nu) ordered} tr(dQ_{rho nu}(x) Bt(x))] with
+#   Bt = B + B^H, B = sum_{st} sigma_{rho nu, st} v_t(x) w_s(x)^H; a link U_rho(y)
+#   sits in the plaquette above it (non-daggered, corner y at the lower left) and
+#   in the one below it (daggered) of each plane (rho, nu), and each plaquette
+#   is a leaf at each of its four corners.
+
+
+def _traceless_hermitian(K):
+    H = 0.5 * (K + _dag(K))
+    tr = np.trace(H, axis1=-2, axis2=-1)
+    return H - tr[..., None, None] * np.eye(3) / 3.0
+
+
+def eigenvalue_force(op, v):
+    """F_mu(x) (dims + (4, 3, 3)), traceless Hermitian, such that
+    d lambda / d eps = sum tr(X_mu(x) F_mu(x)) / (v^H v) along any traceless
+    Hermitian X (links moving as exp(i eps X) U); v a unit-norm-free eigenvector
+    of Q with a simple eigenvalue (Hellmann-Feynman, resolved per link)."""
+    v = np.asarray(v).reshape(op.dims + (4, 3))
+    w = WilsonClover.g5(v)
+    wc = np.conj(w)
+    U = op.U
+    S = shift_field
+    K = np.zeros(op.dims + (4, 3, 3), dtype=np.complex128)
+    I4 = np.eye(4, dtype=np.complex128)
+    for rho in range(4):
+        nb = hop_spinor(v, rho, +1, op.antiperiodic_t)
+        A = np.einsum('st,...ta,...sb->...ab', I4 - GAMMA[rho], nb, wc)
+        K[..., rho, :, :] -= 1j * (U[..., rho, :, :] @ A)
+    if op.csw != 0.0:
+        c = op.csw / 16.0
+        for rho in range(4):
+            for nu in range(4):
+                if nu == rho:
+                    continue
+                B = np.einsum('st,...ta,...sb->...ab', sigma_munu(rho, nu), v, wc)
+                Bt = B + _dag(B)
+                Ur = U[..., rho, :, :]
+                Un = U[..., nu, :, :]
+                # plaquette above U_rho(y): a b c d from y, corners y, y+rho, y+rho+nu, y+nu
+                a = Ur
+                b = S(Un, rho, +1)
+                cc = _dag(S(Ur, nu, +1))
+                d = _dag(Un)
+                B0, B1 = Bt, S(Bt, rho, +1)
+                B2, B3 = S(S(Bt, rho, +1), nu, +1), S(Bt, nu, +1)
+                above = (a @ b @ cc @ d @ B0 + a @ B1 @ b @ cc @ d
+                         + a @ b @ B2 @ cc @ d + a @ b @ cc @ B3 @ d)
+                # plaquette below U_rho(y): path y -> y-nu -> y-nu+rho -> y+rho, then U_rho(y)^H
+                dp = _dag(S(Un, nu, -1))
+                ap = S(Ur, nu, -1)
+                bp = S(S(Un, rho, +1), nu, -1)
+                C0, C1 = Bt, S(Bt, nu, -1)
+                C2, C3 = S(S(Bt, nu, -1), rho, +1), S(Bt, rho, +1)
+                below = (C0 @ dp @ ap @ bp + dp @ C1 @ ap @ bp
+                         + dp @ ap @ C2 @ bp + dp @ ap @ bp @ C3) @ _dag(Ur)
+                K[..., rho, :, :] += c * below - c * above
+    return _traceless_hermitian(K) / float(np.real(np.vdot(v, v)))

@@ -5,4 +5,4 @@ ABI, see ``include/qcd.h``); ``paper_2004_08146_gb300.qcd`` is the thin ctypes
 binding.  Importing this package does not load the library: ``qcd`` raises
 when ``libqcd.so`` is missing, there is no fallback.
 """
-__all__ = ["qcd", "synth", "workloads"]
+__all__ = ["qcd", "synth", "workloads", "autograd"]

@@ -1440,6 +1440,28 @@ int qcd_eig_derivative(qcd_ctx* ctx, const double* X, int nvec, const void* V, d
     });
 }
 
+int qcd_eig_force(qcd_ctx* ctx, int nvec, const void* V, void* F) {
+    return guarded(ctx, [&]() {
+        require_gauge(ctx);
+        if (nvec < 0 || (nvec > 0 && (!V || !F))) throw QcdError(QCD_EINVAL, "bad arguments");
+        if (nvec == 0) return QCD_OK;
+        check_align(V, "V");
+        check_align(F, "F");
+        const FineOp& f = ctx->f;
+        const size_t n = ctx->nfine(), nl = (size_t)f.g.V * 36;
+        double2* Bt = (double2*)ctx->buf("force.Bt", (size_t)f.g.V * 54 * sizeof(double2));
+        double2* nrm = (double2*)ctx->buf("force.nrm", sizeof(double2));
+        double2* part = (double2*)ctx->buf("force.part", (size_t)64 * sizeof(double2));
+        for (int j = 0; j < nvec; ++j) {
+            const double2* v = (const double2*)V + (size_t)j * n;
+            blas_multidot(QCD_FP64, v, 1, n, v, 1, n, nrm, part, ctx->dot_counters(1), ctx->st);
+            eig_force(f, v, nrm, Bt, (double2*)F + (size_t)j * nl, ctx->st);
+        }
+        check_launch("eig force");
+        return QCD_OK;
+    });
+}
+
 int qcd_mg_prolong(qcd_ctx* ctx, int prec, int nrhs, const void* xc, void* x) {
     return guarded(ctx, [&]() {
         require_mg(ctx);

@@ -203,6 +203,141 @@ __global__ void clover_tangent_kernel(const double2* __restrict__ U, const doubl
     }
 }
 
+// ------------------------------------------------------------------ force: the derivative per link
+// F_rho(y) traceless Hermitian with d lambda / d eps = sum tr(X_rho(y) F_rho(y))
+// for every direction field X (links moving as exp(i eps X) U).  With w =
+// Gamma5 v, the hop terms give K = -i U A with the colour outer product
+// A = sum_s ((1 - gamma_rho) v(y + rho))_s w_s(y)^H (the backward hop is its
+// complex conjugate), and the clover term gives, per plane (rho, nu),
+// (c_sw / 16) (below - above): the plaquettes above and below the link with the
+// insertion Bt = B + B^H, B = sum_st sigma_{rho nu, st} v_t w_s^H, placed at
+// each corner.  F is the traceless Hermitian part of K over v^H v.
+
+__device__ __forceinline__ int plane_index(int mu, int nu) {   // mu < nu
+    return mu == 0 ? nu - 1 : (mu == 1 ? nu + 1 : 5);
+}
+
+// Bt_{mu nu}(x) for the six planes mu < nu: [site][plane][3][3].  sigma is
+// block diagonal in chirality and w = +v (spins 0, 1), -v (spins 2, 3).
+__global__ void clover_insertion_kernel(const double2* __restrict__ v, Geom g, double2* __restrict__ Bt) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    double2 p[12];
+    for (int k = 0; k < 12; ++k) p[k] = v[(size_t)s * 12 + k];
+    for (int mu = 0; mu < 4; ++mu)
+        for (int nu = mu + 1; nu < 4; ++nu) {
+            double2 B[3][3];
+            for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) B[a][b] = make_double2(0, 0);
+            for (int chi = 0; chi < 2; ++chi) {
+                double2 S[2][2];
+                sigma_block(mu, nu, chi, S);
+                const double sg = chi == 0 ? 1.0 : -1.0;
+                for (int i = 0; i < 2; ++i) for (int j = 0; j < 2; ++j) {
+                    const double2 c = sg * S[i][j];
+                    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b)
+                        B[a][b] += c * (p[(2 * chi + j) * 3 + a] * conj(p[(2 * chi + i) * 3 + b]));
+                }
+            }
+            double2* o = Bt + ((size_t)s * 6 + plane_index(mu, nu)) * 9;
+            for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) o[a * 3 + b] = B[a][b] + conj(B[b][a]);
+        }
+}
+
+__device__ __forceinline__ M3<double> m3_add(const M3<double>& x, const M3<double>& y) {
+    M3<double> r;
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) r.e[a][b] = x.e[a][b] + y.e[a][b];
+    return r;
+}
+
+// One thread per link (site, rho).  nrm: device v^H v (real part used).
+__global__ void __launch_bounds__(128) link_force_kernel(const double2* __restrict__ U, const double2* __restrict__ v,
+                                                         const double2* __restrict__ Bt, const double2* __restrict__ nrm,
+                                                         Geom g, double csw, double2* __restrict__ F) {
+    const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (e >= (size_t)g.V * 4) return;
+    const int s = (int)(e >> 2), rho = (int)(e & 3);
+    int x[4];
+    site_coords(g, s, x);
+    auto L = [&](int site, int d) { return m3_load(U + ((size_t)site * 4 + d) * 9); };
+    const M3<double> u = L(s, rho);
+    M3<double> K;
+    {
+        // hop: h = up - B dn of the projected neighbour, lower half -B^H h;
+        // A = sum_i h_i v_i^H + (B^H h)_i v_{2+i}^H (w = Gamma5 v flips the lower sign)
+        int neg;
+        const int sf = nb_fwd(g, x, s, rho, neg);
+        const double sg = neg ? -1.0 : 1.0;
+        const SpinMono Bm = kB(rho), BHm = kBH(rho);
+        double2 h[2][3], q[2][3];
+        for (int i = 0; i < 2; ++i) for (int a = 0; a < 3; ++a)
+            h[i][a] = sg * (v[(size_t)sf * 12 + i * 3 + a] -
+                            mul_ipow(v[(size_t)sf * 12 + (2 + Bm.perm[i]) * 3 + a], Bm.ph[i]));
+        for (int i = 0; i < 2; ++i) for (int a = 0; a < 3; ++a) q[i][a] = mul_ipow(h[BHm.perm[i]][a], BHm.ph[i]);
+        M3<double> A;
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+            double2 t = make_double2(0, 0);
+            for (int i = 0; i < 2; ++i)
+                t += h[i][a] * conj(v[(size_t)s * 12 + i * 3 + b]) + q[i][a] * conj(v[(size_t)s * 12 + (2 + i) * 3 + b]);
+            A.e[a][b] = t;
+        }
+        const M3<double> UA = m3_mul(u, A);
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) K.e[a][b] = mul_ipow(UA.e[a][b], 3);   // -i U A
+    }
+    if (csw != 0.0) {
+        const double c = csw / 16.0;
+        for (int nu = 0; nu < 4; ++nu) {
+            if (nu == rho) continue;
+            const int pl = rho < nu ? plane_index(rho, nu) : plane_index(nu, rho);
+            const double sg = rho < nu ? c : -c;   // Bt_{rho nu} = -Bt_{nu rho}
+            auto Bx = [&](int site) { return m3_load(Bt + ((size_t)site * 6 + pl) * 9); };
+            // plaquette above: a b c d from y, corners y, y+rho, y+rho+nu, y+nu
+            M3<double> above;
+            {
+                const M3<double> b = L(shifted(g, x, rho, 1, nu, 0), nu);
+                const M3<double> cm = m3_dag(L(shifted(g, x, rho, 0, nu, 1), rho));
+                const M3<double> d = m3_dag(L(s, nu));
+                const M3<double> cd = m3_mul(cm, d);
+                const M3<double> t1 = m3_add(m3_mul(Bx(shifted(g, x, rho, 0, nu, 1)), d), m3_mul(d, Bx(s)));
+                const M3<double> t2 = m3_add(m3_mul(Bx(shifted(g, x, rho, 1, nu, 1)), cd), m3_mul(cm, t1));
+                const M3<double> t3 = m3_add(m3_mul(Bx(shifted(g, x, rho, 1, nu, 0)), m3_mul(b, cd)), m3_mul(b, t2));
+                above = m3_mul(u, t3);
+            }
+            // plaquette below: path y -> y-nu -> y-nu+rho -> y+rho, then U_rho(y)^H
+            M3<double> below;
+            {
+                const M3<double> dp = m3_dag(L(shifted(g, x, rho, 0, nu, -1), nu));
+                const M3<double> ap = L(shifted(g, x, rho, 0, nu, -1), rho);
+                const M3<double> bp = L(shifted(g, x, rho, 1, nu, -1), nu);
+                const M3<double> apbp = m3_mul(ap, bp);
+                const M3<double> t1 = m3_add(m3_mul(Bx(shifted(g, x, rho, 1, nu, -1)), bp),
+                                             m3_mul(bp, Bx(shifted(g, x, rho, 1, nu, 0))));
+                const M3<double> t2 = m3_add(m3_mul(Bx(shifted(g, x, rho, 0, nu, -1)), apbp), m3_mul(ap, t1));
+                const M3<double> pre = m3_add(m3_mul(Bx(s), m3_mul(dp, apbp)), m3_mul(dp, t2));
+                below = m3_mul(pre, m3_dag(u));
+            }
+            for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b)
+                K.e[a][b] += sg * (below.e[a][b] - above.e[a][b]);
+        }
+    }
+    const double n = nrm[0].x;
+    const double inv = n > 0 ? 1.0 / n : 0.0;
+    double2 H[3][3];
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) H[a][b] = 0.5 * (K.e[a][b] + conj(K.e[b][a]));
+    const double tr = (H[0][0].x + H[1][1].x + H[2][2].x) / 3.0;
+    for (int a = 0; a < 3; ++a) H[a][a].x -= tr;
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) F[e * 9 + a * 3 + b] = inv * H[a][b];
+}
+
+void eig_force(const FineOp& f, const double2* v, const double2* nrm, double2* Bt, double2* F, cudaStream_t st) {
+    {
+        KTimer kt("clover_insertion", 0.0, 0.0, st);
+        clover_insertion_kernel<<<(f.g.V + 127) / 128, 128, 0, st>>>(v, f.g, Bt);
+    }
+    KTimer kt("link_force", 0.0, 0.0, st);
+    const size_t nl = (size_t)f.g.V * 4;
+    link_force_kernel<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(f.U64, v, Bt, nrm, f.g, f.csw, F);
+}
+
 // ------------------------------------------------------------------ stencil
 // out_j = op(tau_j) in_j, or out_j = b_j - op(tau_j) in_j when b != nullptr.
 // op = QCD_OP_D: D - tau Gamma5 ; op = QCD_OP_Q: Gamma5 D - tau.

@@ -98,6 +98,9 @@ void launch_clover_build(const FineOp& f, cudaStream_t st);
 void tangent_fields(const FineOp& f, const double2* X, double2* dU, double* dA, cudaStream_t st);
 void apply_tangent(const FineOp& f, const double2* dU, const double* dA, int nrhs, const double2* in, double2* out,
                    cudaStream_t st);
+// Per-link force of the eigenvalue v^H Q v / v^H v: insertion fields Bt
+// ([V][6][9]) then F ([V][4][9], traceless Hermitian); nrm: device v^H v.
+void eig_force(const FineOp& f, const double2* v, const double2* nrm, double2* Bt, double2* F, cudaStream_t st);
 void apply_op(const FineOp& f, int prec, int op, int nrhs, const void* in, void* out,
               const double* tau, cudaStream_t st, const int* act = nullptr);
 void residual_op(const FineOp& f, int prec, int op, int nrhs, const void* b, const void* x, void* r,

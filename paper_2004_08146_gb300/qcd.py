@@ -100,6 +100,7 @@ _SIGS = {
     "qcd_mg_prolong": (_I, [_P, _I, _I, _P, _P]),
     "qcd_local_coherence": (_I, [_P, _I, _P, _DP]),
     "qcd_eig_derivative": (_I, [_P, _DP, _I, _P, _DP]),
+    "qcd_eig_force": (_I, [_P, _I, _P, _P]),
     "qcd_coarse_apply": (_I, [_P, _I, _I, _I, _P, _P, _DP]),
     "qcd_mg_get_P": (_I, [_P, _DP]),
     "qcd_mg_get_coarse": (_I, [_P, _DP]),
@@ -251,6 +252,9 @@ class Context:
         self._check(_lib.qcd_eig_derivative(self.h, Xh.ctypes.data_as(_DP), int(nvec), _ptr(V),
                                             out.ctypes.data_as(_DP)))
         return out
+
+    def qcd_eig_force(self, nvec, V, F):
+        return self._check(_lib.qcd_eig_force(self.h, int(nvec), _ptr(V), _ptr(F)))
 
     def qcd_local_coherence(self, nvec, V):
         out = np.zeros(int(nvec), dtype=np.float64)

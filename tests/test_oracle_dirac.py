@@ -265,3 +265,46 @@ def test_hellmann_feynman_matches_eigenvalue_difference():
         fd = (wp[k] - wm[k]) / (2 * h)                                  # eigvalsh keeps the ascending order
         hf = eigenvalue_derivative(op, X, Y[:, k])
         assert abs(hf - fd) <= 1e-6 * max(abs(fd), 1e-3)
+
+
+@pytest.mark.parametrize("dims,antip,csw", [((2, 2, 2, 2), True, 1.5), ((4, 2, 2, 4), True, 1.5),
+                                            ((2, 4, 2, 2), False, 0.0), ((4, 4, 2, 2), False, 1.2)])
+def test_force_contracts_to_directional_derivative(dims, antip, csw):
+    """sum_{x,mu} tr(X_mu(x) F_mu(x)) of the per-link force equals the
+    product-rule directional derivative (itself pinned by central differences
+    above) for random su(3) directions; F is traceless Hermitian."""
+    from oracle.dirac import eigenvalue_derivative, eigenvalue_force
+    U = synth.gauge_field(dims, 0.5, 7)
+    op = WilsonClover(U, -0.3, csw, antiperiodic_t=antip)
+    v = synth.spinor(dims, 8)
+    F = eigenvalue_force(op, v)
+    assert np.max(np.abs(F - np.conj(np.swapaxes(F, -1, -2)))) < 1e-15
+    assert np.max(np.abs(np.trace(F, axis1=-2, axis2=-1))) < 1e-15
+    for X in synth.su3_directions(dims, 9, 2):
+        con = np.sum(X * np.swapaxes(F, -1, -2))
+        ref = eigenvalue_derivative(op, X, v)
+        assert abs(con.imag) < 1e-14 and abs(con.real - ref) < 1e-12 * abs(ref)
+
+
+def test_force_single_link_central_difference():
+    """One link moved alone: tr(X F) at that link against the central
+    difference of the Rayleigh quotient v^H Q(U(+-h)) v / v^H v (h = 1e-5),
+    for a time link across the antiperiodic boundary and a spatial link."""
+    from oracle.dirac import eigenvalue_force
+    dims = (4, 2, 2, 2)
+    U = synth.gauge_field(dims, 0.5, 17)
+    op = WilsonClover(U, -0.3, 1.5)
+    v = synth.spinor(dims, 18)
+    F = eigenvalue_force(op, v)
+    Xall = synth.su3_directions(dims, 19, 1)[0]
+    h = 1e-5
+    for site, mu in [((3, 1, 0, 1), 0), ((1, 0, 1, 1), 2)]:
+        X = np.zeros_like(Xall)
+        X[site + (mu,)] = Xall[site + (mu,)]
+
+        def rq(eps):
+            Q = WilsonClover(_moved_links(U, X, eps), -0.3, 1.5).Q(v)
+            return np.real(np.vdot(v, Q)) / np.real(np.vdot(v, v))
+        fd = (rq(h) - rq(-h)) / (2 * h)
+        got = np.real(np.trace(X[site + (mu,)] @ F[site + (mu,)]))
+        assert abs(got - fd) < 1e-8 * max(abs(fd), 1e-3), (site, mu, got, fd)
