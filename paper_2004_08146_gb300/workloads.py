@@ -15,6 +15,14 @@ WORKLOADS = {
     # 16 x 8^3, two-level MG with 2^4 aggregates, Nv = 8, SAP on 2^4 blocks, 50 pairs
     "c2_16x8c3": dict(dims=(16, 8, 8, 8), eps=0.5, csw=1.5, m0=-0.85, seed=1002, k=50,
                       use_mg=1, agg=(2, 2, 2, 2), nv=8, sap=(2, 2, 2, 2), target=1e-2),
+    # 32 x 16^3, two-level MG with 4^4 aggregates, Nv = 20, 100 pairs with 16
+    # targets per outer iteration and P rebuilt every 20 locks.  m0 is NOT
+    # oracle-tuned (the oracle's GD does not finish at 1.5M unknowns in the
+    # time a tuning grid allows): it is the 16 x 8^3 value, and runs report the
+    # min |lambda| it gives instead of the 5e-3 target.
+    "c3_32x16c3": dict(dims=(32, 16, 16, 16), eps=0.6, csw=1.7, m0=-0.85, seed=1003, k=100,
+                       use_mg=1, agg=(4, 4, 4, 4), nv=20, sap=(2, 2, 2, 2), target=5e-3, m0_tuned=False,
+                       block=16, m_min=30, m_max=48, update_every=20),
 }
 
 
