@@ -77,7 +77,11 @@ typedef struct qcd_params {
     int    plain_maxiter;    /* plain GMRES inner iterations without MG (default 20) */
     int    m_min;            /* Table 2: 30 */
     int    m_max;            /* Table 2: 50 */
-    int    block;            /* targets per outer iteration (>= 1; default 2) */
+    int    block;            /* targets per outer iteration (>= 1; default 2).  Keep
+                                m_max - m_min >= 2 * block: with one outer step
+                                between restarts a dense cluster can lose an
+                                eigenvalue (16 targets at m_min 30, m_max 48
+                                did on a 32x16^3 field) */
     int    n_init;           /* random start vectors when use_mg = 0 (default 8) */
     int    shift_rho;        /* 1: correction-equation shift = Rayleigh quotient rho of the
                                 target vector (default); 0: its harmonic Ritz value theta */
