@@ -36,7 +36,9 @@ Readings taken where the paper is silent:
 * Setup: iteration 1 smooths each random test vector on D x = 0; later
   iterations replace each vector by one application of the current
   two-level preconditioner to it (inverse iteration); P and D_c are rebuilt
-  after every iteration.
+  after every iteration.  Its result is not unique (only the solver's speed
+  depends on it) and the GPU setup is not compared with it; it is pinned by
+  a property only: the vectors it returns approach the near-kernel of D.
 """
 import numpy as np
 
