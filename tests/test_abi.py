@@ -69,6 +69,10 @@ def test_calls_without_gauge_fail_cleanly():
     with pytest.raises(qcd.QcdError) as e:
         ctx.qcd_mg_setup(0, (2, 2, 2, 2))
     assert e.value.code == qcd.QCD_EINVAL
+    for call in (lambda: ctx.qcd_eig_force(1, 0, 0), lambda: ctx.qcd_local_coherence(1, 0)):
+        with pytest.raises(qcd.QcdError) as e:
+            call()
+        assert e.value.code in (qcd.QCD_ENOTSETUP, qcd.QCD_EINVAL)
     ctx.close()
 
 
