@@ -14,8 +14,8 @@ dirac   Wilson-clover operator D, Gamma5, Q = Gamma5 D (Sec. 2, Eq. 2.4, 2.5, 2.
         eigenvalue derivative (pinned by central differences)
 mg      aggregation interpolation P, restriction P^H, Galerkin coarse operator
         D_c = P^H D P, SAP smoother, GMRES/FGMRES, the two-level cycle
-        E_2g (Sec. 2, Eq. 2.8-2.11, Prop. 1) and the local coherence measure
-        (Sec. 3)
+        E_2g (Sec. 2, Eq. 2.8-2.11, Prop. 1), the three-level K-cycle and the
+        local coherence measure (Sec. 3)
 gd      generalized Davidson with harmonic (or Rayleigh-Ritz) extraction,
         thick restart, locking and interpolation updates (Sec. 3,
         Algorithm 1, Algorithm 2, Theorem 1, Eq. 3.4-3.6)

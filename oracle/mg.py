@@ -16,7 +16,11 @@ coherence", Sec. 4 "Solving the correction equation" and Table 2):
 * GMRES, flexible GMRES and the two-level cycle E_2g with post-smoothing only
   (Eq. 2.8, Table 2);
 * the adaptive setup of the test vectors (Table 2; the procedure itself is
-  deferred by the paper to the DD-alpha-AMG literature -- reading below).
+  deferred by the paper to the DD-alpha-AMG literature -- reading below);
+* the three-level hierarchy: the aggregation and Galerkin construction
+  applied to the coarse operator, and the K-cycle whose middle level is
+  FGMRES preconditioned by the level-1 two-level cycle (``ThreeLevelMG``;
+  readings in its docstring).
 
 Readings taken where the paper is silent:
 
@@ -273,6 +277,70 @@ class Interpolation:
         return M
 
 
+class CoarseInterpolation:
+    """The same aggregation one level down (three-level hierarchy, Sec. 2
+    "Algebraic multigrid methods": the construction is applied recursively).
+    A level-1 vector x[site, chi, i] (N_v1 components per chirality) is cut
+    into level-2 aggregates of extent ``block`` on the level-1 lattice and
+    split by the level-1 chirality index, so Gamma5^c P2 = P2 Gamma5^cc; each
+    (aggregate, chirality) piece of the test vectors is orthonormalised by
+    modified Gram-Schmidt applied twice.
+
+    ``P[b, chi, j, l, i]``: level-2 site b, chirality chi, vector j, local
+    level-1 site l, component i < N_v1 of chirality chi.
+    """
+
+    def __init__(self, cdims, block, nv_in, vectors):
+        self.blk = Blocking(cdims, block)
+        self.nv_in = int(nv_in)
+        W = np.asarray(vectors, dtype=np.complex128)
+        self.nv = W.shape[0]
+        nb, bs = self.blk.nblocks, self.blk.bsites
+        Wf = W.reshape(self.nv, -1, 2, self.nv_in)[:, self.blk.sites]   # (nv, nb, bs, 2, nv_in)
+        P = np.zeros((nb, 2, self.nv, bs, self.nv_in), dtype=np.complex128)
+        for chi in range(2):
+            Wc = np.transpose(Wf[..., chi, :].reshape(self.nv, nb, bs * self.nv_in), (1, 0, 2)).copy()
+            for _ in range(2):
+                for i in range(self.nv):
+                    for j in range(i):
+                        h = np.einsum('bk,bk->b', np.conj(Wc[:, j]), Wc[:, i])
+                        Wc[:, i] -= h[:, None] * Wc[:, j]
+                    nrm = np.linalg.norm(Wc[:, i], axis=1)
+                    Wc[:, i] /= np.where(nrm > 0, nrm, 1.0)[:, None]
+            P[:, chi] = Wc.reshape(nb, self.nv, bs, self.nv_in)
+        self.P = P
+        self.cdims_in = tuple(cdims)
+        self.nc = 2 * self.nv
+
+    def restrict(self, r):
+        """P2^H r for a level-1 vector r (V1 x 2 N_v1); returns (nb, 2, nv)."""
+        rb = np.asarray(r).reshape(-1, 2, self.nv_in)[self.blk.sites]      # (nb, bs, 2, nv_in)
+        out = np.empty((self.blk.nblocks, 2, self.nv), dtype=np.complex128)
+        for chi in range(2):
+            out[:, chi] = np.einsum('bjli,bli->bj', np.conj(self.P[:, chi]), rb[:, :, chi, :])
+        return out
+
+    def prolong(self, xc):
+        """P2 x_c as a level-1 vector (V1, 2 N_v1)."""
+        xc = np.asarray(xc).reshape(self.blk.nblocks, 2, self.nv)
+        fb = np.zeros((self.blk.nblocks, self.blk.bsites, 2, self.nv_in), dtype=np.complex128)
+        for chi in range(2):
+            fb[:, :, chi, :] = np.einsum('bjli,bj->bli', self.P[:, chi], xc[:, chi])
+        out = np.zeros((int(np.prod(self.cdims_in)), 2, self.nv_in), dtype=np.complex128)
+        out[self.blk.sites.reshape(-1)] = fb.reshape(-1, 2, self.nv_in)
+        return out.reshape(-1, 2 * self.nv_in)
+
+    def dense(self):
+        ncol = self.blk.nblocks * self.nc
+        M = np.zeros((int(np.prod(self.cdims_in)) * 2 * self.nv_in, ncol), dtype=np.complex128)
+        e = np.zeros(ncol, dtype=np.complex128)
+        for j in range(ncol):
+            e[j] = 1.0
+            M[:, j] = self.prolong(e).reshape(-1)
+            e[j] = 0.0
+        return M
+
+
 def local_coherence(interp, v):
     """Local coherence measure lc(v) = ||Pi v|| / ||v|| (Sec. 3), with Pi the
     orthogonal projection on the range of P: Pi v = P (P^H v), P having
@@ -338,6 +406,46 @@ class CoarseOperator:
                 for d in range(9):
                     A[:, d, :, col] = interp.restrict(parts[d]).reshape(nb, nc)
         return cls(A, blk.cdims, nv)
+
+    @classmethod
+    def galerkin_coarse(cls, cop, interp2):
+        """The next level's Galerkin operator A2 = P2^H D_c P2 as a stencil on
+        the level-2 lattice, built like ``galerkin``: each column class of P2
+        goes through the nine terms of the level-1 stencil, and a term that
+        reads across the face of a level-2 aggregate (level-2 extent > 1) is
+        attributed to that level-2 direction, every other term to the self
+        term."""
+        blk = interp2.blk
+        nv2, nc2, nc1 = interp2.nv, interp2.nc, cop.nc
+        nb2 = blk.nblocks
+        V1 = int(np.prod(cop.cdims))
+        coords = np.indices(blk.dims).reshape(4, -1).T
+        face = {}
+        for mu in range(4):
+            loc = coords[:, mu] % blk.block[mu]
+            leaves = blk.cdims[mu] > 1
+            face[(mu, +1)] = (loc == blk.block[mu] - 1) & leaves
+            face[(mu, -1)] = (loc == 0) & leaves
+        A1 = cop.A.reshape(cop.cdims + (9, nc1, nc1))
+        A2 = np.zeros((nb2, 9, nc2, nc2), dtype=np.complex128)
+        for chi in range(2):
+            for j in range(nv2):
+                e = np.zeros((nb2, 2, nv2), dtype=np.complex128)
+                e[:, chi, j] = 1.0
+                v = interp2.prolong(e).reshape(cop.cdims + (nc1,))
+                parts = [np.zeros((V1, nc1), dtype=np.complex128) for _ in range(9)]
+                for d in range(9):
+                    h = np.einsum('...rc,...c->...r', A1[..., d, :, :], cop.neighbour(v, d)).reshape(V1, nc1)
+                    if d == 0:
+                        parts[0] += h
+                        continue
+                    f = face[((d - 1) % 4, +1 if d <= 4 else -1)][:, None]
+                    parts[d] += np.where(f, h, 0.0)
+                    parts[0] += np.where(f, 0.0, h)
+                col = chi * nv2 + j
+                for d in range(9):
+                    A2[:, d, :, col] = interp2.restrict(parts[d]).reshape(nb2, nc2)
+        return cls(A2, blk.cdims, nv2)
 
     def neighbour(self, x, d):
         """x(b + d) on the coarse lattice (periodic; phases live inside A)."""
@@ -530,3 +638,62 @@ class TwoLevelMG:
                 W[i] /= np.linalg.norm(W[i])
             self.set_vectors(W)
         return W
+
+
+# ----------------------------------------------------------------- three-level solver
+class ThreeLevelMG(TwoLevelMG):
+    """Three-level K-cycle (Sec. 2: the two-level construction applied
+    recursively; Table 2's coarse tolerance at the middle level).  The fine
+    level is ``TwoLevelMG``; its coarse solve becomes FGMRES on the level-1
+    operator to ``coarse_tol`` (at most ``coarse_maxiter`` steps), right-
+    preconditioned by the level-1 two-level cycle:
+    x2 = GMRES(level-2 operator, P2^H r) to ``coarse2_tol``, x = P2 x2, then
+    ``nu2`` GMRES smoothing steps of ``smooth2_iters`` iterations on the
+    level-1 system.
+
+    Readings taken where the paper is silent: the middle level smooths with
+    GMRES (the paper's alternative smoother, Sec. 2 last paragraph) instead
+    of SAP on the coarse lattice; without explicit level-2 test vectors, the
+    first ``nv2`` fine test vectors restricted by P^H serve (they span the
+    level-1 near-kernel that the fine test vectors carry down).
+    """
+
+    def __init__(self, op, agg_block, agg_block2, sap_block, nv, nv2, nu2=2, smooth2_iters=4,
+                 coarse2_tol=0.5, coarse2_maxiter=100, **kw):
+        super().__init__(op, agg_block, sap_block, nv, **kw)
+        self.agg_block2 = tuple(agg_block2)
+        self.nv2 = int(nv2)
+        self.nu2 = int(nu2)
+        self.smooth2_iters = int(smooth2_iters)
+        self.coarse2_tol = coarse2_tol
+        self.coarse2_maxiter = coarse2_maxiter
+        self.interp2 = None
+        self.coarse2 = None
+
+    def set_vectors(self, vectors, vectors2=None):
+        super().set_vectors(vectors)
+        if vectors2 is None:
+            W = np.asarray(vectors).reshape((-1,) + self.op.dims + (4, 3))
+            if W.shape[0] < self.nv2:
+                raise ValueError("need at least nv2 fine test vectors")
+            vectors2 = [self.interp.restrict(W[i]).reshape(-1) for i in range(self.nv2)]
+        self.interp2 = CoarseInterpolation(self.coarse.cdims, self.agg_block2, self.nv, vectors2)
+        self.coarse2 = CoarseOperator.galerkin_coarse(self.coarse, self.interp2)
+
+    def coarse_cycle(self, rc, tau):
+        """The level-1 two-level cycle applied to a level-1 vector."""
+        rc = np.asarray(rc).reshape(1, -1)
+        A2 = lambda v: self.coarse2.apply(v, tau, self.form).reshape(1, -1)
+        x2, _ = gmres(A2, self.interp2.restrict(rc).reshape(1, -1), self.coarse2_tol, self.coarse2_maxiter)
+        x = self.interp2.prolong(x2).reshape(1, -1)
+        A1 = lambda v: self.coarse.apply(v, tau, self.form).reshape(1, -1)
+        for _ in range(self.nu2):
+            e, _ = gmres(A1, rc - A1(x), 0.0, self.smooth2_iters)
+            x = x + e
+        return x.reshape(-1)
+
+    def coarse_solve(self, rc, tau):
+        A1 = lambda v: self.coarse.apply(v, tau, self.form).reshape(-1)
+        M1 = lambda v: self.coarse_cycle(v, tau)
+        xc, it, _ = fgmres(A1, M1, np.asarray(rc).reshape(-1), self.coarse_tol, self.coarse_maxiter)
+        return xc.reshape(-1, self.interp.nc), int(it)

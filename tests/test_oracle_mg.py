@@ -287,3 +287,81 @@ def test_setup_enriches_the_near_kernel():
     assert np.allclose([np.linalg.norm(w) for w in W], 1.0, atol=1e-12)
     assert np.all(after >= sigma_min * (1 - 1e-12))
     assert np.all(after < 2.0 * sigma_min) and np.mean(after) < 0.25 * np.mean(before)
+
+
+# ----------------------------------------------------------------- three levels
+@pytest.fixture(scope="module")
+def level1():
+    dims = (8, 4, 4, 4)
+    op = WilsonClover(synth.gauge_field(dims, 0.4, 31), -0.3, 1.2)
+    vec = synth.spinor(dims, 32, nvec=4)
+    I1 = mg.Interpolation(dims, (2, 2, 2, 2), vec)
+    return op, vec, mg.CoarseOperator.galerkin(op, I1)
+
+
+@pytest.mark.parametrize("block2", [(2, 1, 1, 1), (2, 2, 2, 2), (1, 2, 1, 2)])
+def test_level2_interpolation_and_galerkin(level1, block2):
+    """One level down (level-1 lattice 4 x 2^3, 2 N_v1 = 8): P2^H P2 = I,
+    Gamma5^c P2 = P2 Gamma5^cc, P2 P2^H w = w for the level-2 test vectors,
+    and the level-2 stencil equals dense P2^H D_c P2 (aggregate extents 1
+    and 2, level-2 extents 1, 2 and 4)."""
+    _, _, C1 = level1
+    V1 = int(np.prod(C1.cdims))
+    w2 = synth.complex_gaussian((3, V1 * C1.nc), 33)
+    I2 = mg.CoarseInterpolation(C1.cdims, block2, C1.nv, w2)
+    C2 = mg.CoarseOperator.galerkin_coarse(C1, I2)
+    P2, D1, D2 = I2.dense(), C1.dense(), C2.dense()
+    assert np.max(np.abs(P2.conj().T @ P2 - np.eye(P2.shape[1]))) < 1e-13
+    g1 = np.tile(mg.gamma5_coarse(C1.nv), V1)
+    g2 = np.tile(mg.gamma5_coarse(I2.nv), int(np.prod(C2.cdims)))
+    assert np.max(np.abs(g1[:, None] * P2 - P2 * g2[None, :])) == 0.0
+    for w in w2:
+        assert np.linalg.norm(P2 @ (P2.conj().T @ w) - w) < 1e-12 * np.linalg.norm(w)
+    assert np.max(np.abs(P2.conj().T @ D1 @ P2 - D2)) < 1e-13 * np.max(np.abs(D2))
+
+
+def test_level1_cycle_is_coarse_grid_correction(level1):
+    """Without middle-level smoothing and with an exact level-2 solve, the
+    level-1 cycle is the coarse-grid correction P2 (P2^H A1 P2)^-1 P2^H r
+    (Eq. 2.8 one level down), A1 = D_c - tau Gamma5^c."""
+    op, vec, _ = level1
+    h = mg.ThreeLevelMG(op, (2, 2, 2, 2), (2, 1, 1, 1), (2, 2, 2, 2), 4, 3, nu2=0,
+                        coarse2_tol=1e-14, coarse2_maxiter=400)
+    h.set_vectors(vec)
+    tau = 0.07
+    V1 = int(np.prod(h.coarse.cdims))
+    A1 = h.coarse.dense() - tau * np.diag(np.tile(mg.gamma5_coarse(h.nv), V1))
+    P2 = h.interp2.dense()
+    r = synth.complex_gaussian((V1 * h.coarse.nc,), 35)
+    ref = P2 @ np.linalg.solve(P2.conj().T @ A1 @ P2, P2.conj().T @ r)
+    got = h.coarse_cycle(r, tau)
+    assert np.linalg.norm(got - ref) < 1e-11 * np.linalg.norm(ref)
+
+
+def test_k_cycle_with_exact_coarse_solve_is_two_level(level1):
+    """Solving the level-1 system to 1e-13 inside the K-cycle gives the
+    two-level cycle with an exact coarse solve, whatever the middle level
+    does."""
+    op, vec, _ = level1
+    b = synth.spinor(op.dims, 34)
+    two = mg.TwoLevelMG(op, (2, 2, 2, 2), (2, 2, 2, 2), 4, coarse_tol=1e-13, coarse_maxiter=400)
+    two.set_vectors(vec)
+    three = mg.ThreeLevelMG(op, (2, 2, 2, 2), (2, 1, 1, 1), (2, 2, 2, 2), 4, 3, coarse_tol=1e-13,
+                            coarse_maxiter=400)
+    three.set_vectors(vec)
+    for tau in (0.0, 0.1):
+        x2, x3 = two.cycle(b, tau), three.cycle(b, tau)
+        assert np.linalg.norm(x3 - x2) < 1e-11 * np.linalg.norm(x2)
+
+
+def test_three_level_solve_matches_dense():
+    """FGMRES with the three-level K-cycle (Table 2 tolerances inside) solves
+    (D - tau Gamma5) x = b on the 4^4 field to the dense solution."""
+    dims = (4, 4, 4, 4)
+    op = WilsonClover(synth.gauge_field(dims, 0.3, 1001), -0.2, 1.0)
+    h = mg.ThreeLevelMG(op, (2, 2, 2, 2), (2, 2, 2, 2), (2, 2, 2, 2), 8, 6)
+    h.set_vectors(synth.spinor(dims, 5, nvec=8))
+    b = synth.spinor(dims, 6)
+    x, it = h.solve(b, 0.05, tol=1e-12, maxiter=200)
+    xd = np.linalg.solve(op.dense('Dg5', 0.05), b.reshape(-1))
+    assert np.linalg.norm(x.reshape(-1) - xd) < 1e-10 * np.linalg.norm(xd)
