@@ -101,3 +101,25 @@ def test_rayleigh_ritz_galerkin_condition():
     theta2, S2 = gd.rayleigh_ritz(Y[:, 10:18], A @ Y[:, 10:18])
     assert np.max(np.abs(np.sort(theta2) - np.sort(w[10:18]))) < 1e-12 * np.max(np.abs(w))
 
+
+
+@pytest.mark.slow
+def test_gd_three_level_corrections_c1():
+    """GD-lambda-AMG whose correction equations (Eq. 3.7) are solved by FGMRES
+    with the three-level K-cycle (4^4 -> 2^4 -> 1^4, Nv 8 then 6; Table 2
+    tolerances): the 10 smallest |lambda| of the dense Q to 1e-10."""
+    dims = (4, 4, 4, 4)
+    op = WilsonClover(synth.gauge_field(dims, 0.3, 1001), -0.2, 1.0)
+    ev = np.linalg.eigvalsh(op.dense('Q'))
+    ev = ev[np.lexsort((ev, np.abs(ev)))]
+    Q = lambda v: op.Q(v.reshape(dims + (4, 3))).reshape(-1)
+    h = mg.ThreeLevelMG(op, (2, 2, 2, 2), (2, 2, 2, 2), (2, 2, 2, 2), 8, 6)
+    W = h.setup(synth.spinor(dims, 11, nvec=8), iterations=3)
+
+    def corr(theta, r):
+        x, it = h.solve(op.g5(r.reshape(dims + (4, 3))), theta, 1e-1, 5)
+        return x.reshape(-1), it
+    res = gd.gd_lambda_amg(Q, 10, W.reshape(8, -1).T, synth.complex_gaussian((op.n, 2), 12), corr,
+                           m_min=30, m_max=50, eps=1e-8, block=2)
+    assert res.converged
+    assert np.max(np.abs(res.lam - ev[:10]) / np.abs(ev[:10])) < 1e-10
