@@ -210,7 +210,9 @@ int qcd_coarse_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* x, vo
  * X: HOST complex128 [site][mu][3][3] traceless Hermitian; V: DEVICE
  * complex128 [nvec][V*12] eigenvectors (16-byte aligned); out: HOST nvec
  * doubles.  FP64 throughout; dD/d eps is the stencil with dU = i X U and the
- * product-rule derivative of every clover leaf. */
+ * product-rule derivative of every clover leaf.  Errors: ENOTSETUP before
+ * qcd_set_gauge; EINVAL for nvec < 0, NULL or misaligned pointers; nvec = 0
+ * does nothing; a zero vector gives 0. */
 int qcd_eig_derivative(qcd_ctx* ctx, const double* X, int nvec, const void* V, double* out);
 
 /* The same derivative resolved per link (the force of each eigenvalue):
@@ -221,7 +223,9 @@ int qcd_eig_derivative(qcd_ctx* ctx, const double* X, int nvec, const void* V, d
  * the clover term the plaquettes above and below each link with the clover
  * insertion at each corner.  V: DEVICE complex128 [nvec][V*12]; F: DEVICE
  * complex128 [nvec][site][mu][3][3] (gauge-field layout), caller-owned and
- * overwritten; both 16-byte aligned.  FP64 throughout. */
+ * overwritten; both 16-byte aligned.  FP64 throughout.  Errors: ENOTSETUP
+ * before qcd_set_gauge; EINVAL for nvec < 0, NULL or misaligned pointers;
+ * nvec = 0 does nothing.  A zero vector gives a zero force. */
 int qcd_eig_force(qcd_ctx* ctx, int nvec, const void* V, void* F);
 
 /* Local coherence lc(v) = ||Pi v|| / ||v|| (Sec. 3, the local coherence
