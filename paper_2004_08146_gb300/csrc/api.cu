@@ -1280,6 +1280,7 @@ int qcd_set_gauge(qcd_ctx* ctx, const double* U, const int dims[4], double m0, d
             V *= dims[mu];
         }
         if (V > (1ll << 28)) throw QcdError(QCD_EINVAL, "lattice too large");
+        if (!std::isfinite(m0) || !std::isfinite(csw)) throw QcdError(QCD_EINVAL, "m0 and csw must be finite");
         CK(cudaStreamSynchronize(ctx->st));
         ctx->release();
         ctx->have_gauge = false;

@@ -93,3 +93,18 @@ def test_default_params_method_variants():
     p = qcd.default_params()
     assert p.extraction == qcd.QCD_EXTRACT_HARMONIC and p.update_every == 1
     assert p.shift_rho == 1 and p.block == 2
+
+
+@pytest.mark.parametrize("dims,m0,csw", [((1, 4, 4, 4), -0.2, 1.0), ((4, 4, 4, 5000), -0.2, 1.0),
+                                         ((4, 4, 4, 4), float("nan"), 1.0), ((4, 4, 4, 4), -0.2, float("inf"))])
+def test_set_gauge_rejects_bad_lattice_and_couplings(dims, m0, csw):
+    """Extents outside [2, 4096] and non-finite m0 or c_sw come back as EINVAL
+    before any device work (the gauge array is only a placeholder)."""
+    import numpy as np
+    from paper_2004_08146_gb300 import qcd
+    ctx = qcd.Context()
+    U = np.zeros((2, 4, 3, 3), dtype=np.complex128)
+    with pytest.raises(qcd.QcdError) as e:
+        ctx.qcd_set_gauge(U, dims, m0, csw)
+    assert e.value.code == qcd.QCD_EINVAL
+    ctx.close()
