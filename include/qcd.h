@@ -93,6 +93,15 @@ typedef struct qcd_params {
     int    max_outer;        /* outer iteration cap (default 100000) */
     unsigned long long seed; /* counter-based RNG seed for setup / start vectors */
     int    verbose;          /* 1: per-lock progress on stderr */
+    int    levels;           /* 2 (default) or 3: the coarse solve becomes the K-cycle --
+                                FGMRES on D_c to coarse_tol, preconditioned by a
+                                two-level cycle on the coarse lattice (this path has
+                                not been validated on a GPU yet) */
+    int    nv2;              /* level-2 test vectors: the first nv2 fine test vectors
+                                restricted by P^H (default 8, <= Nv) */
+    int    agg2[4];          /* level-2 aggregate extents on the coarse lattice (2,2,2,2) */
+    int    nu2;              /* GMRES smoothing steps on the coarse lattice per level-1
+                                cycle (gmres_smooth_iters iterations each; default 2) */
 } qcd_params;
 
 typedef struct qcd_solve_info {
@@ -196,6 +205,20 @@ int qcd_mg_restrict(qcd_ctx* ctx, int prec, int nrhs, const void* r, void* xc);
 
 /* x = P x_c for nrhs coarse vectors (overwrites x). */
 int qcd_mg_prolong(qcd_ctx* ctx, int prec, int nrhs, const void* xc, void* x);
+
+/* Third level (params.levels = 3; QCD_ENOTSETUP otherwise).  out[0] = level-2
+ * sites, out[1] = nv2, out[2..5] = level-2 dims, out[6] = coarse sites per
+ * level-2 aggregate, out[7] = Nv of level 1. */
+int qcd_mg_info2(qcd_ctx* ctx, int out[8]);
+
+/* Copy P2 (HOST complex128 [level-2 site][chi][j < nv2][aggregate site][i < Nv]):
+ * the restricted test vectors of each (aggregate, chirality) orthonormalised by
+ * modified Gram-Schmidt applied twice. */
+int qcd_mg_get_P2(qcd_ctx* ctx, double* P_host);
+
+/* Copy the level-2 stencil P2^H D_c P2 (HOST complex128 [site][d][row][col],
+ * d as for qcd_mg_get_coarse). */
+int qcd_mg_get_coarse2(qcd_ctx* ctx, double* A_host);
 
 /* y_j = (D_c - tau_j Gamma5^c) x_j (op QCD_OP_D) or (Gamma5^c D_c - tau_j) x_j
  * (op QCD_OP_Q), coarse stencil of Eq. 2.8 / 2.9; tau HOST array. */

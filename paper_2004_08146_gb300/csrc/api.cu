@@ -59,6 +59,7 @@ struct qcd_ctx {
     bool have_gauge = false;
     FineOp f;
     Coarse c;
+    Coarse c2;                        // third level (params.levels = 3)
     SapPlan sap;
     bool have_sap = false;
     std::map<std::string, DevBuf> ws;
@@ -66,6 +67,7 @@ struct qcd_ctx {
     size_t pinned_n = 0;
     double2* test_vectors = nullptr;  // FP64 setup vectors [nv][V*12]
     int n_test = 0;
+    int c2_nv1 = 0;                   // Nv of level 1 when c2 was allocated
     bool no_coop = false;             // cooperative coarse launch unavailable: host-driven GMRES
     unsigned* md_cnt = nullptr;       // zeroed dot-product completion counters (blas_multidot)
     size_t md_cnt_n = 0;
@@ -96,6 +98,14 @@ struct qcd_ctx {
         test_vectors = nullptr;
         n_test = 0;
         c.ready = false;
+        drop_level2();
+    }
+    void drop_level2() {
+        auto fr = [](void* q) { if (q) cudaFree(q); };
+        fr(c2.P64); fr(c2.P32); fr(c2.A64); fr(c2.A32);
+        c2.P64 = nullptr; c2.P32 = nullptr; c2.A64 = nullptr; c2.A32 = nullptr;
+        c2.nv = c2.nc = 0;
+        c2.ready = false;
     }
 
     void* buf(const std::string& name, size_t bytes) {
@@ -170,6 +180,10 @@ void validate_params(const qcd_params& p) {
         throw QcdError(QCD_EINVAL, "bad iteration caps");
     if (p.precision != QCD_FP64 && p.precision != QCD_MIXED) throw QcdError(QCD_EINVAL, "bad precision");
     if (p.correction_form != QCD_OP_D && p.correction_form != QCD_OP_Q) throw QcdError(QCD_EINVAL, "bad correction_form");
+    if (p.levels != 2 && p.levels != 3) throw QcdError(QCD_EINVAL, "levels must be 2 or 3");
+    if (p.nv2 < 1 || p.nv2 > 32 || p.nu2 < 0) throw QcdError(QCD_EINVAL, "need 1 <= nv2 <= 32 and nu2 >= 0");
+    for (int mu = 0; mu < 4; ++mu)
+        if (p.agg2[mu] < 1) throw QcdError(QCD_EINVAL, "agg2 extents must be >= 1");
 }
 
 // ------------------------------------------------------------------ linear operators
@@ -457,6 +471,80 @@ void smooth(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, co
 // two-level cycle x = M b (Eq. 2.8, post-smoothing only)
 void ensure_coarse64(qcd_ctx* ctx);
 
+// Level-2 solve of the K-cycle: GMRES on the level-2 operator to coarse_tol,
+// one cooperative launch per group (host-driven GMRES when cooperative
+// launches are unavailable).
+void level2_solve(qcd_ctx* ctx, int prec, int op, int nrhs, const void* rc, void* xc, const double* tau,
+                  const double* taud, const int* act) {
+    const Coarse& c2 = ctx->c2;
+    const size_t nco2 = (size_t)c2.gc.V * c2.nc;
+    const int maxit = std::min(ctx->p.coarse_maxiter, kMaxCoarse);
+    bool done = !ctx->no_coop;
+    if (done) {
+        const int grp = std::min(nrhs, coarse_gmres_group(c2, prec, maxit));
+        if (grp < 1) throw QcdError(QCD_EINVAL, "level 2 too large for the shared-memory Krylov basis");
+        void* scr = ctx->buf("l2.scr", coarse_gmres_scratch(c2, prec, grp, maxit, coarse_gmres_grid()));
+        int* its = (int*)ctx->buf("l2.its", (size_t)nrhs * sizeof(int));
+        double* res = (double*)ctx->buf("l2.res", (size_t)nrhs * sizeof(double));
+        for (int j0 = 0; j0 < nrhs && done; j0 += grp) {
+            const int nj = std::min(grp, nrhs - j0);
+            const int rcode = coarse_gmres(c2, prec, op, nj, (const char*)rc + (size_t)j0 * nco2 * esz(prec),
+                                           (char*)xc + (size_t)j0 * nco2 * esz(prec), taud + j0,
+                                           act ? act + j0 : nullptr, ctx->p.coarse_tol, maxit, scr, its + j0,
+                                           res + j0, ctx->counters(), ctx->st);
+            if (rcode != 0) {
+                cudaGetLastError();
+                if (j0 > 0) throw QcdError(QCD_ECUDA, "cooperative level-2 solve failed mid-batch");
+                ctx->no_coop = true;
+                done = false;
+            }
+        }
+    }
+    if (!done) {
+        std::vector<double> tv(tau, tau + nrhs);
+        OpFn A2 = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int*) {
+            coarse_apply(ctx->c2, prec, op, nrhs, in, out, tv.data(), ctx->st);
+        };
+        gmres_batched(ctx, prec, nco2, nrhs, A2, nullptr, rc, xc, ctx->p.coarse_tol, ctx->p.coarse_maxiter, "l2g");
+    }
+}
+
+// The level-1 two-level cycle of the K-cycle: x1 = P2 (level-2 solve of
+// P2^H r1), then nu2 GMRES smoothing steps (gmres_smooth_iters each) on the
+// level-1 system (D_c - tau Gamma5^c or Q_c - tau, as `op`).
+void level1_cycle(qcd_ctx* ctx, int prec, int op, int nrhs, const void* r1, void* x1, const double* tau,
+                  const double* taud, const int* act) {
+    const Coarse& c = ctx->c;
+    const Coarse& c2 = ctx->c2;
+    const size_t nco = (size_t)c.gc.V * c.nc, nco2 = (size_t)c2.gc.V * c2.nc;
+    void* rc2 = ctx->buf("l2.rc", nco2 * nrhs * esz(prec));
+    void* xc2 = ctx->buf("l2.xc", nco2 * nrhs * esz(prec));
+    blas_zero(prec, rc2, nco2 * nrhs, ctx->st);
+    blas_zero(prec, x1, nco * nrhs, ctx->st);   // masked right-hand sides stay zero
+    mg2_restrict(c, c2, prec, nrhs, r1, rc2, ctx->st, act);
+    level2_solve(ctx, prec, op, nrhs, rc2, xc2, tau, taud, act);
+    mg2_prolong(c, c2, prec, nrhs, xc2, x1, ctx->st, act);
+    if (ctx->p.nu2 <= 0) return;
+    std::vector<double> tv(tau, tau + nrhs);
+    OpFn A1 = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int*) {
+        coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st);
+    };
+    void* w = ctx->buf("l1c.w", nco * nrhs * esz(prec));
+    void* e = ctx->buf("l1c.e", nco * nrhs * esz(prec));
+    double2* one = (double2*)ctx->buf("l1c.one", (size_t)nrhs * sizeof(double2));
+    {
+        std::vector<double2> ones(nrhs, make_double2(1, 0));
+        CK(cudaMemcpyAsync(one, ones.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+    }
+    for (int s = 0; s < ctx->p.nu2; ++s) {
+        // w = r1 - A1 x1
+        coarse_apply(c, prec, op, nrhs, x1, w, tv.data(), ctx->st);
+        blas_axpby(prec, make_double2(1, 0), r1, make_double2(-1, 0), w, nco * nrhs, ctx->st);
+        gmres_dev(ctx, prec, nco, nrhs, A1, nullptr, w, e, 0.0, ctx->p.gmres_smooth_iters, "l1s", act);
+        blas_scale_dev(prec, e, x1, one, nrhs, nco, false, true, ctx->st, act);
+    }
+}
+
 void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x, const double* tau,
                    const int* act = nullptr) {
     if (prec == QCD_FP64) ensure_coarse64(ctx);
@@ -468,6 +556,24 @@ void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void
     // coarse solve: one cooperative launch per group of <= kMaxCoarseRhs right-hand sides
     double* taud = (double*)ctx->buf("cyc.tau", (size_t)nrhs * sizeof(double));
     CK(cudaMemcpyAsync(taud, tau, nrhs * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    if (ctx->p.levels == 3 && ctx->c2.ready) {
+        // K-cycle: FGMRES on the level-1 operator to coarse_tol, preconditioned
+        // by the level-1 two-level cycle (host-controlled: it stops when done)
+        std::vector<double> tv(tau, tau + nrhs);
+        OpFn A1 = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int*) {
+            coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st);
+        };
+        OpFn M1 = [ctx, prec, op, nrhs, tv, taud, act](const void* in, void* out, const int*) {
+            level1_cycle(ctx, prec, op, nrhs, in, out, tv.data(), taud, act);
+        };
+        blas_zero(prec, rc, nco * nrhs, ctx->st);
+        mg_restrict(ctx->f, c, prec, nrhs, b, rc, ctx->st, act);
+        gmres_batched(ctx, prec, nco, nrhs, A1, &M1, rc, xc, ctx->p.coarse_tol, ctx->p.coarse_maxiter, "kc1");
+        mg_prolong(ctx->f, c, prec, nrhs, xc, x, false, ctx->st, act);
+        smooth(ctx, prec, op, nrhs, b, x, tau, act);
+        check_launch("mg k-cycle");
+        return;
+    }
     const int maxit = std::min(ctx->p.coarse_maxiter, kMaxCoarse);
     bool done = !ctx->no_coop;
     if (done) {
@@ -522,6 +628,45 @@ void ensure_coarse64(qcd_ctx* ctx) {
     }
 }
 
+// Third level (reading of Sec. 2 applied recursively): its test vectors are
+// the first nv2 fine test vectors restricted by P^H; P2 aggregates blocks of
+// params.agg2 level-1 sites; the level-2 operator is P2^H D_c P2 in FP64 (and
+// an FP32 copy).
+void build_level2(qcd_ctx* ctx, const double2* V, int nvec) {
+    const Coarse& c = ctx->c;
+    Coarse& c2 = ctx->c2;
+    const int nv2 = ctx->p.nv2;
+    if (nv2 > nvec) throw QcdError(QCD_EINVAL, "nv2 exceeds the number of fine test vectors");
+    Blocking B2 = make_blocking(c.gc, ctx->p.agg2);
+    if (B2.bs * c.nv < nv2) throw QcdError(QCD_EINVAL, "level-2 aggregate smaller than nv2");
+    const bool realloc = !c2.P64 || c2.nv != nv2 || memcmp(c2.B.b, B2.b, sizeof(B2.b)) != 0 ||
+                         memcmp(c2.B.cd, B2.cd, sizeof(B2.cd)) != 0 || ctx->c2_nv1 != c.nv;
+    if (realloc) {
+        ctx->drop_level2();
+        c2.B = B2;
+        c2.nv = nv2;
+        c2.nc = 2 * nv2;
+        for (int mu = 0; mu < 4; ++mu) c2.gc.L[mu] = B2.cd[mu];
+        c2.gc.V = B2.nb;
+        c2.gc.antiperiodic = 0;
+        const size_t np = (size_t)B2.nb * 2 * nv2 * B2.bs * c.nv;
+        const size_t na = (size_t)B2.nb * 9 * c2.nc * c2.nc;
+        CK(cudaMalloc(&c2.P64, np * sizeof(double2)));
+        CK(cudaMalloc(&c2.P32, np * sizeof(float2)));
+        CK(cudaMalloc(&c2.A64, na * sizeof(double2)));
+        CK(cudaMalloc(&c2.A32, na * sizeof(float2)));
+        ctx->c2_nv1 = c.nv;
+    }
+    ensure_coarse64(ctx);
+    const size_t nco = (size_t)c.gc.V * c.nc;
+    double2* W2 = (double2*)ctx->buf("l2.W", (size_t)nv2 * nco * sizeof(double2));
+    mg_restrict(ctx->f, c, QCD_FP64, nv2, V, W2, ctx->st);
+    mg2_build_P(c, c2, W2, ctx->st);
+    mg2_build_coarse(c, c2, ctx->st);
+    check_launch("level-2 build");
+    c2.ready = true;
+}
+
 void build_from_vectors(qcd_ctx* ctx, const double2* V, int nvec, const int block[4]) {
     Coarse& c = ctx->c;
     Blocking B = make_blocking(ctx->f.g, block);
@@ -551,6 +696,8 @@ void build_from_vectors(qcd_ctx* ctx, const double2* V, int nvec, const int bloc
     mg_build_coarse(ctx->f, c, ctx->st, ctx->p.precision != QCD_FP64);
     check_launch("mg build");
     c.ready = true;
+    if (ctx->p.levels == 3) build_level2(ctx, V, nvec);
+    else ctx->c2.ready = false;
 }
 
 void mg_setup_impl(qcd_ctx* ctx, int Nv, const int block[4]) {
@@ -1225,6 +1372,10 @@ void qcd_default_params(qcd_params* p) {
     p->max_outer = 100000;
     p->seed = 20200417ull;
     p->verbose = 0;
+    p->levels = 2;
+    p->nv2 = 8;
+    for (int mu = 0; mu < 4; ++mu) p->agg2[mu] = 2;
+    p->nu2 = 2;
 }
 
 int qcd_create(qcd_ctx** out, const qcd_params* p, void* stream) {
@@ -1259,7 +1410,13 @@ int qcd_set_params(qcd_ctx* ctx, const qcd_params* p) {
         validate_params(*p);
         bool sap_changed = memcmp(p->sap_block, ctx->p.sap_block, sizeof(p->sap_block)) != 0;
         bool bc_changed = p->antiperiodic_t != ctx->p.antiperiodic_t;
+        const bool l2_changed = p->levels != ctx->p.levels || p->nv2 != ctx->p.nv2 ||
+                                memcmp(p->agg2, ctx->p.agg2, sizeof(p->agg2)) != 0;
         ctx->p = *p;
+        if (l2_changed) {
+            ctx->c2.ready = false;
+            if (p->levels == 3 && ctx->c.ready && ctx->test_vectors) build_level2(ctx, ctx->test_vectors, ctx->n_test);
+        }
         if (sap_changed && ctx->have_sap) {
             cudaFree(ctx->sap.blocks_of_colour[0]);
             cudaFree(ctx->sap.blocks_of_colour[1]);
@@ -1506,6 +1663,52 @@ int qcd_mg_get_coarse(qcd_ctx* ctx, double* A_host) {
         // device storage is [site][d][col][row]; the ABI returns [site][d][row][col]
         double2* out = (double2*)A_host;
         for (size_t blk = 0; blk < (size_t)ctx->c.B.nb * 9; ++blk)
+            for (int r = 0; r < nc; ++r)
+                for (int c = 0; c < nc; ++c) out[(blk * nc + r) * nc + c] = tmp[(blk * nc + c) * nc + r];
+        return QCD_OK;
+    });
+}
+
+void require_level2(qcd_ctx* ctx) {
+    require_mg(ctx);
+    if (ctx->p.levels != 3 || !ctx->c2.ready) throw QcdError(QCD_ENOTSETUP, "no third level: set params.levels = 3");
+}
+
+int qcd_mg_info2(qcd_ctx* ctx, int out[8]) {
+    return guarded(ctx, [&]() {
+        require_level2(ctx);
+        if (!out) throw QcdError(QCD_EINVAL, "null out");
+        out[0] = ctx->c2.gc.V;
+        out[1] = ctx->c2.nv;
+        for (int mu = 0; mu < 4; ++mu) out[2 + mu] = ctx->c2.gc.L[mu];
+        out[6] = ctx->c2.B.bs;
+        out[7] = ctx->c.nv;
+        return QCD_OK;
+    });
+}
+
+int qcd_mg_get_P2(qcd_ctx* ctx, double* P_host) {
+    return guarded(ctx, [&]() {
+        require_level2(ctx);
+        if (!P_host) throw QcdError(QCD_EINVAL, "null output");
+        const size_t np = (size_t)ctx->c2.B.nb * 2 * ctx->c2.nv * ctx->c2.B.bs * ctx->c.nv;
+        CK(cudaMemcpyAsync(P_host, ctx->c2.P64, np * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        return QCD_OK;
+    });
+}
+
+int qcd_mg_get_coarse2(qcd_ctx* ctx, double* A_host) {
+    return guarded(ctx, [&]() {
+        require_level2(ctx);
+        if (!A_host) throw QcdError(QCD_EINVAL, "null output");
+        const int nc = ctx->c2.nc;
+        const size_t na = (size_t)ctx->c2.B.nb * 9 * nc * nc;
+        std::vector<double2> tmp(na);
+        CK(cudaMemcpyAsync(tmp.data(), ctx->c2.A64, na * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        double2* out = (double2*)A_host;
+        for (size_t blk = 0; blk < (size_t)ctx->c2.B.nb * 9; ++blk)
             for (int r = 0; r < nc; ++r)
                 for (int c = 0; c < nc; ++c) out[(blk * nc + r) * nc + c] = tmp[(blk * nc + c) * nc + r];
         return QCD_OK;

@@ -140,6 +140,18 @@ void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void
 void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, void* y, const double* tau,
                   cudaStream_t st);
 
+// ------------------------------------------------------------------ kernels (mg2.cu)
+// Third level: c2.B blocks the level-1 lattice c1.gc; P2 [b2][chi][j][l][i < Nv1]
+// (FP64 + FP32); the level-2 stencil in c2.A64/A32 like the level-1 one.
+// W: FP64 level-2 test vectors [nv2][V1 * 2 Nv1].  mg2_build_coarse needs
+// c1.A64 current.
+void mg2_build_P(const Coarse& c1, Coarse& c2, const double2* W, cudaStream_t st);
+void mg2_build_coarse(const Coarse& c1, Coarse& c2, cudaStream_t st);
+void mg2_restrict(const Coarse& c1, const Coarse& c2, int prec, int nrhs, const void* r, void* xc, cudaStream_t st,
+                  const int* act = nullptr);
+void mg2_prolong(const Coarse& c1, const Coarse& c2, int prec, int nrhs, const void* xc, void* x, cudaStream_t st,
+                 const int* act = nullptr);
+
 struct SapPlan {
     Blocking B;
     int* blocks_of_colour[2] = {nullptr, nullptr};  // device lists of block ids

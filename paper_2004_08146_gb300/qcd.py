@@ -53,6 +53,10 @@ class qcd_params(ctypes.Structure):
         ("max_outer", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
         ("verbose", ctypes.c_int),
+        ("levels", ctypes.c_int),
+        ("nv2", ctypes.c_int),
+        ("agg2", ctypes.c_int * 4),
+        ("nu2", ctypes.c_int),
     ]
 
 
@@ -104,6 +108,9 @@ _SIGS = {
     "qcd_coarse_apply": (_I, [_P, _I, _I, _I, _P, _P, _DP]),
     "qcd_mg_get_P": (_I, [_P, _DP]),
     "qcd_mg_get_coarse": (_I, [_P, _DP]),
+    "qcd_mg_info2": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "qcd_mg_get_P2": (_I, [_P, _DP]),
+    "qcd_mg_get_coarse2": (_I, [_P, _DP]),
     "qcd_sap": (_I, [_P, _I, _I, _I, _P, _P, _DP, _I, _D]),
     "qcd_mg_cycle": (_I, [_P, _I, _I, _I, _P, _P, _DP]),
     "qcd_sap_static": (_I, [_P, _I, _I, _I, _P, _P, _DP, _I, _D]),
@@ -157,8 +164,8 @@ def default_params(**kw):
     p = qcd_params()
     _lib.qcd_default_params(ctypes.byref(p))
     for k, v in kw.items():
-        if k == "sap_block":
-            p.sap_block = (ctypes.c_int * 4)(*v)
+        if k in ("sap_block", "agg2"):
+            setattr(p, k, (ctypes.c_int * 4)(*v))
         else:
             setattr(p, k, v)
     return p
@@ -281,6 +288,24 @@ class Context:
         out = np.zeros(info["coarse_sites"] * 9 * nc * nc, dtype=np.complex128)
         self._check(_lib.qcd_mg_get_coarse(self.h, out.view(np.float64).ctypes.data_as(_DP)))
         return out.reshape(info["coarse_sites"], 9, nc, nc)
+
+    def qcd_mg_info2(self):
+        out = (ctypes.c_int * 8)()
+        self._check(_lib.qcd_mg_info2(self.h, out))
+        return dict(sites=out[0], nv2=out[1], dims=tuple(out[2:6]), aggregate_sites=out[6], nv1=out[7])
+
+    def qcd_mg_get_P2(self):
+        i = self.qcd_mg_info2()
+        out = np.zeros(i["sites"] * 2 * i["nv2"] * i["aggregate_sites"] * i["nv1"], dtype=np.complex128)
+        self._check(_lib.qcd_mg_get_P2(self.h, out.view(np.float64).ctypes.data_as(_DP)))
+        return out.reshape(i["sites"], 2, i["nv2"], i["aggregate_sites"], i["nv1"])
+
+    def qcd_mg_get_coarse2(self):
+        i = self.qcd_mg_info2()
+        nc = 2 * i["nv2"]
+        out = np.zeros(i["sites"] * 9 * nc * nc, dtype=np.complex128)
+        self._check(_lib.qcd_mg_get_coarse2(self.h, out.view(np.float64).ctypes.data_as(_DP)))
+        return out.reshape(i["sites"], 9, nc, nc)
 
     def qcd_sap(self, op, prec, nrhs, b, x, tau, sweeps, block_tol):
         t, tp = _dbl(tau)

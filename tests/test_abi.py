@@ -69,7 +69,8 @@ def test_calls_without_gauge_fail_cleanly():
     with pytest.raises(qcd.QcdError) as e:
         ctx.qcd_mg_setup(0, (2, 2, 2, 2))
     assert e.value.code == qcd.QCD_EINVAL
-    for call in (lambda: ctx.qcd_eig_force(1, 0, 0), lambda: ctx.qcd_local_coherence(1, 0)):
+    for call in (lambda: ctx.qcd_eig_force(1, 0, 0), lambda: ctx.qcd_local_coherence(1, 0),
+                 ctx.qcd_mg_info2, ctx.qcd_mg_get_P2, ctx.qcd_mg_get_coarse2):
         with pytest.raises(qcd.QcdError) as e:
             call()
         assert e.value.code in (qcd.QCD_ENOTSETUP, qcd.QCD_EINVAL)
@@ -77,7 +78,9 @@ def test_calls_without_gauge_fail_cleanly():
 
 
 @pytest.mark.parametrize("bad", [dict(extraction=2), dict(update_every=-1), dict(block=0),
-                                 dict(m_max=60, block=8), dict(sap_block_iters=0)])
+                                 dict(m_max=60, block=8), dict(sap_block_iters=0), dict(levels=4),
+                                 dict(levels=1), dict(nv2=0), dict(nv2=33), dict(agg2=(2, 0, 2, 2)),
+                                 dict(nu2=-1)])
 def test_create_rejects_each_bad_field(bad):
     """Parameter validation happens in qcd_create, on the host, before any GPU work."""
     from paper_2004_08146_gb300 import qcd
@@ -93,6 +96,7 @@ def test_default_params_method_variants():
     p = qcd.default_params()
     assert p.extraction == qcd.QCD_EXTRACT_HARMONIC and p.update_every == 1
     assert p.shift_rho == 1 and p.block == 2
+    assert p.levels == 2 and p.nv2 == 8 and tuple(p.agg2) == (2, 2, 2, 2) and p.nu2 == 2
 
 
 @pytest.mark.parametrize("dims,m0,csw", [((1, 4, 4, 4), -0.2, 1.0), ((4, 4, 4, 5000), -0.2, 1.0),
