@@ -95,8 +95,7 @@ typedef struct qcd_params {
     int    verbose;          /* 1: per-lock progress on stderr */
     int    levels;           /* 2 (default) or 3: the coarse solve becomes the K-cycle --
                                 FGMRES on D_c to coarse_tol, preconditioned by a
-                                two-level cycle on the coarse lattice (this path has
-                                not been validated on a GPU yet) */
+                                two-level cycle on the coarse lattice */
     int    nv2;              /* level-2 test vectors: the first nv2 fine test vectors
                                 restricted by P^H (default 8, <= Nv) */
     int    agg2[4];          /* level-2 aggregate extents on the coarse lattice (2,2,2,2) */

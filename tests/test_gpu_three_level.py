@@ -1,9 +1,7 @@
 """GPU parity of the three-level hierarchy against the oracle's
 ``ThreeLevelMG`` through the C ABI: P2 and the level-2 Galerkin stencil
 (element by element), one K-cycle with fixed iteration counts (FP64 to
-rounding, FP32 to 1e-4), and a shifted solve with the K-cycle inside.
-
-Not yet run on a GPU: skipped until the first GPU run of this path."""
+rounding, FP32 to 1e-4), and a shifted solve with the K-cycle inside."""
 import numpy as np
 import pytest
 
@@ -12,7 +10,7 @@ from oracle import mg
 from paper_2004_08146_gb300 import synth
 from gpu_util import make_ctx, dev, host, relerr, torch_cuda
 
-pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="three-level GPU path not yet run on a GPU")]
+pytestmark = pytest.mark.gpu
 
 DIMS = (8, 4, 4, 4)
 BLOCK = (2, 2, 2, 2)
