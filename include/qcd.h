@@ -101,6 +101,11 @@ typedef struct qcd_params {
     int    agg2[4];          /* level-2 aggregate extents on the coarse lattice (2,2,2,2) */
     int    nu2;              /* GMRES smoothing steps on the coarse lattice per level-1
                                 cycle (gmres_smooth_iters iterations each; default 2) */
+    int    coarse_layout;    /* data placement of the one-launch coarse GMRES: 0 automatic
+                                (default); 1 stencil blocks and Krylov basis in shared
+                                memory; 2 Krylov basis in shared memory; 3 Krylov basis
+                                in global memory (any coarse lattice).  A forced layout
+                                that does not fit returns EINVAL. */
 } qcd_params;
 
 typedef struct qcd_solve_info {
@@ -264,6 +269,21 @@ int qcd_local_coherence(qcd_ctx* ctx, int nvec, const void* V, double* out);
 int qcd_mg_get_P(qcd_ctx* ctx, double* P_host);
 int qcd_mg_get_coarse(qcd_ctx* ctx, double* A_host);
 
+/* The small projected eigenproblem of one Davidson step (Sec. 3): with
+ * extraction QCD_EXTRACT_HARMONIC, the harmonic Ritz pencil of Theorem 1 /
+ * Eq. 3.5, (W^H V) s = (1/theta) (W^H W) s, given G = W^H W (Hermitian
+ * positive definite) and H = W^H V (Hermitian) for W = Q V; with
+ * QCD_EXTRACT_RITZ the Ritz-Galerkin problem H s = theta s for orthonormal V
+ * (G is ignored and may be NULL).  G, H: HOST complex128 m x m column-major,
+ * 1 <= m <= 112 (the library's Davidson basis cap).  Outputs (HOST): theta[m]
+ * sorted by ascending |theta| (ties ascending theta) and S (complex128
+ * m x m column-major, column i the coefficient vector of pair i, normalised
+ * so that S^H G S = I; S^H S = I for Rayleigh-Ritz).  Computed by the kernels
+ * of qcd_eigs: Cholesky, FP32 Jacobi and FP64 refinement of every pair.
+ * EINVAL on bad arguments or a G that is not positive definite. */
+int qcd_projected_eig(qcd_ctx* ctx, int m, const double* G, const double* H, int extraction, double* theta,
+                      double* S);
+
 /* `sweeps` SAP sweeps (Eq. 2.10; colour 0 blocks, then colour 1) on
  * op(tau) x = b with GMRES block solves of params.sap_block_iters steps to
  * params.sap_block_tol (block_tol < 0 forces exactly sap_block_iters
@@ -280,7 +300,8 @@ int qcd_mg_cycle(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* 
  * application that gives the library a fixed memory budget up front, or a
  * plugin whose host owns every allocation).  Same arguments, layout and
  * result as qcd_sap; all scratch (colour block lists, nrhs residual fields,
- * block-GMRES vectors for blocks of more than 32 sites) comes from one 64 MiB
+ * block-GMRES vectors for every block size other than 16 and 32 sites, whose
+ * kernels keep them in shared memory) comes from one 64 MiB
  * file-scope device array that every GPU loading libqcd keeps until the
  * process exits.  Needs lists + 12 * V * nrhs complex fields (+ Krylov
  * vectors) <= 64 MiB, else EINVAL with a message.  The first call on a device

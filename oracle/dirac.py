@@ -90,13 +90,15 @@ def _dag(M):
 
 
 def _cmul(U, psi):
-    """Colour matrix (..., 3, 3) times spinor (..., 4, 3) on the colour index."""
-    return np.einsum('...ab,...sb->...sa', U, psi)
+    """Colour matrix (..., 3, 3) times spinor (..., 4, 3) on the colour index:
+    out[s, a] = sum_b U[a, b] psi[s, b] (as a batched matrix product psi U^T)."""
+    return np.matmul(psi, np.swapaxes(U, -1, -2))
 
 
 def _smul(G, psi):
-    """Spin matrix (4, 4) times spinor (..., 4, 3) on the spin index."""
-    return np.einsum('st,...tc->...sc', G, psi)
+    """Spin matrix (4, 4) times spinor (..., 4, 3) on the spin index:
+    out[s, c] = sum_t G[s, t] psi[t, c]."""
+    return np.matmul(G, psi)
 
 
 # ---------------------------------------------------------------- clover

@@ -74,11 +74,28 @@ class Blocking:
         self.colour = c.sum(axis=1) % 2
         self.bcoords = c
 
+    def _split_shape(self):
+        sh = []
+        for c, b in zip(self.cdims, self.block):
+            sh += [c, b]
+        return tuple(sh)
+
+    def gather(self, f, tail):
+        """dims + tail -> (nblocks, bsites) + tail, the same as
+        ``f.reshape((-1,) + tail)[self.sites]`` (a pure re-indexing: each fine
+        axis split into (block coordinate, local coordinate), block axes
+        first)."""
+        nt = len(tail)
+        g = np.asarray(f).reshape(self._split_shape() + tail)
+        g = g.transpose((0, 2, 4, 6, 1, 3, 5, 7) + tuple(range(8, 8 + nt)))
+        return g.reshape((self.nblocks, self.bsites) + tail)
+
     def scatter(self, fb, tail):
-        """(nblocks, bsites) + tail -> dims + tail."""
-        out = np.zeros((int(np.prod(self.dims)),) + tail, dtype=fb.dtype)
-        out[self.sites.reshape(-1)] = fb.reshape((-1,) + tail)
-        return out.reshape(self.dims + tail)
+        """(nblocks, bsites) + tail -> dims + tail (inverse of ``gather``)."""
+        nt = len(tail)
+        g = np.asarray(fb).reshape(tuple(self.cdims) + tuple(self.block) + tail)
+        g = g.transpose((0, 4, 1, 5, 2, 6, 3, 7) + tuple(range(8, 8 + nt)))
+        return np.ascontiguousarray(g).reshape(self.dims + tail)
 
 
 def _flat(psi):
@@ -250,11 +267,15 @@ class Interpolation:
 
     def restrict(self, r):
         """R r = P^H r; returns coarse vector (nblocks, 2, nv) (Eq. 2.8, R = P^H)."""
-        rb = _flat(r)[self.blk.sites]                                  # (nb, bs, 4, 3)
+        rb = self.blk.gather(r, (4, 3))                                 # (nb, bs, 4, 3)
         out = np.empty((self.blk.nblocks, 2, self.nv), dtype=np.complex128)
+        nb = self.blk.nblocks
         for chi in range(2):
-            out[:, chi] = np.einsum('bilsc,blsc->bi', np.conj(self.P[:, chi]),
-                                    rb[:, :, 2 * chi:2 * chi + 2, :])
+            # per aggregate: the nv inner products <P_i, r> = conj(sum P_i conj(r))
+            # over (site, spin, colour)
+            Pc = self.P[:, chi].reshape(nb, self.nv, -1)
+            rc = np.conj(rb[:, :, 2 * chi:2 * chi + 2, :]).reshape(nb, -1, 1)
+            out[:, chi] = np.conj(np.matmul(Pc, rc)[..., 0])
         return out
 
     def prolong(self, xc):

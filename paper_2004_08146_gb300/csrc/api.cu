@@ -6,6 +6,7 @@
 // control decisions; every vector operation runs in the kernels of the other
 // translation units.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -108,6 +109,12 @@ struct qcd_ctx {
         c2.ready = false;
     }
 
+    void drop_buf(const std::string& name) {
+        auto it = ws.find(name);
+        if (it == ws.end()) return;
+        if (it->second.p) cudaFree(it->second.p);
+        ws.erase(it);
+    }
     void* buf(const std::string& name, size_t bytes) {
         DevBuf& b = ws[name];
         if (b.bytes < bytes) {
@@ -167,13 +174,14 @@ namespace {
 size_t esz(int prec) { return prec == QCD_FP64 ? sizeof(double2) : sizeof(float2); }
 
 void validate_params(const qcd_params& p) {
-    if (p.m_min < 1 || p.m_max < p.m_min + 1 || p.m_max > 64)
-        throw QcdError(QCD_EINVAL, "need 1 <= m_min < m_max <= 64");
-    if (p.block < 1 || p.block > 16) throw QcdError(QCD_EINVAL, "block must be in [1, 16]");
+    if (p.m_min < 1 || p.m_max < p.m_min + 1 || p.m_max > kMaxBasis - 1)
+        throw QcdError(QCD_EINVAL, "need 1 <= m_min < m_max < " + std::to_string(kMaxBasis));
+    if (p.block < 1 || p.block > 32) throw QcdError(QCD_EINVAL, "block must be in [1, 32]");
     if (p.update_every < 0) throw QcdError(QCD_EINVAL, "update_every must be >= 0");
     if (p.extraction != QCD_EXTRACT_HARMONIC && p.extraction != QCD_EXTRACT_RITZ)
         throw QcdError(QCD_EINVAL, "bad extraction");
-    if (p.m_max + p.block > 64) throw QcdError(QCD_EINVAL, "need m_max + block <= 64");
+    if (p.m_max + p.block > kMaxBasis)
+        throw QcdError(QCD_EINVAL, "need m_max + block <= " + std::to_string(kMaxBasis));
     if (p.nu < 0 || p.sap_block_iters < 1 || p.sap_block_iters > 32) throw QcdError(QCD_EINVAL, "bad smoother params");
     if (p.inner_maxiter < 1 || p.inner_maxiter > 64 || p.coarse_maxiter < 1 || p.coarse_maxiter > 200 ||
         p.plain_maxiter < 1 || p.plain_maxiter > 200)
@@ -184,6 +192,7 @@ void validate_params(const qcd_params& p) {
     if (p.nv2 < 1 || p.nv2 > 32 || p.nu2 < 0) throw QcdError(QCD_EINVAL, "need 1 <= nv2 <= 32 and nu2 >= 0");
     for (int mu = 0; mu < 4; ++mu)
         if (p.agg2[mu] < 1) throw QcdError(QCD_EINVAL, "agg2 extents must be >= 1");
+    if (p.coarse_layout < 0 || p.coarse_layout > 3) throw QcdError(QCD_EINVAL, "coarse_layout must be in [0, 3]");
 }
 
 // ------------------------------------------------------------------ linear operators
@@ -327,11 +336,15 @@ GmresResult gmres_batched(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn
 // kry_* kernels and converged right-hand sides are skipped through the
 // device `active` flags, so the solve is one launch sequence with no host
 // round trip.  `outer_act` (may be null) masks right-hand sides from the start.
+// poll > 0: every `poll` steps the host reads the active flags (one small
+// copy) and stops once every right-hand side has converged, so a solve that
+// usually ends far below maxit launches only the steps it needs.
 struct DevGmresOut {
     KryDev K;
+    int steps = 0;   // steps launched
 };
 DevGmresOut gmres_dev(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn& A, const OpFn* M, const void* b,
-                      void* x, double tol, int maxit, const std::string& tag, const int* outer_act) {
+                      void* x, double tol, int maxit, const std::string& tag, const int* outer_act, int poll = 0) {
     cudaStream_t st = ctx->st;
     if (maxit > kMaxKry) throw QcdError(QCD_EINVAL, "too many Krylov steps");
     const size_t vs = n * nrhs;
@@ -348,6 +361,7 @@ DevGmresOut gmres_dev(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn& A,
     kry_init(K, nr, outer_act, st);
     blas_zero(prec, x, vs, st);
     blas_scale_dev(prec, b, Vk, K.scale, nrhs, n, false, false, st, K.active);
+    int steps = 0;
     for (int it = 0; it < maxit; ++it) {
         void* vj = Vk + (size_t)it * vs * eb;
         if (M) {
@@ -365,11 +379,25 @@ DevGmresOut gmres_dev(qcd_ctx* ctx, int prec, size_t n, int nrhs, const OpFn& A,
         kry_step(K, it, h1, h2, nr, st);
         if (it + 1 < maxit) blas_scale_dev(prec, w, Vk + (size_t)(it + 1) * vs * eb, K.scale, nrhs, n, false, false, st,
                                            K.active);
+        steps = it + 1;
+        if (poll > 0 && steps % poll == 0 && steps < maxit) {
+            // (the staging buffer is taken here: preconditioner calls may regrow it)
+            int* hact = (int*)ctx->host(((size_t)nrhs * sizeof(int) + sizeof(double2) - 1) / sizeof(double2));
+            CK(cudaMemcpyAsync(hact, K.active, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            bool any = false;
+            for (int j = 0; j < nrhs; ++j) any = any || hact[j] != 0;
+            if (!any) break;
+        }
     }
     kry_finish(K, st);
-    blas_multiaxpy(prec, M ? (const void*)Zk : (const void*)Vk, maxit, vs, K.coef, 1.0, x, nrhs, n, st, outer_act);
+    if (steps > 0)
+        blas_multiaxpy(prec, M ? (const void*)Zk : (const void*)Vk, steps, vs, K.coef, 1.0, x, nrhs, n, st, outer_act);
     check_launch("gmres_dev");
-    return DevGmresOut{K};
+    DevGmresOut out;
+    out.K = K;
+    out.steps = steps;
+    return out;
 }
 
 // per-right-hand-side steps of a finished gmres_dev (one device-to-host copy)
@@ -481,9 +509,10 @@ void level2_solve(qcd_ctx* ctx, int prec, int op, int nrhs, const void* rc, void
     const int maxit = std::min(ctx->p.coarse_maxiter, kMaxCoarse);
     bool done = !ctx->no_coop;
     if (done) {
-        const int grp = std::min(nrhs, coarse_gmres_group(c2, prec, maxit));
-        if (grp < 1) throw QcdError(QCD_EINVAL, "level 2 too large for the shared-memory Krylov basis");
-        void* scr = ctx->buf("l2.scr", coarse_gmres_scratch(c2, prec, grp, maxit, coarse_gmres_grid()));
+        const int lay = ctx->p.coarse_layout;
+        const int grp = std::min(nrhs, coarse_gmres_group(c2, prec, maxit, lay));
+        if (grp < 1) throw QcdError(QCD_EINVAL, "level-2 GMRES: the coarse_layout asked for does not fit in shared memory");
+        void* scr = ctx->buf("l2.scr", coarse_gmres_scratch(c2, prec, grp, maxit, lay));
         int* its = (int*)ctx->buf("l2.its", (size_t)nrhs * sizeof(int));
         double* res = (double*)ctx->buf("l2.res", (size_t)nrhs * sizeof(double));
         for (int j0 = 0; j0 < nrhs && done; j0 += grp) {
@@ -491,7 +520,7 @@ void level2_solve(qcd_ctx* ctx, int prec, int op, int nrhs, const void* rc, void
             const int rcode = coarse_gmres(c2, prec, op, nj, (const char*)rc + (size_t)j0 * nco2 * esz(prec),
                                            (char*)xc + (size_t)j0 * nco2 * esz(prec), taud + j0,
                                            act ? act + j0 : nullptr, ctx->p.coarse_tol, maxit, scr, its + j0,
-                                           res + j0, ctx->counters(), ctx->st);
+                                           res + j0, ctx->counters(), lay, ctx->st);
             if (rcode != 0) {
                 cudaGetLastError();
                 if (j0 > 0) throw QcdError(QCD_ECUDA, "cooperative level-2 solve failed mid-batch");
@@ -558,17 +587,18 @@ void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void
     CK(cudaMemcpyAsync(taud, tau, nrhs * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     if (ctx->p.levels == 3 && ctx->c2.ready) {
         // K-cycle: FGMRES on the level-1 operator to coarse_tol, preconditioned
-        // by the level-1 two-level cycle (host-controlled: it stops when done)
+        // by the level-1 two-level cycle.  Device-controlled (Givens and
+        // stopping in kry_* kernels, converged right-hand sides skipped); the
+        // host looks at the active flags every 4 steps to stop early.
         std::vector<double> tv(tau, tau + nrhs);
         OpFn A1 = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int*) {
             coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st);
         };
-        OpFn M1 = [ctx, prec, op, nrhs, tv, taud, act](const void* in, void* out, const int*) {
-            level1_cycle(ctx, prec, op, nrhs, in, out, tv.data(), taud, act);
+        OpFn M1 = [ctx, prec, op, nrhs, tv, taud, act](const void* in, void* out, const int* a) {
+            level1_cycle(ctx, prec, op, nrhs, in, out, tv.data(), taud, a ? a : act);
         };
-        blas_zero(prec, rc, nco * nrhs, ctx->st);
-        mg_restrict(ctx->f, c, prec, nrhs, b, rc, ctx->st, act);
-        gmres_batched(ctx, prec, nco, nrhs, A1, &M1, rc, xc, ctx->p.coarse_tol, ctx->p.coarse_maxiter, "kc1");
+        const int kmax = std::min(ctx->p.coarse_maxiter, kMaxKry);
+        gmres_dev(ctx, prec, nco, nrhs, A1, &M1, rc, xc, ctx->p.coarse_tol, kmax, "kc1", act, 4);
         mg_prolong(ctx->f, c, prec, nrhs, xc, x, false, ctx->st, act);
         smooth(ctx, prec, op, nrhs, b, x, tau, act);
         check_launch("mg k-cycle");
@@ -577,16 +607,18 @@ void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void
     const int maxit = std::min(ctx->p.coarse_maxiter, kMaxCoarse);
     bool done = !ctx->no_coop;
     if (done) {
-        const int grp = std::min(nrhs, coarse_gmres_group(c, prec, maxit));
-        if (grp < 1) throw QcdError(QCD_EINVAL, "coarse level too large for the shared-memory Krylov basis");
-        void* scr = ctx->buf("cyc.scr", coarse_gmres_scratch(c, prec, grp, maxit, coarse_gmres_grid()));
+        const int lay = ctx->p.coarse_layout;
+        const int grp = std::min(nrhs, coarse_gmres_group(c, prec, maxit, lay));
+        if (grp < 1) throw QcdError(QCD_EINVAL, "coarse GMRES: the coarse_layout asked for does not fit in shared memory");
+        void* scr = ctx->buf("cyc.scr", coarse_gmres_scratch(c, prec, grp, maxit, lay));
         int* its = (int*)ctx->buf("cyc.its", (size_t)nrhs * sizeof(int));
         double* res = (double*)ctx->buf("cyc.res", (size_t)nrhs * sizeof(double));
         for (int j0 = 0; j0 < nrhs && done; j0 += grp) {
             const int nj = std::min(grp, nrhs - j0);
             int rcode = coarse_gmres(c, prec, op, nj, (const char*)rc + (size_t)j0 * nco * esz(prec),
                                      (char*)xc + (size_t)j0 * nco * esz(prec), taud + j0, act ? act + j0 : nullptr,
-                                     ctx->p.coarse_tol, maxit, scr, its + j0, res + j0, ctx->counters(), ctx->st);
+                                     ctx->p.coarse_tol, maxit, scr, its + j0, res + j0, ctx->counters(), lay,
+                                     ctx->st);
             if (rcode != 0) {
                 cudaGetLastError();
                 if (j0 > 0) throw QcdError(QCD_ECUDA, "cooperative coarse solve failed mid-batch");
@@ -730,6 +762,10 @@ void mg_setup_impl(qcd_ctx* ctx, int Nv, const int block[4]) {
         build_from_vectors(ctx, W, Nv, block);
     }
     CK(cudaStreamSynchronize(ctx->st));
+    // the setup work fields (3 Nv fine fields) are not needed afterwards
+    ctx->drop_buf("setup.w");
+    ctx->drop_buf("setup.b");
+    ctx->drop_buf("setup.x");
 }
 
 // ------------------------------------------------------------------ shifted solves
@@ -786,18 +822,30 @@ double shifted_solve_impl(qcd_ctx* ctx, int nrhs, const double2* b, double2* x, 
     const int max_refine = 200;
     const int restart = std::max(ctx->p.inner_maxiter, 20);
     std::vector<double> relres(nrhs, 1.0);
-    for (; refine < max_refine; ++refine) {
+    // best iterate of each right-hand side so far (returned on ENOCONV)
+    double2* xbest = (double2*)ctx->buf("ss.xbest", n * nrhs * sizeof(double2));
+    std::vector<double> best(nrhs, INFINITY);
+    for (;; ++refine) {
         // current residuals
         blas_multidot(QCD_FP64, r, 1, n * nrhs, r, nrhs, n, nr, part, ctx->dot_counters(nrhs), ctx->st);
         const double2* h = ctx->fetch(nr, nrhs);
         worst = 0.0;
-        double maxr = 0.0;
         for (int j = 0; j < nrhs; ++j) {
             relres[j] = bn[j] > 0 ? std::sqrt(h[j].x) / bn[j] : 0.0;
             worst = std::max(worst, relres[j]);
-            maxr = std::max(maxr, std::sqrt(h[j].x));
         }
+        for (int j = 0; j < nrhs; ++j)
+            if (relres[j] < best[j]) {
+                best[j] = relres[j];
+                blas_copy(QCD_FP64, x + (size_t)j * n, xbest + (size_t)j * n, n, ctx->st);
+            }
         if (worst <= tol) break;
+        if (refine == max_refine) {
+            // cap reached: return the best iterate of every right-hand side
+            blas_copy(QCD_FP64, xbest, x, n * nrhs, ctx->st);
+            worst = *std::max_element(best.begin(), best.end());
+            break;
+        }
         // correction equation on the chosen form: (D - tau G5) c = G5 r or (Q - tau) c = r
         if (form == QCD_OP_D) blas_gamma5(QCD_FP64, r, rr, (size_t)ctx->f.g.V * nrhs, ctx->st);
         else blas_copy(QCD_FP64, r, rr, n * nrhs, ctx->st);
@@ -819,35 +867,45 @@ double shifted_solve_impl(qcd_ctx* ctx, int nrhs, const double2* b, double2* x, 
 }
 
 // ------------------------------------------------------------------ GD-lambda-AMG
-// tall-skinny basis transform: Out[j] = sum_i C[i + j m] In[i] (j < p), FP64
-__global__ void basis_transform_kernel(const double2* __restrict__ In, int m, const double2* __restrict__ C, int p,
-                                       double2* __restrict__ Out, size_t n) {
-    extern __shared__ double2 Cs[];
-    for (int e = threadIdx.x; e < m * p; e += blockDim.x) Cs[e] = C[e];
-    __syncthreads();
-    const int j0 = blockIdx.y * 8;
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        double2 acc[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) acc[jj] = make_double2(0, 0);
-        for (int i = 0; i < m; ++i) {
-            double2 v = In[(size_t)i * n + k];
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj)
-                if (j0 + jj < p) acc[jj] += Cs[(j0 + jj) * m + i] * v;
+// Tall-skinny basis transform in place: A[j] <- sum_i C[i + j m] A[i] for
+// j < p <= m, FP64 (thick restart V <- V C).  Each CTA stages a tile of
+// kTileRows rows of all m vectors in shared memory, then writes the p new
+// vectors' rows over them: rows are independent, so no second basis copy is
+// needed.  A warp computes one output vector for the tile's 32 rows (one row
+// per lane), so every coefficient C[i + j m] is a warp-wide broadcast.
+constexpr int kTileRows = 32;
+__global__ void __launch_bounds__(256) basis_transform_inplace_kernel(double2* __restrict__ A, int m,
+                                                                      const double2* __restrict__ C, int p, size_t n) {
+    extern __shared__ double2 tile[];   // [m][kTileRows]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t ntiles = (n + kTileRows - 1) / kTileRows;
+    for (size_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const size_t k0 = t * kTileRows;
+        const int rows = (int)min((size_t)kTileRows, n - k0);
+        for (int e = threadIdx.x; e < m * kTileRows; e += blockDim.x) {
+            const int i = e / kTileRows, r = e % kTileRows;
+            tile[e] = r < rows ? A[(size_t)i * n + k0 + r] : make_double2(0, 0);
         }
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-            if (j0 + jj < p) Out[(size_t)(j0 + jj) * n + k] = acc[jj];
+        __syncthreads();
+        for (int j = warp; j < p; j += nw) {
+            double2 acc = make_double2(0, 0);
+            for (int i = 0; i < m; ++i) acc += __ldg(&C[(size_t)j * m + i]) * tile[i * kTileRows + lane];
+            if (lane < rows) A[(size_t)j * n + k0 + lane] = acc;
+        }
+        __syncthreads();
     }
 }
-void basis_transform(const double2* In, int m, const double2* C, int p, double2* Out, size_t n, cudaStream_t st) {
-    int gx = (int)std::min<size_t>((n + 255) / 256, 2048);
-    dim3 grid(gx, (p + 7) / 8);
-    const size_t sm = (size_t)m * p * sizeof(double2);
-    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(basis_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+void basis_transform_inplace(double2* A, int m, const double2* C, int p, size_t n, cudaStream_t st) {
+    const size_t sm = (size_t)m * kTileRows * sizeof(double2);
+    if (sm > 48 * 1024)
+        CK(cudaFuncSetAttribute(basis_transform_inplace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t ntiles = (n + kTileRows - 1) / kTileRows;
+    const int grid = (int)std::min<size_t>(ntiles, (size_t)std::max(1, sms) * 4);
     KTimer kt("basis_transform", (double)(m + p) * n * 16, 8.0 * m * p * n, st);
-    basis_transform_kernel<<<grid, 256, sm, st>>>(In, m, C, p, Out, n);
+    basis_transform_inplace_kernel<<<grid, 256, sm, st>>>(A, m, C, p, n);
 }
 // G[i][m] = d1[i], G[m][i] = conj d1[i]; Hm[i][m] = d2[i]; Hm[m][i] = conj d2[i]  (ld = column stride).
 // H = W^H V = V^H Q V is Hermitian because Q is (Sec. 2), so its new row
@@ -894,7 +952,7 @@ __global__ void householder_vector_kernel(const double2* __restrict__ s, int m, 
 // rows in place: it reads In[j][k] before it writes position j-1.
 __global__ void householder_deflate_kernel(double2* __restrict__ A0, double2* __restrict__ A1, int m, size_t n,
                                            const double2* __restrict__ hw) {
-    __shared__ double2 w[kMaxKry + 1];
+    __shared__ double2 w[kMaxBasis + 1];
     for (int i = threadIdx.x; i <= m; i += blockDim.x) w[i] = hw[i];
     __syncthreads();
     double2* A = blockIdx.y ? A1 : A0;
@@ -912,7 +970,7 @@ __global__ void householder_deflate_kernel(double2* __restrict__ A0, double2* __
 __global__ void householder_gram_kernel(const double2* __restrict__ G, double2* __restrict__ Gt,
                                         const double2* __restrict__ Hm, double2* __restrict__ Hmt, int m, int ld,
                                         const double2* __restrict__ hw) {
-    __shared__ double2 w[kMaxKry + 1], a[kMaxKry], b[kMaxKry];
+    __shared__ double2 w[kMaxBasis + 1], a[kMaxBasis], b[kMaxBasis];
     __shared__ double2 g;
     const double2* M = blockIdx.x ? Hm : G;
     double2* out = blockIdx.x ? Hmt : Gt;
@@ -946,7 +1004,7 @@ struct GD {
     qcd_ctx* ctx;
     size_t n;
     int mcap, kcap;
-    double2 *V, *W, *Vt, *Wt, *X, *G, *Hm, *Gt, *Hmt, *S, *work, *C, *dots, *part, *u, *Qu, *R, *T, *tmp;
+    double2 *V, *W, *X, *G, *Hm, *Gt, *Hmt, *S, *work, *C, *dots, *part, *u, *Qu, *R, *T, *tmp;
     double* mu;
     double* mu_ref;   // refined eigenvalues of the targets
     int* status;
@@ -964,7 +1022,6 @@ struct GD {
         kcap = kcap_;
         auto B = [&](const char* nm, size_t cnt) { return (double2*)ctx->buf(std::string("gd.") + nm, cnt * sizeof(double2)); };
         V = B("V", (size_t)mcap * n); W = B("W", (size_t)mcap * n);
-        Vt = B("Vt", (size_t)mcap * n); Wt = B("Wt", (size_t)mcap * n);
         X = B("X", (size_t)kcap * n);
         G = B("G", (size_t)mcap * mcap); Hm = B("Hm", (size_t)mcap * mcap);
         Gt = B("Gt", (size_t)mcap * mcap); Hmt = B("Hmt", (size_t)mcap * mcap);
@@ -1032,7 +1089,7 @@ struct GD {
         blas_multidot(QCD_FP64, W, m + 1, n, W + (size_t)m * n, 1, n, dots, part, ctx->dot_counters(m + 1), st);
         blas_multidot(QCD_FP64, W, m + 1, n, v, 1, n, dots + mcap, part, ctx->dot_counters(m + 1), st);
         KTimer kt("gram_update", 0.0, 0.0, st);
-        gram_update_kernel<<<1, 64, 0, st>>>(G, Hm, mcap, m, dots, dots + mcap);
+        gram_update_kernel<<<1, kMaxBasis + 1, 0, st>>>(G, Hm, mcap, m, dots, dots + mcap);
         check_launch("add_vector");
         ++m;
         return true;
@@ -1069,10 +1126,8 @@ struct GD {
     // replace the basis by V C (m x p), W C and the Gram matrices by C^H G C
     void transform(const double2* Cm, int p) {
         cudaStream_t st = ctx->st;
-        basis_transform(V, m, Cm, p, Vt, n, st);
-        basis_transform(W, m, Cm, p, Wt, n, st);
-        std::swap(V, Vt);
-        std::swap(W, Wt);
+        basis_transform_inplace(V, m, Cm, p, n, st);
+        basis_transform_inplace(W, m, Cm, p, n, st);
         small_gram_transform(G, m, mcap, Cm, p, Gt, mcap, work, st);
         small_gram_transform(Hm, m, mcap, Cm, p, Hmt, mcap, work, st);
         std::swap(G, Gt);
@@ -1136,7 +1191,10 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
     gd.ritz = P.extraction == QCD_EXTRACT_RITZ;
     const int n0 = P.use_mg ? ctx->n_test : P.n_init;
     if (n0 + block > P.m_max) throw QcdError(QCD_EINVAL, "m_max too small for the start basis");
-    gd.alloc(P.m_max + block, k + P.m_max + 2 * block + 8, block);
+    // locked-pair slots: k plus room for the pairs locked while the last
+    // targets finish; when they are full, a new lock replaces the locked
+    // pair of largest |lambda| (or is dropped if it is larger still)
+    gd.alloc(P.m_max + block, k + 2 * block + 8, block);
     CK(cudaMemsetAsync(ctx->counters(), 0, 2 * sizeof(unsigned long long), st));
     double2* t0 = gd.tmp;
     // start basis: setup test vectors (or random vectors without MG)
@@ -1149,7 +1207,9 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
     int nT = block;
     int outer = 0, inner = 0, updates = 0, locks_since_update = 0;
     bool finished = false;
-    double2* vbuf = (double2*)ctx->buf("gd.vupd", (size_t)std::max(1, ctx->n_test) * n * sizeof(double2));
+    // interpolation updates stage their vectors in the test-vector buffer
+    // (the setup vectors are in the start basis already)
+    double2* vbuf = ctx->test_vectors;
     std::vector<double> theta;
     std::vector<int> col;
     std::vector<double> tsel;
@@ -1213,10 +1273,20 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                 const double2* hr = ctx->fetch(gd.dots, 1);
                 const double rn = std::sqrt(std::max(hr[0].x, 0.0));
                 if (rn <= tol) {
-                    if (gd.nlock >= gd.kcap) throw QcdError(QCD_EINVAL, "too many locked vectors");
-                    gd.lock_vector(gd.u);
-                    gd.lam.push_back(rho);
-                    gd.lres.push_back(rn);
+                    if (gd.nlock < gd.kcap) {
+                        gd.lock_vector(gd.u);
+                        gd.lam.push_back(rho);
+                        gd.lres.push_back(rn);
+                    } else {
+                        int big = 0;
+                        for (int q = 1; q < gd.nlock; ++q)
+                            if (std::fabs(gd.lam[q]) > std::fabs(gd.lam[big])) big = q;
+                        if (std::fabs(rho) < std::fabs(gd.lam[big])) {
+                            blas_copy(QCD_FP64, gd.u, gd.X + (size_t)big * n, n, st);
+                            gd.lam[big] = rho;
+                            gd.lres[big] = rn;
+                        }
+                    }
                     // deflate: V <- V C with C the complement of s/||s||
                     gd.deflate(s);
                     ++locks_since_update;
@@ -1455,6 +1525,15 @@ int qcd_set_gauge(qcd_ctx* ctx, const double* U, const int dims[4], double m0, d
         CK(cudaMalloc(&f.U32s, nl * sizeof(float2)));
         CK(cudaMalloc(&f.A32s, (size_t)V * 18 * sizeof(float4)));
         CK(cudaMemcpyAsync(f.U64, U, nl * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+        // the links must be SU(3) matrices (Sec. 2): finite and unitary
+        const double dev = gauge_unitarity_deviation(f.U64, (size_t)V * 4, ctx->counters(), ctx->st);
+        check_launch("gauge check");
+        if (!(dev <= 1e-6)) {
+            ctx->release();
+            throw QcdError(QCD_EINVAL, std::isfinite(dev) ? "gauge links are not unitary (max |U U^H - I| = " +
+                                                                std::to_string(dev) + ")"
+                                                          : "gauge links contain non-finite entries");
+        }
         blas_convert(QCD_FP64, f.U64, QCD_FP32, f.U32, nl, ctx->st);
         launch_clover_build(f, ctx->st);
         check_launch("set_gauge");
@@ -1715,6 +1794,59 @@ int qcd_mg_get_coarse2(qcd_ctx* ctx, double* A_host) {
     });
 }
 
+int qcd_projected_eig(qcd_ctx* ctx, int m, const double* G, const double* H, int extraction, double* theta,
+                      double* S) {
+    return guarded(ctx, [&]() {
+        if (m < 1 || m > kMaxBasis || !H || !theta || !S || (extraction == QCD_EXTRACT_HARMONIC && !G))
+            throw QcdError(QCD_EINVAL, "bad arguments");
+        if (extraction != QCD_EXTRACT_HARMONIC && extraction != QCD_EXTRACT_RITZ)
+            throw QcdError(QCD_EINVAL, "bad extraction");
+        const size_t mm = (size_t)m * m;
+        double2* Gd = (double2*)ctx->buf("pe.G", mm * sizeof(double2));
+        double2* Hd = (double2*)ctx->buf("pe.H", mm * sizeof(double2));
+        double2* Sd = (double2*)ctx->buf("pe.S", mm * sizeof(double2));
+        double2* state = (double2*)ctx->buf("pe.state", 3 * mm * sizeof(double2));
+        double* mu = (double*)ctx->buf("pe.mu", (size_t)m * sizeof(double));
+        double* mu_ref = (double*)ctx->buf("pe.mu_ref", (size_t)m * sizeof(double));
+        int* idx = (int*)ctx->buf("pe.idx", (size_t)m * sizeof(int));
+        int* status = (int*)ctx->buf("pe.status", 4 * sizeof(int));
+        std::vector<double2> hG(mm, make_double2(0, 0));
+        if (extraction == QCD_EXTRACT_HARMONIC) memcpy(hG.data(), G, mm * sizeof(double2));
+        else for (int i = 0; i < m; ++i) hG[(size_t)i * m + i] = make_double2(1, 0);
+        std::vector<int> all(m);
+        std::iota(all.begin(), all.end(), 0);
+        CK(cudaMemcpyAsync(Gd, hG.data(), mm * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemcpyAsync(Hd, H, mm * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemcpyAsync(idx, all.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), ctx->st));
+        small_harmonic_eig_inc(Gd, Hd, m, m, 0, mu, Sd, state, status, ctx->st);
+        small_refine_targets(state, m, m, Sd, mu, mu_ref, idx, m, ctx->st);
+        check_launch("projected eig");
+        std::vector<double> hmu(m);
+        std::vector<double2> hS(mm);
+        int hst = 0;
+        CK(cudaMemcpyAsync(hmu.data(), mu_ref, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(hS.data(), Sd, mm * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if (hst != 0) throw QcdError(QCD_EINVAL, "G is not positive definite");
+        std::vector<double> th(m);
+        for (int i = 0; i < m; ++i)
+            th[i] = extraction == QCD_EXTRACT_RITZ ? hmu[i] : (hmu[i] != 0.0 ? 1.0 / hmu[i] : INFINITY);
+        std::vector<int> ord(all);
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+            const double fa = std::fabs(th[a]), fb = std::fabs(th[b]);
+            if (fa != fb) return fa < fb;
+            return th[a] < th[b];
+        });
+        for (int i = 0; i < m; ++i) {
+            theta[i] = th[ord[i]];
+            memcpy(S + (size_t)2 * i * m, hS.data() + (size_t)ord[i] * m, m * sizeof(double2));
+        }
+        return QCD_OK;
+    });
+}
+
 int qcd_sap(qcd_ctx* ctx, int op, int prec, int nrhs, const void* b, void* x, const double* tau, int sweeps,
             double block_tol) {
     return guarded(ctx, [&]() {
@@ -1785,8 +1917,9 @@ int qcd_eigs(qcd_ctx* ctx, int k, double tol, double* lambda, void* V, qcd_eig_i
 // qcd_sap_static: the SAP sweeps of qcd_sap for callers that cannot allocate
 // device memory (a host application that hands the library a fixed memory
 // budget up front, or a plugin whose host owns every allocation).  All
-// scratch -- the colour block lists, the residual fields and, for blocks of
-// more than 32 sites, the block-GMRES Krylov vectors -- lives in one
+// scratch -- the colour block lists, the residual fields and, for block
+// sizes other than 16 and 32 sites (whose kernels keep the Krylov basis in
+// shared memory), the block-GMRES Krylov vectors -- lives in one
 // file-scope device array of kSapStaticBytes that every GPU loading the
 // library keeps until the process exits.
 namespace {
@@ -1795,7 +1928,9 @@ constexpr size_t kSapStaticBytes = 64ull << 20;   // 64 MiB
 __device__ __align__(256) unsigned char g_sap_static[kSapStaticBytes];
 
 constexpr int kStaticMaxDevices = 64;
-void* g_sap_static_ptr[kStaticMaxDevices] = {};   // device address of g_sap_static, per device
+// device address of g_sap_static, per device; first calls on several host
+// threads may race to fill a slot, which they do with the same value
+std::atomic<void*> g_sap_static_ptr[kStaticMaxDevices] = {};
 
 // block lists of the two colours: with an even block-grid extent in mu = 3
 // the blocks of each colour are exactly every second block, so block b goes
@@ -1848,22 +1983,24 @@ extern "C" int qcd_sap_static(qcd_ctx* ctx, int op, int prec, int nrhs, const vo
     const size_t n = ctx->nfine();
     const size_t lists = ((size_t)B.nb * sizeof(int) + 255) & ~size_t(255);
     const size_t rbytes = ((n * nrhs * esz(prec)) + 255) & ~size_t(255);
-    const size_t kbytes = B.bs > 32 ? sap_scratch_bytes(plan, prec, nrhs, ctx->p.sap_block_iters) : 0;
+    // Krylov vectors of the block solves, for exactly the block sizes whose
+    // kernel keeps them in global memory (the same predicate sap_blocks uses)
+    const size_t kbytes = sap_scratch_bytes(plan, prec, nrhs, ctx->p.sap_block_iters);
     if (lists + rbytes + kbytes > kSapStaticBytes)
         return static_fail(ctx, QCD_EINVAL, "qcd_sap_static: problem needs more scratch than the 64 MiB static array");
     // set-up, once per device, with that device current
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
         return static_fail(ctx, QCD_ECUDA, "qcd_sap_static: no usable current device");
-    if (g_sap_static_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_sap_static) != cudaSuccess || p == nullptr) {
+    void* sym = g_sap_static_ptr[dev].load(std::memory_order_acquire);
+    if (sym == nullptr) {
+        if (cudaGetSymbolAddress(&sym, g_sap_static) != cudaSuccess || sym == nullptr) {
             cudaGetLastError();
             return static_fail(ctx, QCD_ECUDA, "qcd_sap_static: cudaGetSymbolAddress failed");
         }
-        g_sap_static_ptr[dev] = p;
+        g_sap_static_ptr[dev].store(sym, std::memory_order_release);
     }
-    unsigned char* base = (unsigned char*)g_sap_static_ptr[dev];
+    unsigned char* base = (unsigned char*)sym;
     plan.blocks_of_colour[0] = (int*)base;
     plan.blocks_of_colour[1] = (int*)base + B.nb / 2;
     void* r = base + lists;

@@ -1,6 +1,9 @@
 // Fine-lattice operator kernels: clover construction (Sec. 4, Table 1 clover
 // term; Sheikholeslami-Wohlert) and the Wilson-clover stencil of Eq. 2.5 in
 // the shifted forms D - tau Gamma5 (Eq. 3.7) and Q - tau (Eq. 3.6).
+#include <algorithm>
+#include <cstring>
+
 #include "internal.h"
 #include "dirac.cuh"
 
@@ -500,6 +503,47 @@ __global__ void soa_copies_kernel(const float2* __restrict__ U, const float* __r
 }
 
 // ------------------------------------------------------------------ host launchers
+// Largest deviation of U U^H from the identity over all links, as the bit
+// pattern of a non-negative double (which orders like the value); a
+// non-finite entry records +inf.
+__global__ void gauge_check_kernel(const double2* __restrict__ U, size_t nlinks, unsigned long long* __restrict__ dev) {
+    double worst = 0.0;
+    for (size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x; l < nlinks; l += (size_t)gridDim.x * blockDim.x) {
+        double2 u[9];
+        bool fin = true;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            u[k] = U[l * 9 + k];
+            fin = fin && isfinite(u[k].x) && isfinite(u[k].y);
+        }
+        if (!fin) { worst = INFINITY; continue; }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                double2 acc = make_double2(a == b ? -1.0 : 0.0, 0.0);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc += u[a * 3 + c] * conj(u[b * 3 + c]);
+                worst = fmax(worst, fmax(fabs(acc.x), fabs(acc.y)));
+            }
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dev, (unsigned long long)__double_as_longlong(worst));
+}
+
+double gauge_unitarity_deviation(const double2* U, size_t nlinks, unsigned long long* scratch, cudaStream_t st) {
+    cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), st);
+    KTimer kt("gauge_check", (double)nlinks * 144, (double)nlinks * 27 * 8, st);
+    const int grid = (int)std::min<size_t>((nlinks + 255) / 256, 4096);
+    gauge_check_kernel<<<grid, 256, 0, st>>>(U, nlinks, scratch);
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return NAN;
+    double d;
+    memcpy(&d, &h, sizeof(d));
+    return d;
+}
+
 void launch_clover_build(const FineOp& f, cudaStream_t st) {
     int th = 128;
     KTimer kt("clover_build", 0.0, 0.0, st);

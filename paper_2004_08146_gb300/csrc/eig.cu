@@ -3,7 +3,7 @@
 // with mu = 1/theta, solved as Cholesky W^H W = L L^H, C = L^-1 (W^H V) L^-H
 // and a parallel (round-robin) complex Jacobi eigensolver, the FP64
 // refinement of the targeted pairs and the QR used for thick restarts.  All
-// run in one CTA (per target) on column-major matrices with m <= 64.
+// run in one CTA (per target) on column-major matrices with m <= kMaxBasis.
 #include "internal.h"
 
 namespace qcd {
@@ -57,10 +57,11 @@ __global__ void __launch_bounds__(kTE) harmonic_eig_inc_kernel(const double2* __
                                                               const double2* __restrict__ Hm, int m, int ld, int m0,
                                                               double* __restrict__ mu, double2* __restrict__ S,
                                                               double2* __restrict__ state, int* __restrict__ status) {
+    constexpr int kPairs = kMaxBasis / 2 + 1;
     __shared__ double red[33];
-    __shared__ int pp[33], qq[33];
-    __shared__ float2 pj[33][3];   // per pair: (c, s), e^{i phi}, unused
-    __shared__ double2 rowv[64], rowt[64];
+    __shared__ int pp[kPairs], qq[kPairs];
+    __shared__ float2 pj[kPairs][3];   // per pair: (c, s), e^{i phi}, unused
+    __shared__ double2 rowv[kMaxBasis], rowt[kMaxBasis];
     __shared__ double lkk_s;
     extern __shared__ double2 shm[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
@@ -265,15 +266,17 @@ __global__ void __launch_bounds__(kTE) harmonic_eig_inc_kernel(const double2* __
 // with |mu_j - rho| below 1e-6 max|mu| (an unresolved cluster) are left out.
 // Then s = Li^H z (FP64) replaces column idx[b] of S and rho goes to
 // mu_out[b] (mu itself is only read, so the CTAs do not race on it).
-__global__ void __launch_bounds__(64) refine_targets_kernel(const double2* __restrict__ state, int m, int ld,
+constexpr int kRefineThreads = 128;   // >= kMaxBasis
+static_assert(kRefineThreads >= kMaxBasis, "one thread per pencil row");
+__global__ void __launch_bounds__(kRefineThreads) refine_targets_kernel(const double2* __restrict__ state, int m, int ld,
                                                             double2* __restrict__ S, const double* __restrict__ mu,
                                                             double* __restrict__ mu_out, const int* __restrict__ idx,
                                                             int steps) {
     __shared__ double red[33];
-    __shared__ double2 zv[64], rv[64];
-    __shared__ float2 cf[64];
-    __shared__ double muv[64];
-    const int tid = threadIdx.x;   // one thread per row, m <= 64
+    __shared__ double2 zv[kRefineThreads], rv[kRefineThreads];
+    __shared__ float2 cf[kRefineThreads];
+    __shared__ double muv[kRefineThreads];
+    const int tid = threadIdx.x;   // one thread per row, m <= kRefineThreads
     const int col = idx[blockIdx.x];
     const double2* Li = state;
     const double2* C = state + (size_t)ld * ld;
@@ -293,7 +296,8 @@ __global__ void __launch_bounds__(64) refine_targets_kernel(const double2* __res
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if ((tid & 31) == 0) red[tid >> 5] = amax;
     __syncthreads();
-    amax = fmax(red[0], blockDim.x > 32 ? red[1] : 0.0);
+    amax = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) amax = fmax(amax, red[w]);
     __syncthreads();
     const double gap_min = 1e-6 * amax;
     double rho = 0.0;
@@ -339,13 +343,13 @@ __global__ void __launch_bounds__(64) refine_targets_kernel(const double2* __res
     if (tid == 0) mu_out[blockIdx.x] = rho;
 }
 
-// Q = orthonormal basis of the columns of S (m x k <= 64): column by column,
+// Q = orthonormal basis of the columns of S (m x k <= kMaxBasis): column by column,
 // classical Gram-Schmidt twice against the previous columns (all inner
 // products of a pass at once, one warp each), then normalisation.
 __global__ void __launch_bounds__(kT) small_qr_kernel(const double2* __restrict__ S, int m, int k, int lds,
                                                       double2* __restrict__ Q) {
     __shared__ double red[33];
-    __shared__ double2 h[64];
+    __shared__ double2 h[kMaxBasis];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     for (int e = tid; e < m * k; e += blockDim.x) Q[e] = S[(e / m) * lds + e % m];
     __syncthreads();
@@ -411,7 +415,7 @@ void small_harmonic_eig_inc(const double2* G, const double2* H, int m, int ld, i
 void small_refine_targets(const double2* state, int m, int ld, double2* S, const double* mu, double* mu_out,
                           const int* idx, int nb, cudaStream_t st) {
     KTimer kt("refine_targets", 0.0, 0.0, st);
-    refine_targets_kernel<<<nb, 64, 0, st>>>(state, m, ld, S, mu, mu_out, idx, 3);
+    refine_targets_kernel<<<nb, kRefineThreads, 0, st>>>(state, m, ld, S, mu, mu_out, idx, 3);
 }
 void small_qr(const double2* S, int m, int k, int lds, double2* Q, double2* work, cudaStream_t st) {
     (void)work;

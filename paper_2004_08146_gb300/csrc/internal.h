@@ -90,6 +90,9 @@ struct Coarse {
 
 // ------------------------------------------------------------------ kernels (dirac.cu)
 void launch_clover_build(const FineOp& f, cudaStream_t st);
+// max |U U^H - I| over nlinks device FP64 links (+inf if any entry is not
+// finite); `scratch` is one device word.  Synchronises the stream.
+double gauge_unitarity_deviation(const double2* U, size_t nlinks, unsigned long long* scratch, cudaStream_t st);
 // `act` (device, per right-hand side, may be null): skip right-hand sides
 // whose flag is 0 (converged systems of a batched Krylov solve).
 // dU = i X U (V*36 double2) and the packed clover derivative dA (V*72 double)
@@ -161,10 +164,17 @@ struct SapPlan {
 void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op, int nrhs,
                 const void* r, void* x, const double* tau, int iters, double tol,
                 void* scratch, cudaStream_t st, const int* act = nullptr);
+// Global scratch of sap_blocks: blocks of 16 and 32 sites keep their Krylov
+// basis in shared memory (0 bytes); every other block size needs
+// (iters + 1) block vectors per block of the larger colour and per rhs.
+bool sap_needs_scratch(const Blocking& B);
 size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters);
 
 // ------------------------------------------------------------------ kernels (krylov.cu)
 constexpr int kMaxKry = 64;        // fine (F)GMRES steps per solve
+// Davidson basis size cap (m_max + targets per iteration): the harmonic
+// pencil kernel keeps two FP32 m x m matrices in shared memory (200 KB at 112)
+constexpr int kMaxBasis = 112;
 constexpr int kMaxCoarse = 200;    // coarse GMRES steps per solve
 constexpr int kMaxCoarseRhs = 16;  // right-hand sides per coarse launch
 
@@ -190,12 +200,15 @@ void kry_step(const KryDev& K, int it, const double2* h1, const double2* h2, con
 void kry_finish(const KryDev& K, cudaStream_t st);
 // Whole batched GMRES on the coarse stencil in one cooperative launch;
 // returns 0 on success, < 0 when the cooperative launch is not possible.
-size_t coarse_gmres_scratch(const Coarse& c, int prec, int nrhs, int maxit, int nct);
+// want_layout: 0 automatic; 1 stencil blocks and Krylov basis in shared
+// memory; 2 basis in shared memory; 3 basis in global memory (any size).
+size_t coarse_gmres_scratch(const Coarse& c, int prec, int nrhs, int maxit, int want_layout);
 int coarse_gmres_grid();
-int coarse_gmres_group(const Coarse& c, int prec, int maxit);   // right-hand sides per launch
+int coarse_gmres_group(const Coarse& c, int prec, int maxit, int want_layout);   // right-hand sides per launch
+int coarse_gmres_layout(const Coarse& c, int prec, int nrhs, int maxit, int want_layout);
 int coarse_gmres(const Coarse& c, int prec, int op, int nrhs, const void* b, void* x, const double* tau_dev,
                  const int* act, double tol, int maxit, void* scratch, int* iters, double* resid,
-                 unsigned long long* counter, cudaStream_t st);
+                 unsigned long long* counter, int want_layout, cudaStream_t st);
 
 // ------------------------------------------------------------------ kernels (eig.cu)
 // Harmonic Ritz pairs of the pencil G s = theta H s (G = W^H W, H = W^H V):
@@ -210,7 +223,7 @@ void small_harmonic_eig_inc(const double2* G, const double2* H, int m, int ld, i
 // small_harmonic_eig_inc.
 void small_refine_targets(const double2* state, int m, int ld, double2* S, const double* mu, double* mu_out,
                           const int* idx, int nb, cudaStream_t st);
-// Orthonormal Q (m x k, column-major, leading dim m) of the columns of S
+// Orthonormal Q (m x k <= kMaxBasis, column-major, leading dim m) of the columns of S
 // (m x k, leading dimension lds) by modified Gram-Schmidt applied twice.
 void small_qr(const double2* S, int m, int k, int lds, double2* Q, double2* work, cudaStream_t st);
 // C (m x p) = A^H B for small column-major matrices: used for Gram updates

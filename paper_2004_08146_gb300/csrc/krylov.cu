@@ -152,6 +152,8 @@ struct CoarseArgs {
     int E;               // chunk length per CTA (= sites per CTA * nc)
     int sps;             // coarse sites per CTA
     int a_smem;          // 1: this CTA's stencil blocks are staged in shared memory
+    Z* Vglob;            // non-null: the Krylov basis and w chunks live in global
+    Z* wglob;            //   memory ([CTA][(maxit+1)][nrhs][E] and [CTA][nrhs][E])
 };
 
 template <typename Z, typename R>
@@ -178,16 +180,20 @@ __device__ __forceinline__ void coarse_row(const CoarseArgs<Z, R>& a, const Z* x
 }
 
 struct CoarseSmem { size_t As, xn, nbr, Vs, ws, hc, h1, hr, hcol, cs, sn, g, beta, after, live, kd, again, total; };
+// Shared-memory layout of one CTA.  sps = 0: no staged stencil blocks;
+// basis_in_smem = false: the Krylov basis and w chunks are in global memory.
 template <typename Z>
-__host__ __device__ inline CoarseSmem coarse_smem(int nrhs, int maxit, int E, int sps = 0, int nc = 0) {
+__host__ __device__ inline CoarseSmem coarse_smem(int nrhs, int maxit, int E, int sps = 0, int nc = 0,
+                                                  bool basis_in_smem = true) {
     auto up = [](size_t v) { return (v + 15) & ~size_t(15); };
+    const size_t Eb = basis_in_smem ? (size_t)E : 0;
     CoarseSmem L;
     size_t o = 0;
     L.As = o;   o = up(o + sizeof(Z) * (size_t)sps * 9 * nc * nc);
     L.xn = o;   o = up(o + sizeof(Z) * (size_t)nrhs * sps * 9 * nc);
     L.nbr = o;  o = up(o + sizeof(int) * (size_t)sps * 9);
-    L.Vs = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 1) * nrhs * E);
-    L.ws = o;   o = up(o + sizeof(Z) * (size_t)nrhs * E);
+    L.Vs = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 1) * nrhs * Eb);
+    L.ws = o;   o = up(o + sizeof(Z) * (size_t)nrhs * Eb);
     L.hc = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 2) * nrhs);
     L.h1 = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 2) * nrhs);
     L.hr = o;   o = up(o + sizeof(Z) * (size_t)(maxit + 1) * nrhs);
@@ -209,12 +215,14 @@ __global__ void __launch_bounds__(256) coarse_gmres_kernel(CoarseArgs<Z, R> a) {
     cg::grid_group grid = cg::this_grid();
     extern __shared__ __align__(16) unsigned char sraw[];
     const int nrhs = a.nrhs, maxit = a.maxit, E = a.E, nc = a.nc;
-    const CoarseSmem LY = coarse_smem<Z>(nrhs, maxit, E, a.a_smem ? a.sps : 0, a.a_smem ? nc : 0);
+    const bool gbasis = a.Vglob != nullptr;
+    const CoarseSmem LY = coarse_smem<Z>(nrhs, maxit, E, a.a_smem ? a.sps : 0, a.a_smem ? nc : 0, !gbasis);
     Z* As = reinterpret_cast<Z*>(sraw + LY.As);          // [sps][9][col][row] stencil blocks of my sites
     Z* xn = reinterpret_cast<Z*>(sraw + LY.xn);          // [nrhs][sps][9][nc] neighbour vectors
     int* nbr = reinterpret_cast<int*>(sraw + LY.nbr);    // [sps][9] neighbour sites
-    Z* Vs = reinterpret_cast<Z*>(sraw + LY.Vs);          // [(maxit+1)][nrhs][E]
-    Z* ws = reinterpret_cast<Z*>(sraw + LY.ws);          // [nrhs][E]
+    // [(maxit+1)][nrhs][E] basis chunk and [nrhs][E] w chunk of this CTA
+    Z* Vs = gbasis ? a.Vglob + (size_t)blockIdx.x * (maxit + 1) * nrhs * E : reinterpret_cast<Z*>(sraw + LY.Vs);
+    Z* ws = gbasis ? a.wglob + (size_t)blockIdx.x * nrhs * E : reinterpret_cast<Z*>(sraw + LY.ws);
     // the serial per-iteration bookkeeping runs in the working precision R:
     // a dependent chain of FP64 operations is very slow on this part
     Z* hc = reinterpret_cast<Z*>(sraw + LY.hc);          // coefficients of the current pass (+ norms)
@@ -556,15 +564,6 @@ void kry_finish(const KryDev& K, cudaStream_t st) {
     kry_finish_kernel<<<1, 64, 0, st>>>(K);
 }
 
-size_t coarse_gmres_scratch(const Coarse& c, int prec, int nrhs, int maxit, int nct) {
-    const size_t nco = (size_t)c.gc.V * c.nc;
-    const size_t es = prec == QCD_FP64 ? sizeof(double2) : sizeof(float2);
-    const size_t npair = (size_t)(maxit + 2) * nrhs;
-    (void)nct;
-    return es * nco * nrhs * 2 + sizeof(double2) * (4 * npair + (size_t)nrhs * maxit * maxit + (size_t)nrhs * maxit) +
-           4096;
-}
-
 int coarse_gmres_grid() {
     static int nct = 0;
     if (nct == 0) {
@@ -584,34 +583,72 @@ static void coarse_partition(const Coarse& c, int& sps, int& nblk) {
 }
 constexpr size_t kCoarseSmemCap = 200 * 1024;
 
-// Largest right-hand-side group whose basis chunks fit in shared memory.
-int coarse_gmres_group(const Coarse& c, int prec, int maxit) {
+// Where the cooperative kernel keeps its data, in order of preference:
+// stencil blocks and Krylov basis in shared memory (layout 1), basis only
+// (layout 2), basis in global memory (layout 3).  `want` = 0 picks the first
+// that fits; 1..3 forces one (it must fit).
+struct CoarseMode {
+    int layout = 0;       // 1, 2, 3; 0: nothing fits
+    size_t smem = 0;
+};
+static CoarseMode coarse_mode(const Coarse& c, int prec, int nrhs, int maxit, int want) {
     int sps, nblk;
     coarse_partition(c, sps, nblk);
     const int E = sps * c.nc;
-    int best = 0;
-    for (int g = 1; g <= kMaxCoarseRhs; ++g) {
-        size_t sm = prec == QCD_FP64 ? coarse_smem<double2>(g, maxit, E).total : coarse_smem<float2>(g, maxit, E).total;
-        if (sm <= kCoarseSmemCap) best = g;
+    CoarseMode m;
+    for (int layout = 1; layout <= 3; ++layout) {
+        if (want != 0 && layout != want) continue;
+        const int s = layout == 1 ? sps : 0, nc = layout == 1 ? c.nc : 0;
+        const bool smem_basis = layout != 3;
+        const size_t t = prec == QCD_FP64 ? coarse_smem<double2>(nrhs, maxit, E, s, nc, smem_basis).total
+                                          : coarse_smem<float2>(nrhs, maxit, E, s, nc, smem_basis).total;
+        if (t <= kCoarseSmemCap) {
+            m.layout = layout;
+            m.smem = t;
+            return m;
+        }
     }
-    return best;
+    return m;
+}
+
+size_t coarse_gmres_scratch(const Coarse& c, int prec, int nrhs, int maxit, int want_layout) {
+    const size_t nco = (size_t)c.gc.V * c.nc;
+    const size_t es = prec == QCD_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t npair = (size_t)(maxit + 2) * nrhs;
+    size_t bytes = es * nco * nrhs * 2 + sizeof(double2) * (4 * npair + (size_t)nrhs * maxit * maxit + (size_t)nrhs * maxit) +
+                   4096;
+    if (coarse_mode(c, prec, nrhs, maxit, want_layout).layout == 3) {
+        int sps, nblk;
+        coarse_partition(c, sps, nblk);
+        const size_t E = (size_t)sps * c.nc;
+        bytes += es * nblk * E * nrhs * (size_t)(maxit + 2) + 1024;
+    }
+    return bytes;
+}
+
+// Right-hand sides per launch: the library's cap whenever some layout fits
+// (the global-memory basis always does unless the bookkeeping alone is too big).
+int coarse_gmres_group(const Coarse& c, int prec, int maxit, int want_layout) {
+    for (int g = kMaxCoarseRhs; g >= 1; --g)
+        if (coarse_mode(c, prec, g, maxit, want_layout).layout != 0) return g;
+    return 0;
+}
+
+int coarse_gmres_layout(const Coarse& c, int prec, int nrhs, int maxit, int want_layout) {
+    return coarse_mode(c, prec, nrhs, maxit, want_layout).layout;
 }
 
 template <typename Z, typename R>
 static int launch_coarse(const Coarse& c, int op, int nrhs, const void* b, void* x, const double* tau_dev,
                          const int* act, double tol, int maxit, void* scratch, int* iters, double* resid,
-                         unsigned long long* counter, cudaStream_t st) {
+                         unsigned long long* counter, int want_layout, cudaStream_t st) {
     const size_t nco = (size_t)c.gc.V * c.nc;
     int sps, nblk;
     coarse_partition(c, sps, nblk);
     const int E = sps * c.nc;
-    CoarseSmem LY = coarse_smem<Z>(nrhs, maxit, E, sps, c.nc);
-    int a_smem = 1;
-    if (LY.total > kCoarseSmemCap) {
-        a_smem = 0;
-        LY = coarse_smem<Z>(nrhs, maxit, E);
-    }
-    if (LY.total > kCoarseSmemCap) return -4;
+    const CoarseMode md = coarse_mode(c, std::is_same<R, double>::value ? QCD_FP64 : QCD_FP32, nrhs, maxit,
+                                      want_layout);
+    if (md.layout == 0) return -4;
     const size_t npair = (size_t)(maxit + 2) * nrhs;
     char* p = (char*)scratch;
     auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return (void*)q; };
@@ -625,6 +662,12 @@ static int launch_coarse(const Coarse& c, int op, int nrhs, const void* b, void*
     a.tot = (double2*)take(sizeof(double2) * 4 * npair);
     a.Rg = (double2*)take(sizeof(double2) * (size_t)nrhs * maxit * maxit);
     a.yv = (double2*)take(sizeof(double2) * (size_t)nrhs * maxit);
+    a.Vglob = nullptr;
+    a.wglob = nullptr;
+    if (md.layout == 3) {
+        a.Vglob = (Z*)take(sizeof(Z) * (size_t)nblk * (maxit + 1) * nrhs * E);
+        a.wglob = (Z*)take(sizeof(Z) * (size_t)nblk * nrhs * E);
+    }
     a.iters = iters;
     a.counter = counter;
     a.resid = resid;
@@ -636,10 +679,10 @@ static int launch_coarse(const Coarse& c, int op, int nrhs, const void* b, void*
     a.nrhs = nrhs;
     a.E = E;
     a.sps = sps;
-    a.a_smem = a_smem;
+    a.a_smem = md.layout == 1 ? 1 : 0;
     cudaMemsetAsync(a.tot, 0, sizeof(double2) * 4 * npair, st);
     auto kern = coarse_gmres_kernel<Z, R>;
-    const size_t sm = LY.total;
+    const size_t sm = md.smem;
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
@@ -649,19 +692,18 @@ static int launch_coarse(const Coarse& c, int op, int nrhs, const void* b, void*
     KTimer kt(std::is_same<R, double>::value ? "coarse_gmres_f64" : "coarse_gmres_f32",
               es * ((double)c.gc.V * 9 * c.nc * c.nc + 4.0 * nrhs * nco), 0.0, st);
     cudaError_t e = cudaLaunchCooperativeKernel((void*)kern, dim3(nblk), dim3(256), args, sm, st);
-    (void)E;
     return e == cudaSuccess ? 0 : -2;
 }
 
 int coarse_gmres(const Coarse& c, int prec, int op, int nrhs, const void* b, void* x, const double* tau_dev,
                  const int* act, double tol, int maxit, void* scratch, int* iters, double* resid,
-                 unsigned long long* counter, cudaStream_t st) {
+                 unsigned long long* counter, int want_layout, cudaStream_t st) {
     if (nrhs < 1 || nrhs > kMaxCoarseRhs || maxit < 1 || maxit > kMaxCoarse) return -3;
     if (prec == QCD_FP64)
         return launch_coarse<double2, double>(c, op, nrhs, b, x, tau_dev, act, tol, maxit, scratch, iters, resid,
-                                              counter, st);
+                                              counter, want_layout, st);
     return launch_coarse<float2, float>(c, op, nrhs, b, x, tau_dev, act, tol, maxit, scratch, iters, resid, counter,
-                                        st);
+                                        want_layout, st);
 }
 
 }  // namespace qcd

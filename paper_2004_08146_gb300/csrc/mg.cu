@@ -1029,7 +1029,10 @@ void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, vo
                                                                        op, sh, nrhs);
 }
 
+bool sap_needs_scratch(const Blocking& B) { return B.bs != 16 && B.bs != 32; }
+
 size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters) {
+    if (!sap_needs_scratch(sp.B)) return 0;
     size_t per = (size_t)(iters + 1) * sp.B.bs * 12 * (prec == QCD_FP64 ? sizeof(double2) : sizeof(float2));
     int nmax = sp.ncol[0] > sp.ncol[1] ? sp.ncol[0] : sp.ncol[1];
     return per * nmax * nrhs;
@@ -1060,33 +1063,22 @@ void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op
         return;
     }
     if (bs == 32) {
-        const int spw = 32 / bs;
-        dim3 grid((sp.ncol[colour] + spw - 1) / spw, nrhs);
+        // one 32-site block per single-warp CTA
+        dim3 grid(sp.ncol[colour], nrhs);
         if (prec == QCD_FP64) {
-            size_t sm = sap_layout<double>(bs, iters).total * spw;
-            if (bs == 16) {
-                if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                sap_warp_kernel<double, 16><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
-                    sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
-            } else {
-                if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                sap_warp_kernel<double, 32><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
-                    sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
-            }
+            const size_t sm = sap_layout<double>(32, iters).total;
+            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            sap_warp_kernel<double, 32><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
+                sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
         } else {
-            size_t sm = sap_layout<float>(bs, iters).total * spw;
-            if (bs == 16) {
-                if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                sap_warp_kernel<float, 16><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
-                    sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
-            } else {
-                if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                sap_warp_kernel<float, 32><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
-                    sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
-            }
+            const size_t sm = sap_layout<float>(32, iters).total;
+            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            sap_warp_kernel<float, 32><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
+                sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
         }
         return;
     }
+    // every other block size: one thread per block site, Krylov vectors in `scratch`
     dim3 grid(sp.ncol[colour], nrhs);
     size_t sm = sizeof(double2) * ((size_t)bs + (size_t)(iters + 1) * iters + (iters + 1) + 2 * iters) +
                 sizeof(double) * iters + 4 * sizeof(int) +

@@ -57,6 +57,7 @@ class qcd_params(ctypes.Structure):
         ("nv2", ctypes.c_int),
         ("agg2", ctypes.c_int * 4),
         ("nu2", ctypes.c_int),
+        ("coarse_layout", ctypes.c_int),
     ]
 
 
@@ -111,6 +112,7 @@ _SIGS = {
     "qcd_mg_info2": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "qcd_mg_get_P2": (_I, [_P, _DP]),
     "qcd_mg_get_coarse2": (_I, [_P, _DP]),
+    "qcd_projected_eig": (_I, [_P, _I, _DP, _DP, _I, _DP, _DP]),
     "qcd_sap": (_I, [_P, _I, _I, _I, _P, _P, _DP, _I, _D]),
     "qcd_mg_cycle": (_I, [_P, _I, _I, _I, _P, _P, _DP]),
     "qcd_sap_static": (_I, [_P, _I, _I, _I, _P, _P, _DP, _I, _D]),
@@ -306,6 +308,20 @@ class Context:
         out = np.zeros(i["sites"] * 9 * nc * nc, dtype=np.complex128)
         self._check(_lib.qcd_mg_get_coarse2(self.h, out.view(np.float64).ctypes.data_as(_DP)))
         return out.reshape(i["sites"], 9, nc, nc)
+
+    def qcd_projected_eig(self, G, H, extraction=QCD_EXTRACT_HARMONIC):
+        """(theta, S) of the projected eigenproblem (G, H: m x m complex matrices)."""
+        H = np.asfortranarray(np.asarray(H, dtype=np.complex128))
+        m = H.shape[0]
+        Gf = None if G is None else np.asfortranarray(np.asarray(G, dtype=np.complex128))
+        theta = np.zeros(m, dtype=np.float64)
+        Gflat = None if Gf is None else np.ascontiguousarray(Gf.reshape(-1, order='F'))
+        gp = None if Gflat is None else Gflat.view(np.float64).ctypes.data_as(_DP)
+        Hflat = np.ascontiguousarray(H.reshape(-1, order='F'))
+        Sflat = np.zeros(m * m, dtype=np.complex128)
+        self._check(_lib.qcd_projected_eig(self.h, m, gp, Hflat.view(np.float64).ctypes.data_as(_DP), int(extraction),
+                                           theta.ctypes.data_as(_DP), Sflat.view(np.float64).ctypes.data_as(_DP)))
+        return theta, Sflat.reshape(m, m, order='F')
 
     def qcd_sap(self, op, prec, nrhs, b, x, tau, sweeps, block_tol):
         t, tp = _dbl(tau)

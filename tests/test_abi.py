@@ -77,16 +77,26 @@ def test_calls_without_gauge_fail_cleanly():
     ctx.close()
 
 
-@pytest.mark.parametrize("bad", [dict(extraction=2), dict(update_every=-1), dict(block=0),
-                                 dict(m_max=60, block=8), dict(sap_block_iters=0), dict(levels=4),
-                                 dict(levels=1), dict(nv2=0), dict(nv2=33), dict(agg2=(2, 0, 2, 2)),
-                                 dict(nu2=-1)])
+@pytest.mark.parametrize("bad", [dict(extraction=2), dict(update_every=-1), dict(block=0), dict(block=33),
+                                 dict(m_max=106, block=8), dict(m_max=112), dict(sap_block_iters=0),
+                                 dict(levels=4), dict(levels=1), dict(nv2=0), dict(nv2=33),
+                                 dict(agg2=(2, 0, 2, 2)), dict(nu2=-1), dict(coarse_layout=4),
+                                 dict(coarse_layout=-1)])
 def test_create_rejects_each_bad_field(bad):
     """Parameter validation happens in qcd_create, on the host, before any GPU work."""
     from paper_2004_08146_gb300 import qcd
     with pytest.raises(qcd.QcdError) as e:
         qcd.Context(params=qcd.default_params(**bad))
     assert e.value.code == qcd.QCD_EINVAL
+
+
+def test_basis_cap_accepts_the_large_workloads():
+    """m_max 50 (Table 2) with 16 or 32 targets per iteration fits the basis
+    cap of 112 (m_max + block <= 112)."""
+    from paper_2004_08146_gb300 import qcd
+    for block in (16, 32):
+        qcd.Context(params=qcd.default_params(m_max=50, block=block)).close()
+    qcd.Context(params=qcd.default_params(m_max=80, block=32)).close()
 
 
 def test_default_params_method_variants():

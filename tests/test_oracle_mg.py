@@ -365,3 +365,17 @@ def test_three_level_solve_matches_dense():
     x, it = h.solve(b, 0.05, tol=1e-12, maxiter=200)
     xd = np.linalg.solve(op.dense('Dg5', 0.05), b.reshape(-1))
     assert np.linalg.norm(x.reshape(-1) - xd) < 1e-10 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("dims,block", [((4, 4, 4, 4), (2, 2, 2, 2)), ((8, 4, 2, 6), (4, 1, 2, 3)),
+                                        ((6, 4, 4, 2), (3, 4, 1, 2))])
+def test_blocking_gather_scatter_is_the_site_map(dims, block):
+    """Blocking.gather / scatter (reshape form used by the restriction and
+    prolongation) equal the explicit site map sites[b, l]."""
+    blk = mg.Blocking(dims, block)
+    f = synth.spinor(dims, 7)
+    assert np.array_equal(blk.gather(f, (4, 3)), f.reshape(-1, 4, 3)[blk.sites])
+    fb = synth.complex_gaussian((blk.nblocks, blk.bsites, 4, 3), 8)
+    out = np.zeros((int(np.prod(dims)), 4, 3), dtype=np.complex128)
+    out[blk.sites.reshape(-1)] = fb.reshape(-1, 4, 3)
+    assert np.array_equal(blk.scatter(fb, (4, 3)), out.reshape(dims + (4, 3)))
