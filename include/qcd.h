@@ -255,6 +255,22 @@ int qcd_eig_derivative(qcd_ctx* ctx, const double* X, int nvec, const void* V, d
  * nvec = 0 does nothing.  A zero vector gives a zero force. */
 int qcd_eig_force(qcd_ctx* ctx, int nvec, const void* V, void* F);
 
+/* Link gradient of a real bilinear form (no counterpart in the paper; the
+ * backward pass of psi -> (Q - tau) psi with respect to the links, for
+ * autograd): for each k < nvec, F[k] = the traceless Hermitian 3x3 fields
+ * F_mu(x) with d/d eps Re <g_k, Q(U(eps)) psi_k> = sum_{x,mu} tr(X_mu(x)
+ * F_mu(x)) for links moving as U -> exp(i eps X) U (X traceless Hermitian);
+ * grad = 1 returns instead the tangent vectors i F_mu(x) U_mu(x), whose real
+ * inner product Re tr(G^H dU) with any such dU = i X U is that derivative.
+ * Hop terms: the two forward outer products of psi and Gamma5 g (Q' is
+ * Hermitian); clover term: plaquettes above and below each link with the
+ * insertion of sigma psi (Gamma5 g)^H at each corner.  G, Psi: DEVICE
+ * complex128 [nvec][V*12]; F: DEVICE complex128 [nvec][site][mu][3][3],
+ * caller-owned and overwritten; all 16-byte aligned.  FP64.  Errors:
+ * ENOTSETUP before qcd_set_gauge; EINVAL for nvec < 0, NULL or misaligned
+ * pointers, grad not 0 or 1; nvec = 0 does nothing. */
+int qcd_bilinear_force(qcd_ctx* ctx, int nvec, const void* G, const void* Psi, int grad, void* F);
+
 /* Local coherence lc(v) = ||Pi v|| / ||v|| (Sec. 3, the local coherence
  * measure) of nvec FP64 fine vectors V (DEVICE, complex128 [nvec][V*12],
  * 16-byte aligned) with respect to the current interpolation P; Pi = P P^H is
@@ -336,6 +352,22 @@ typedef struct qcd_kernel_stat {
 
 int qcd_stats_reset(int mode, const char* filter);
 int qcd_stats_read(qcd_kernel_stat* out, int max, int* n);
+
+/* Work of the SAP block solves (Eq. 2.10, block GMRES) since the last
+ * qcd_stats_reset, summed over every block solve of every launch:
+ * *site_steps = sum (block sites x GMRES steps k), *site_steps_tri =
+ * sum (block sites x k (k + 1) / 2); a flop model of one block solve
+ * (operator applies plus Gram-Schmidt) turns them into the flops actually
+ * executed.  Waits for nothing: read after synchronising.  EINVAL on NULL. */
+int qcd_stats_sap_work(double* site_steps, double* site_steps_tri);
+
+/* Measured fused multiply-add throughput of the current device in TFLOP/s
+ * (2 flops per FMA) for prec QCD_FP32 or QCD_FP64: a kernel of independent
+ * FMA chains on every SM, best of five timed launches on the default stream
+ * (the roofline denominator of FP32- and FP64-ALU-bound kernels; the SM
+ * clock at the time of the call sets the value).  EINVAL on a bad prec or
+ * NULL; ECUDA when the launch fails. */
+int qcd_fma_peak(int prec, double* tflops);
 
 #ifdef __cplusplus
 }

@@ -394,3 +394,63 @@ def eigenvalue_force(op, v):
                          + dp @ ap @ C2 @ bp + dp @ ap @ bp @ C3) @ _dag(Ur)
                 K[..., rho, :, :] += c * below - c * above
     return _traceless_hermitian(K) / float(np.real(np.vdot(v, v)))
+
+
+def bilinear_force(op, g, psi):
+    """Per-link force of the real bilinear form Re <g, Q psi> (the link
+    gradient of a real loss through psi -> Q psi with cotangent g): F_mu(x)
+    (dims + (4, 3, 3)), traceless Hermitian, such that
+    d/d eps Re <g, Q(U(eps)) psi> = sum tr(X_mu(x) F_mu(x)) for links moving
+    as exp(i eps X) U.  Restates ``eigenvalue_force`` for two vectors:
+
+    * hop terms: Q' is Hermitian, so the backward hop of <g, Q' psi> is the
+      complex conjugate of the forward hop of <psi, Q' g>; the real part is
+      the sum of the real parts of the two forward terms, and the force is
+      -i U (A(psi, g) + A(g, psi)) / 2 with A(a, b) = sum_{st}
+      (I - gamma_mu)_{st} a_t(x + mu) (Gamma5 b)_s(x)^H;
+    * clover term: as in ``eigenvalue_force`` with B = sum_{st} sigma_st
+      psi_t(x) (Gamma5 g)_s(x)^H (the real part of the derivative again needs
+      only Bt = B + B^H).
+
+    For g = psi = v this is v^H v times ``eigenvalue_force(op, v)``."""
+    g = np.asarray(g).reshape(op.dims + (4, 3))
+    psi = np.asarray(psi).reshape(op.dims + (4, 3))
+    wg = np.conj(WilsonClover.g5(g))
+    wp = np.conj(WilsonClover.g5(psi))
+    U = op.U
+    S = shift_field
+    K = np.zeros(op.dims + (4, 3, 3), dtype=np.complex128)
+    I4 = np.eye(4, dtype=np.complex128)
+    for rho in range(4):
+        nb_p = hop_spinor(psi, rho, +1, op.antiperiodic_t)
+        nb_g = hop_spinor(g, rho, +1, op.antiperiodic_t)
+        A = (np.einsum('st,...ta,...sb->...ab', I4 - GAMMA[rho], nb_p, wg)
+             + np.einsum('st,...ta,...sb->...ab', I4 - GAMMA[rho], nb_g, wp))
+        K[..., rho, :, :] -= 0.5j * (U[..., rho, :, :] @ A)
+    if op.csw != 0.0:
+        c = op.csw / 16.0
+        for rho in range(4):
+            for nu in range(4):
+                if nu == rho:
+                    continue
+                B = np.einsum('st,...ta,...sb->...ab', sigma_munu(rho, nu), psi, wg)
+                Bt = B + _dag(B)
+                Ur = U[..., rho, :, :]
+                Un = U[..., nu, :, :]
+                a = Ur
+                b = S(Un, rho, +1)
+                cc = _dag(S(Ur, nu, +1))
+                d = _dag(Un)
+                B0, B1 = Bt, S(Bt, rho, +1)
+                B2, B3 = S(S(Bt, rho, +1), nu, +1), S(Bt, nu, +1)
+                above = (a @ b @ cc @ d @ B0 + a @ B1 @ b @ cc @ d
+                         + a @ b @ B2 @ cc @ d + a @ b @ cc @ B3 @ d)
+                dp = _dag(S(Un, nu, -1))
+                ap = S(Ur, nu, -1)
+                bp = S(S(Un, rho, +1), nu, -1)
+                C0, C1 = Bt, S(Bt, nu, -1)
+                C2, C3 = S(S(Bt, nu, -1), rho, +1), S(Bt, rho, +1)
+                below = (C0 @ dp @ ap @ bp + dp @ C1 @ ap @ bp
+                         + dp @ ap @ C2 @ bp + dp @ ap @ bp @ C3) @ _dag(Ur)
+                K[..., rho, :, :] += c * below - c * above
+    return _traceless_hermitian(K)

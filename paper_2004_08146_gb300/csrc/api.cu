@@ -689,7 +689,10 @@ void build_level2(qcd_ctx* ctx, const double2* V, int nvec) {
         CK(cudaMalloc(&c2.A32, na * sizeof(float2)));
         ctx->c2_nv1 = c.nv;
     }
-    ensure_coarse64(ctx);
+    // an FP64 context builds level 2 from the FP64 level-1 operator; a
+    // mixed-precision one from the FP32 operator its cycles use (no FP64
+    // Galerkin rebuild per interpolation update)
+    if (ctx->p.precision == QCD_FP64) ensure_coarse64(ctx);
     const size_t nco = (size_t)c.gc.V * c.nc;
     double2* W2 = (double2*)ctx->buf("l2.W", (size_t)nv2 * nco * sizeof(double2));
     mg_restrict(ctx->f, c, QCD_FP64, nv2, V, W2, ctx->st);
@@ -1695,6 +1698,26 @@ int qcd_eig_force(qcd_ctx* ctx, int nvec, const void* V, void* F) {
             eig_force(f, v, nrm, Bt, (double2*)F + (size_t)j * nl, ctx->st);
         }
         check_launch("eig force");
+        return QCD_OK;
+    });
+}
+
+int qcd_bilinear_force(qcd_ctx* ctx, int nvec, const void* G, const void* Psi, int grad, void* F) {
+    return guarded(ctx, [&]() {
+        require_gauge(ctx);
+        if (nvec < 0 || (nvec > 0 && (!G || !Psi || !F)) || (grad != 0 && grad != 1))
+            throw QcdError(QCD_EINVAL, "bad arguments");
+        if (nvec == 0) return QCD_OK;
+        check_align(G, "G");
+        check_align(Psi, "Psi");
+        check_align(F, "F");
+        const FineOp& f = ctx->f;
+        const size_t n = ctx->nfine(), nl = (size_t)f.g.V * 36;
+        double2* Bt = (double2*)ctx->buf("force.Bt", (size_t)f.g.V * 54 * sizeof(double2));
+        for (int j = 0; j < nvec; ++j)
+            bilinear_force(f, (const double2*)G + (size_t)j * n, (const double2*)Psi + (size_t)j * n, nullptr, grad, Bt,
+                           (double2*)F + (size_t)j * nl, ctx->st);
+        check_launch("bilinear force");
         return QCD_OK;
     });
 }

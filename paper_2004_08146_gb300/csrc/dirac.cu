@@ -220,13 +220,18 @@ __device__ __forceinline__ int plane_index(int mu, int nu) {   // mu < nu
     return mu == 0 ? nu - 1 : (mu == 1 ? nu + 1 : 5);
 }
 
-// Bt_{mu nu}(x) for the six planes mu < nu: [site][plane][3][3].  sigma is
-// block diagonal in chirality and w = +v (spins 0, 1), -v (spins 2, 3).
-__global__ void clover_insertion_kernel(const double2* __restrict__ v, Geom g, double2* __restrict__ Bt) {
+// Bt_{mu nu}(x) = B + B^H for the six planes mu < nu: [site][plane][3][3],
+// B = sum_{st} sigma_st psi_t(x) (Gamma5 gv)_s(x)^H.  sigma is block diagonal
+// in chirality and Gamma5 gv = +gv (spins 0, 1), -gv (spins 2, 3).
+__global__ void clover_insertion_kernel(const double2* __restrict__ psi, const double2* __restrict__ gv, Geom g,
+                                        double2* __restrict__ Bt) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.V) return;
-    double2 p[12];
-    for (int k = 0; k < 12; ++k) p[k] = v[(size_t)s * 12 + k];
+    double2 p[12], q[12];
+    for (int k = 0; k < 12; ++k) {
+        p[k] = psi[(size_t)s * 12 + k];
+        q[k] = gv[(size_t)s * 12 + k];
+    }
     for (int mu = 0; mu < 4; ++mu)
         for (int nu = mu + 1; nu < 4; ++nu) {
             double2 B[3][3];
@@ -238,7 +243,7 @@ __global__ void clover_insertion_kernel(const double2* __restrict__ v, Geom g, d
                 for (int i = 0; i < 2; ++i) for (int j = 0; j < 2; ++j) {
                     const double2 c = sg * S[i][j];
                     for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b)
-                        B[a][b] += c * (p[(2 * chi + j) * 3 + a] * conj(p[(2 * chi + i) * 3 + b]));
+                        B[a][b] += c * (p[(2 * chi + j) * 3 + a] * conj(q[(2 * chi + i) * 3 + b]));
                 }
             }
             double2* o = Bt + ((size_t)s * 6 + plane_index(mu, nu)) * 9;
@@ -252,10 +257,36 @@ __device__ __forceinline__ M3<double> m3_add(const M3<double>& x, const M3<doubl
     return r;
 }
 
-// One thread per link (site, rho).  nrm: device v^H v (real part used).
-__global__ void __launch_bounds__(128) link_force_kernel(const double2* __restrict__ U, const double2* __restrict__ v,
-                                                         const double2* __restrict__ Bt, const double2* __restrict__ nrm,
-                                                         Geom g, double csw, double2* __restrict__ F) {
+// Forward-hop colour outer product A(a, b) = sum_{st} (I - gamma_rho)_{st}
+// a_t(x + rho) (Gamma5 b)_s(x)^H: h = up - B dn of the projected neighbour,
+// lower half -B^H h; A = sum_i h_i b_i^H + (B^H h)_i b_{2+i}^H (Gamma5 b
+// flips the lower sign).  sg: boundary phase of the hop.
+__device__ __forceinline__ M3<double> hop_outer(const double2* __restrict__ an, const double2* __restrict__ bs,
+                                                int rho, double sg) {
+    const SpinMono Bm = kB(rho), BHm = kBH(rho);
+    double2 h[2][3], q[2][3];
+    for (int i = 0; i < 2; ++i) for (int a = 0; a < 3; ++a)
+        h[i][a] = sg * (an[i * 3 + a] - mul_ipow(an[(2 + Bm.perm[i]) * 3 + a], Bm.ph[i]));
+    for (int i = 0; i < 2; ++i) for (int a = 0; a < 3; ++a) q[i][a] = mul_ipow(h[BHm.perm[i]][a], BHm.ph[i]);
+    M3<double> A;
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+        double2 t = make_double2(0, 0);
+        for (int i = 0; i < 2; ++i) t += h[i][a] * conj(bs[i * 3 + b]) + q[i][a] * conj(bs[(2 + i) * 3 + b]);
+        A.e[a][b] = t;
+    }
+    return A;
+}
+
+// One thread per link (site, rho): the force of Re <gv, Q' psi> (for
+// psi = gv = v the eigenvalue force times v^H v).  Hop terms: Q' is
+// Hermitian, so the real part is carried by the two forward terms
+// -i/2 U (A(psi, gv) + A(gv, psi)); clover term through the insertions Bt.
+// nrm: device v^H v dividing the result, or null.  grad = 1 writes the link
+// gradient i F U instead of F.
+__global__ void __launch_bounds__(128) link_force_kernel(const double2* __restrict__ U, const double2* __restrict__ psi,
+                                                         const double2* __restrict__ gv, const double2* __restrict__ Bt,
+                                                         const double2* __restrict__ nrm, Geom g, double csw, int grad,
+                                                         double2* __restrict__ F) {
     const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (e >= (size_t)g.V * 4) return;
     const int s = (int)(e >> 2), rho = (int)(e & 3);
@@ -265,23 +296,13 @@ __global__ void __launch_bounds__(128) link_force_kernel(const double2* __restri
     const M3<double> u = L(s, rho);
     M3<double> K;
     {
-        // hop: h = up - B dn of the projected neighbour, lower half -B^H h;
-        // A = sum_i h_i v_i^H + (B^H h)_i v_{2+i}^H (w = Gamma5 v flips the lower sign)
         int neg;
         const int sf = nb_fwd(g, x, s, rho, neg);
         const double sg = neg ? -1.0 : 1.0;
-        const SpinMono Bm = kB(rho), BHm = kBH(rho);
-        double2 h[2][3], q[2][3];
-        for (int i = 0; i < 2; ++i) for (int a = 0; a < 3; ++a)
-            h[i][a] = sg * (v[(size_t)sf * 12 + i * 3 + a] -
-                            mul_ipow(v[(size_t)sf * 12 + (2 + Bm.perm[i]) * 3 + a], Bm.ph[i]));
-        for (int i = 0; i < 2; ++i) for (int a = 0; a < 3; ++a) q[i][a] = mul_ipow(h[BHm.perm[i]][a], BHm.ph[i]);
-        M3<double> A;
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
-            double2 t = make_double2(0, 0);
-            for (int i = 0; i < 2; ++i)
-                t += h[i][a] * conj(v[(size_t)s * 12 + i * 3 + b]) + q[i][a] * conj(v[(size_t)s * 12 + (2 + i) * 3 + b]);
-            A.e[a][b] = t;
+        M3<double> A = hop_outer(psi + (size_t)sf * 12, gv + (size_t)s * 12, rho, sg);
+        if (psi != gv) {
+            const M3<double> A2 = hop_outer(gv + (size_t)sf * 12, psi + (size_t)s * 12, rho, sg);
+            for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) A.e[a][b] = 0.5 * (A.e[a][b] + A2.e[a][b]);
         }
         const M3<double> UA = m3_mul(u, A);
         for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) K.e[a][b] = mul_ipow(UA.e[a][b], 3);   // -i U A
@@ -322,23 +343,42 @@ __global__ void __launch_bounds__(128) link_force_kernel(const double2* __restri
                 K.e[a][b] += sg * (below.e[a][b] - above.e[a][b]);
         }
     }
-    const double n = nrm[0].x;
-    const double inv = n > 0 ? 1.0 / n : 0.0;
+    double inv = 1.0;
+    if (nrm != nullptr) {
+        const double n = nrm[0].x;
+        inv = n > 0 ? 1.0 / n : 0.0;
+    }
     double2 H[3][3];
     for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) H[a][b] = 0.5 * (K.e[a][b] + conj(K.e[b][a]));
     const double tr = (H[0][0].x + H[1][1].x + H[2][2].x) / 3.0;
     for (int a = 0; a < 3; ++a) H[a][a].x -= tr;
-    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) F[e * 9 + a * 3 + b] = inv * H[a][b];
+    if (!grad) {
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) F[e * 9 + a * 3 + b] = inv * H[a][b];
+        return;
+    }
+    // link gradient i F U: the tangent vector whose real inner product with
+    // any dU = i X U is tr(X F)
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double2 t = make_double2(0, 0);
+            for (int c = 0; c < 3; ++c) t += H[a][c] * u.e[c][b];
+            F[e * 9 + a * 3 + b] = inv * mul_ipow(t, 1);
+        }
 }
 
 void eig_force(const FineOp& f, const double2* v, const double2* nrm, double2* Bt, double2* F, cudaStream_t st) {
+    bilinear_force(f, v, v, nrm, 0, Bt, F, st);
+}
+
+void bilinear_force(const FineOp& f, const double2* gv, const double2* psi, const double2* nrm, int grad, double2* Bt,
+                    double2* F, cudaStream_t st) {
     {
         KTimer kt("clover_insertion", 0.0, 0.0, st);
-        clover_insertion_kernel<<<(f.g.V + 127) / 128, 128, 0, st>>>(v, f.g, Bt);
+        clover_insertion_kernel<<<(f.g.V + 127) / 128, 128, 0, st>>>(psi, gv, f.g, Bt);
     }
     KTimer kt("link_force", 0.0, 0.0, st);
     const size_t nl = (size_t)f.g.V * 4;
-    link_force_kernel<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(f.U64, v, Bt, nrm, f.g, f.csw, F);
+    link_force_kernel<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(f.U64, psi, gv, Bt, nrm, f.g, f.csw, grad, F);
 }
 
 // ------------------------------------------------------------------ stencil

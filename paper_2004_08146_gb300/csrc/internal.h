@@ -104,6 +104,10 @@ void apply_tangent(const FineOp& f, const double2* dU, const double* dA, int nrh
 // Per-link force of the eigenvalue v^H Q v / v^H v: insertion fields Bt
 // ([V][6][9]) then F ([V][4][9], traceless Hermitian); nrm: device v^H v.
 void eig_force(const FineOp& f, const double2* v, const double2* nrm, double2* Bt, double2* F, cudaStream_t st);
+// Force of Re <gv, Q' psi> per link (F [V][4][9], traceless Hermitian), or
+// with grad = 1 the link gradient i F U; nrm (device, may be null) divides.
+void bilinear_force(const FineOp& f, const double2* gv, const double2* psi, const double2* nrm, int grad, double2* Bt,
+                    double2* F, cudaStream_t st);
 void apply_op(const FineOp& f, int prec, int op, int nrhs, const void* in, void* out,
               const double* tau, cudaStream_t st, const int* act = nullptr);
 void residual_op(const FineOp& f, int prec, int op, int nrhs, const void* b, const void* x, void* r,
@@ -168,6 +172,12 @@ void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op
 // basis in shared memory (0 bytes); every other block size needs
 // (iters + 1) block vectors per block of the larger colour and per rhs.
 bool sap_needs_scratch(const Blocking& B);
+// SAP work counters (device-wide; see qcd_stats_sap_work): reset / read
+// [sum bs k, sum bs k (k + 1) / 2] over the block solves since the reset.
+void sap_work_reset();
+void sap_work_read(double out[2]);
+// FP32 / FP64 fused multiply-add throughput of the current device (TFLOP/s)
+double fma_peak_tflops(int prec, cudaStream_t st);
 size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters);
 
 // ------------------------------------------------------------------ kernels (krylov.cu)

@@ -8,6 +8,17 @@ namespace qcd {
 
 namespace {
 
+// Work counters of the SAP block solves (for the FP32-ALU roofline): [0] sums
+// block sites x GMRES steps, [1] block sites x k (k + 1) / 2 over all block
+// solves; 64 slots per counter spread the atomics of one launch.
+__device__ unsigned long long g_sap_work[2][64];
+
+__device__ __forceinline__ void count_sap_work(int bs, int kdim) {
+    const int slot = (blockIdx.x + 7 * blockIdx.y) & 63;
+    atomicAdd(&g_sap_work[0][slot], (unsigned long long)bs * kdim);
+    atomicAdd(&g_sap_work[1][slot], (unsigned long long)bs * kdim * (kdim + 1) / 2);
+}
+
 // sum of a double2 over the first blockDim.x (power of two) threads
 __device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
     const int t = threadIdx.x;
@@ -265,36 +276,73 @@ __global__ void narrow_kernel(const double2* __restrict__ a, float2* __restrict_
 }
 
 // ------------------------------------------------------------------ coarse apply
+// Multi-right-hand-side coarse stencil: one CTA per (coarse site, chunk of
+// up to kCoarseRC right-hand sides).  The 9 neighbour vectors of the chunk
+// are staged in shared memory ([d][col][rhs]); every stencil block entry is
+// then loaded once per chunk (coalesced: consecutive threads take consecutive
+// rows of the column-major blocks) and multiplied into kCoarseRPT
+// right-hand sides held in registers, so the (2 Nv)^2 x 9 blocks -- the bulk
+// of the bytes -- are read once per chunk instead of once per right-hand side.
+constexpr int kCoarseRC = 16;
+constexpr int kCoarseRPT = 4;
 template <typename Z, typename R>
-__global__ void coarse_apply_kernel(Geom gc, int nc, const Z* __restrict__ A, const Z* __restrict__ x, Z* __restrict__ y,
-                                    int op, Shifts tau, int nrhs) {
-    const long total = (long)nrhs * gc.V * nc;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int j = (int)(t / ((long)gc.V * nc));
-        const int rem = (int)(t - (long)j * gc.V * nc);
-        const int s = rem / nc, r = rem % nc;
+__global__ void coarse_apply_mrhs_kernel(Geom gc, int nc, const Z* __restrict__ A, const Z* __restrict__ x,
+                                         Z* __restrict__ y, int op, Shifts tau, int nrhs, int rc) {
+    extern __shared__ __align__(16) unsigned char craw[];
+    Z* xs = reinterpret_cast<Z*>(craw);                 // [9][nc][rc]
+    __shared__ int nbr[9];
+    const int s = blockIdx.x;
+    const int j0 = blockIdx.y * rc;
+    const size_t vstride = (size_t)gc.V * nc;
+    if (threadIdx.x < 9) {
+        const int d = threadIdx.x;
         int c[4];
         site_coords(gc, s, c);
-        const Z* xj = x + (size_t)j * gc.V * nc;
-        Z acc; acc.x = 0; acc.y = 0;
-        for (int d = 0; d < 9; ++d) {
-            int sn = s;
-            if (d > 0) {
-                int mu = (d - 1) & 3, step = d <= 4 ? 1 : -1;
-                int cn[4] = {c[0], c[1], c[2], c[3]};
-                cn[mu] = (cn[mu] + step + gc.L[mu]) % gc.L[mu];
-                sn = site_index(gc, cn);
-            }
-            const Z* a = A + (((size_t)s * 9 + d) * nc) * nc + r;
-            const Z* xs = xj + (size_t)sn * nc;
-            for (int col = 0; col < nc; ++col) acc += a[(size_t)col * nc] * xs[col];
+        int sn = s;
+        if (d > 0) {
+            const int mu = (d - 1) & 3, step = d <= 4 ? 1 : -1;
+            c[mu] = (c[mu] + step + gc.L[mu]) % gc.L[mu];
+            sn = site_index(gc, c);
         }
-        const R sg = r < nc / 2 ? R(1) : R(-1);
+        nbr[d] = sn;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 9 * nc * rc; e += blockDim.x) {
+        const int col = e % nc, jj = (e / nc) % rc, d = e / (nc * rc);
+        const int j = j0 + jj;
+        Z v; v.x = 0; v.y = 0;
+        if (j < nrhs) v = x[(size_t)j * vstride + (size_t)nbr[d] * nc + col];
+        xs[((size_t)d * nc + col) * rc + jj] = v;
+    }
+    __syncthreads();
+    const int r = threadIdx.x % nc, grp = threadIdx.x / nc;
+    if (grp * kCoarseRPT >= rc) return;
+    Z acc[kCoarseRPT];
+#pragma unroll
+    for (int k = 0; k < kCoarseRPT; ++k) { acc[k].x = 0; acc[k].y = 0; }
+    const Z* As = A + (size_t)s * 9 * nc * nc + r;
+    for (int d = 0; d < 9; ++d) {
+        const Z* Ad = As + (size_t)d * nc * nc;
+        const Z* xd = xs + (size_t)d * nc * rc + grp * kCoarseRPT;
+#pragma unroll 4
+        for (int col = 0; col < nc; ++col) {
+            const Z a = __ldg(Ad + (size_t)col * nc);
+            const Z* xv = xd + (size_t)col * rc;
+#pragma unroll
+            for (int k = 0; k < kCoarseRPT; ++k) acc[k] += a * xv[k];
+        }
+    }
+    const R sg = r < nc / 2 ? R(1) : R(-1);
+#pragma unroll
+    for (int k = 0; k < kCoarseRPT; ++k) {
+        const int jj = grp * kCoarseRPT + k, j = j0 + jj;
+        if (j >= nrhs) break;
         const R tj = (R)tau.t[j];
-        Z xv = xj[(size_t)s * nc + r];
-        if (op == QCD_OP_D) { acc -= (tj * sg) * xv; }
-        else { acc = sg * acc; acc -= tj * xv; }
-        y[(size_t)j * gc.V * nc + (size_t)s * nc + r] = acc;
+        const Z xv = xs[(size_t)r * rc + jj];        // direction 0 is the site itself
+        Z o = acc[k];
+        if (op == QCD_OP_D) { o -= (tj * sg) * xv; }
+        else { o = sg * o; o -= tj * xv; }
+        y[(size_t)j * vstride + (size_t)s * nc + r] = o;
     }
 }
 
@@ -463,6 +511,7 @@ __global__ void sap_block_kernel(Geom g, Blocking B, const cplx<R>* __restrict__
         if (flag[0]) break;
     }
     if (l == 0) {
+        count_sap_work(bs, kdim);
         for (int i = kdim - 1; i >= 0; --i) {
             double2 s = gv[i];
             for (int k = i + 1; k < kdim; ++k) s -= H[i * iters + k] * yv[k];
@@ -696,6 +745,7 @@ __global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const 
     }
     const int kdim = flag[1];
     if (l == 0) {
+        if (valid) count_sap_work(BS, kdim);
         for (int i = kdim - 1; i >= 0; --i) {
             cplx<R> sacc = gv[i];
             for (int k = i + 1; k < kdim; ++k) sacc -= H[i * iters + k] * yv[k];
@@ -918,6 +968,7 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
     }
     const int kdim = flag[1];
     if (lane == 0) {
+        count_sap_work(BS, kdim);
         for (int i = kdim - 1; i >= 0; --i) {
             cplx<R> sacc = gv[i];
             for (int k = i + 1; k < kdim; ++k) sacc -= H[i * iters + k] * yv[k];
@@ -1019,17 +1070,46 @@ void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, vo
     size_t n = (size_t)nrhs * c.gc.V * c.nc;
     const double es = prec == QCD_FP64 ? 16.0 : 8.0;
     KTimer kt(prec == QCD_FP64 ? "coarse_apply_f64" : "coarse_apply_f32",
-              es * ((double)c.gc.V * 9 * c.nc * c.nc + 2.0 * nrhs * c.gc.V * c.nc),
+              es * ((double)c.gc.V * 9 * c.nc * c.nc * ((nrhs + kCoarseRC - 1) / kCoarseRC) +
+                    2.0 * nrhs * c.gc.V * c.nc),
               8.0 * 9 * c.nc * c.nc * (double)c.gc.V * nrhs, st);
-    if (prec == QCD_FP64)
-        coarse_apply_kernel<double2, double><<<grid_for(n), 256, 0, st>>>(c.gc, c.nc, c.A64, (const double2*)x,
-                                                                         (double2*)y, op, sh, nrhs);
-    else
-        coarse_apply_kernel<float2, float><<<grid_for(n), 256, 0, st>>>(c.gc, c.nc, c.A32, (const float2*)x, (float2*)y,
-                                                                       op, sh, nrhs);
+    (void)n;
+    // right-hand sides per CTA: a multiple of kCoarseRPT, at most kCoarseRC
+    const int rc = std::min(kCoarseRC, (nrhs + kCoarseRPT - 1) / kCoarseRPT * kCoarseRPT);
+    const dim3 grid(c.gc.V, (nrhs + rc - 1) / rc);
+    const int threads = c.nc * (rc / kCoarseRPT);
+    const size_t ebytes = prec == QCD_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t sm = (size_t)9 * c.nc * rc * ebytes;
+    if (prec == QCD_FP64) {
+        if (sm > 48 * 1024)
+            cudaFuncSetAttribute(coarse_apply_mrhs_kernel<double2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
+        coarse_apply_mrhs_kernel<double2, double><<<grid, threads, sm, st>>>(c.gc, c.nc, c.A64, (const double2*)x,
+                                                                            (double2*)y, op, sh, nrhs, rc);
+    } else {
+        if (sm > 48 * 1024)
+            cudaFuncSetAttribute(coarse_apply_mrhs_kernel<float2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
+        coarse_apply_mrhs_kernel<float2, float><<<grid, threads, sm, st>>>(c.gc, c.nc, c.A32, (const float2*)x,
+                                                                          (float2*)y, op, sh, nrhs, rc);
+    }
 }
 
 bool sap_needs_scratch(const Blocking& B) { return B.bs != 16 && B.bs != 32; }
+
+void sap_work_reset() {
+    static const unsigned long long zero[2][64] = {};
+    cudaMemcpyToSymbol(g_sap_work, zero, sizeof(zero));
+}
+void sap_work_read(double out[2]) {
+    unsigned long long h[2][64];
+    cudaMemcpyFromSymbol(h, g_sap_work, sizeof(h));
+    out[0] = out[1] = 0.0;
+    for (int i = 0; i < 64; ++i) {
+        out[0] += (double)h[0][i];
+        out[1] += (double)h[1][i];
+    }
+}
 
 size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters) {
     if (!sap_needs_scratch(sp.B)) return 0;

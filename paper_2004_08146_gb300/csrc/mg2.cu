@@ -142,9 +142,12 @@ __global__ void prolong2_kernel(Geom g1, Blocking B2, int nv1, int nv2, const Z*
 // through the nine terms of the level-1 stencil from every level-1 site x of
 // aggregate b2; a term that reads across the face of the aggregate in a
 // direction with level-2 extent > 1 goes to that level-2 direction, every
-// other term to the self term; each piece is restricted with P2_b2^H.  FP64.
+// other term to the self term; each piece is restricted with P2_b2^H.  FP64
+// arithmetic; the level-1 stencil is read in FP64, or in FP32 when only the
+// FP32 operator of a mixed-precision hierarchy is current.
+template <typename Z1>
 __global__ void __launch_bounds__(kC2Threads) build_coarse2_kernel(Geom g1, Blocking B2, int nv1, int nv2,
-                                                                   const double2* __restrict__ A1,
+                                                                   const Z1* __restrict__ A1,
                                                                    const double2* __restrict__ P2,
                                                                    double2* __restrict__ A2) {
     __shared__ double2 sv[32];
@@ -181,9 +184,9 @@ __global__ void __launch_bounds__(kC2Threads) build_coarse2_kernel(Geom g1, Bloc
             if (t < nv1) sv[t] = P2[(((size_t)b2y * 2 + chic) * nv2 + jc) * nloc + (size_t)ly * nv1 + t];
             __syncthreads();
             if (t < nc1) {
-                const double2* a = A1 + ((size_t)x * 9 + d1) * nc1 * nc1 + (size_t)chic * nv1 * nc1 + t;
+                const Z1* a = A1 + ((size_t)x * 9 + d1) * nc1 * nc1 + (size_t)chic * nv1 * nc1 + t;
                 double2 s = make_double2(0, 0);
-                for (int i = 0; i < nv1; ++i) s += a[(size_t)i * nc1] * sv[i];
+                for (int i = 0; i < nv1; ++i) s += cvt<double2>(a[(size_t)i * nc1]) * sv[i];
                 h[t] = s;
             }
             __syncthreads();
@@ -209,8 +212,12 @@ void mg2_build_P(const Coarse& c1, Coarse& c2, const double2* W, cudaStream_t st
 void mg2_build_coarse(const Coarse& c1, Coarse& c2, cudaStream_t st) {
     {
         KTimer kt("build_coarse2", 0.0, 0.0, st);
-        build_coarse2_kernel<<<dim3(c2.B.nb, c2.nc), kC2Threads, 0, st>>>(c1.gc, c2.B, c1.nv, c2.nv, c1.A64, c2.P64,
-                                                                         c2.A64);
+        if (c1.a64_stale)
+            build_coarse2_kernel<float2><<<dim3(c2.B.nb, c2.nc), kC2Threads, 0, st>>>(c1.gc, c2.B, c1.nv, c2.nv, c1.A32,
+                                                                                     c2.P64, c2.A64);
+        else
+            build_coarse2_kernel<double2><<<dim3(c2.B.nb, c2.nc), kC2Threads, 0, st>>>(c1.gc, c2.B, c1.nv, c2.nv,
+                                                                                      c1.A64, c2.P64, c2.A64);
     }
     blas_convert(QCD_FP64, c2.A64, QCD_FP32, c2.A32, (size_t)c2.B.nb * 9 * c2.nc * c2.nc, st);
     c2.a64_stale = false;
@@ -220,6 +227,9 @@ void mg2_restrict(const Coarse& c1, const Coarse& c2, int prec, int nrhs, const 
                   const int* act) {
     const long warps = (long)c2.B.nb * c2.nc * nrhs;
     const int grid = (int)std::min<long>((warps * 32 + 255) / 256, 152L * 16);
+    const double es = prec == QCD_FP64 ? 16.0 : 8.0, n1 = (double)c1.gc.V * c1.nc;
+    KTimer kt(prec == QCD_FP64 ? "restrict2_f64" : "restrict2_f32",
+              es * (n1 * c2.nv + nrhs * (n1 + (double)c2.gc.V * c2.nc)), 8.0 * n1 * c2.nv * nrhs, st);
     if (prec == QCD_FP64)
         restrict2_kernel<double2, double><<<grid, 256, 0, st>>>(c1.gc, c2.B, c1.nv, c2.nv, c2.P64, (const double2*)r,
                                                                 (double2*)xc, nrhs, act);
@@ -232,6 +242,9 @@ void mg2_prolong(const Coarse& c1, const Coarse& c2, int prec, int nrhs, const v
                  const int* act) {
     const size_t total = (size_t)nrhs * c2.B.nb * 2 * c2.B.bs * c1.nv;
     const int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    const double es = prec == QCD_FP64 ? 16.0 : 8.0, n1 = (double)c1.gc.V * c1.nc;
+    KTimer kt(prec == QCD_FP64 ? "prolong2_f64" : "prolong2_f32",
+              es * (n1 * c2.nv + nrhs * (n1 + (double)c2.gc.V * c2.nc)), 8.0 * n1 * c2.nv * nrhs, st);
     if (prec == QCD_FP64)
         prolong2_kernel<double2><<<grid, 256, 0, st>>>(c1.gc, c2.B, c1.nv, c2.nv, c2.P64, (const double2*)xc,
                                                        (double2*)x, nrhs, act);

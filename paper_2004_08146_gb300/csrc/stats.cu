@@ -74,9 +74,79 @@ KTimer::~KTimer() {
     s.pending.push_back(Pending{name_, ea_, eb_, bytes_, flops_});
 }
 
+// FMA throughput probe: every thread runs kChains independent multiply-add
+// chains x <- x * a + b for `iters` rounds; the result is stored only when
+// it equals a value it cannot take, so the work is not optimised away.
+namespace {
+constexpr int kChains = 8;
+template <typename R>
+__global__ void __launch_bounds__(256) fma_chain_kernel(R a, R b, int iters, R* sink) {
+    R x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = R(threadIdx.x + c) * R(1e-3);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    R acc = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) acc += x[c];
+    if (acc == R(-12345.678)) sink[threadIdx.x] = acc;
+}
+}  // namespace
+
+double fma_peak_tflops(int prec, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = sms * 8, threads = 256;
+    const int iters = prec == QCD_FP64 ? 64 : 2048;
+    void* sink = nullptr;
+    if (cudaMalloc(&sink, threads * sizeof(double)) != cudaSuccess) return 0.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 6; ++rep) {
+        cudaEventRecord(e0, st);
+        if (prec == QCD_FP64)
+            fma_chain_kernel<double><<<grid, threads, 0, st>>>(0.999999, 1e-7, iters, (double*)sink);
+        else
+            fma_chain_kernel<float><<<grid, threads, 0, st>>>(0.9999f, 1e-4f, iters, (float*)sink);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;   // the first launch loads the module
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    const double flops = 2.0 * kChains * 16.0 * iters * (double)grid * threads;
+    return best > 0 && best < 1e29f ? flops / (best * 1e-3) / 1e12 : 0.0;
+}
+
 }  // namespace qcd
 
 extern "C" {
+
+int qcd_stats_sap_work(double* site_steps, double* site_steps_tri) {
+    if (!site_steps || !site_steps_tri) return QCD_EINVAL;
+    double w[2];
+    qcd::sap_work_read(w);
+    *site_steps = w[0];
+    *site_steps_tri = w[1];
+    return QCD_OK;
+}
+
+int qcd_fma_peak(int prec, double* tflops) {
+    if (!tflops || (prec != QCD_FP64 && prec != QCD_FP32)) return QCD_EINVAL;
+    *tflops = qcd::fma_peak_tflops(prec, nullptr);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess && *tflops > 0 ? QCD_OK : QCD_ECUDA;
+}
 
 int qcd_stats_reset(int mode, const char* filter) {
     using namespace qcd;
@@ -91,6 +161,9 @@ int qcd_stats_reset(int mode, const char* filter) {
     s.pending.clear();
     s.agg.clear();
     s.mode = mode;
+    // the SAP work counters restart with the accounting (outside timed regions)
+    if (cudaDeviceSynchronize() == cudaSuccess) sap_work_reset();
+    cudaGetLastError();
     s.filter = filter ? filter : "";
     return QCD_OK;
 }

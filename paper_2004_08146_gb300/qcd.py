@@ -106,6 +106,7 @@ _SIGS = {
     "qcd_local_coherence": (_I, [_P, _I, _P, _DP]),
     "qcd_eig_derivative": (_I, [_P, _DP, _I, _P, _DP]),
     "qcd_eig_force": (_I, [_P, _I, _P, _P]),
+    "qcd_bilinear_force": (_I, [_P, _I, _P, _P, _I, _P]),
     "qcd_coarse_apply": (_I, [_P, _I, _I, _I, _P, _P, _DP]),
     "qcd_mg_get_P": (_I, [_P, _DP]),
     "qcd_mg_get_coarse": (_I, [_P, _DP]),
@@ -118,6 +119,8 @@ _SIGS = {
     "qcd_sap_static": (_I, [_P, _I, _I, _I, _P, _P, _DP, _I, _D]),
     "qcd_stats_reset": (_I, [_I, ctypes.c_char_p]),
     "qcd_stats_read": (_I, [ctypes.POINTER(qcd_kernel_stat), _I, _IP]),
+    "qcd_stats_sap_work": (_I, [_DP, _DP]),
+    "qcd_fma_peak": (_I, [_I, _DP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -160,6 +163,24 @@ def qcd_stats_read():
     _lib.qcd_stats_read(arr, n.value, ctypes.byref(n))
     return [dict(name=a.name.decode(), launches=a.launches, timed=a.timed, total_ms=a.total_ms, bytes=a.bytes,
                  flops=a.flops, timed_bytes=a.timed_bytes, timed_flops=a.timed_flops) for a in arr[:n.value]]
+
+
+def qcd_stats_sap_work():
+    """(sum block sites x steps, sum block sites x k(k+1)/2) of the SAP block solves."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    rc = _lib.qcd_stats_sap_work(ctypes.byref(a), ctypes.byref(b))
+    if rc != QCD_OK:
+        raise QcdError(rc, "qcd_stats_sap_work")
+    return a.value, b.value
+
+
+def qcd_fma_peak(prec):
+    """Measured FMA throughput (TFLOP/s) of the current device for QCD_FP32 / QCD_FP64."""
+    t = ctypes.c_double(0)
+    rc = _lib.qcd_fma_peak(int(prec), ctypes.byref(t))
+    if rc != QCD_OK:
+        raise QcdError(rc, "qcd_fma_peak")
+    return t.value
 
 
 def default_params(**kw):
@@ -207,6 +228,7 @@ class Context:
     def qcd_set_gauge(self, U, dims, m0, csw):
         Uh = np.ascontiguousarray(np.asarray(U, dtype=np.complex128)).view(np.float64)
         d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+        self.dims = tuple(int(x) for x in dims)
         self._U_keep = Uh
         return self._check(_lib.qcd_set_gauge(self.h, Uh.ctypes.data_as(_DP), d, float(m0), float(csw)))
 
@@ -264,6 +286,9 @@ class Context:
 
     def qcd_eig_force(self, nvec, V, F):
         return self._check(_lib.qcd_eig_force(self.h, int(nvec), _ptr(V), _ptr(F)))
+
+    def qcd_bilinear_force(self, nvec, G, Psi, grad, F):
+        return self._check(_lib.qcd_bilinear_force(self.h, int(nvec), _ptr(G), _ptr(Psi), int(grad), _ptr(F)))
 
     def qcd_local_coherence(self, nvec, V):
         out = np.zeros(int(nvec), dtype=np.float64)

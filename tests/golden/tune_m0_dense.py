@@ -1,0 +1,75 @@
+"""Choose m0 for the two large synthetic workloads (32 x 16^3 and 64 x 32^3)
+so that min |lambda(Q)| comes as close as the field allows to its target (the
+stand-in for the paper's "comparable conditioning", Sec. 4).  Calls only the
+oracle and the seeded input generator; adds entries to
+tests/golden/workloads.json.
+
+The oracle cannot diagonalise Q at those volumes, so min |lambda| is taken on
+proxy lattices with the workload's link roughness eps and clover coefficient
+c_sw, where the oracle's dense Q fits: 4^4 and 8 x 4^3 (3072 and 6144
+unknowns), two seeds each, by dense Hermitian eigendecomposition.  The m0 grid
+runs across the region where the smallest |lambda| is smallest; the chosen m0
+is the grid point whose larger proxy (8 x 4^3, mean over the seeds) is closest
+to the target in log distance.  What min |lambda| the chosen m0 gives on the
+full lattice is measured by the GPU runs and reported with them: a larger
+volume has more low modes, so it is at most the proxy's value when the
+spectrum near zero has no gap.
+
+usage: python tests/golden/tune_m0_dense.py <name> [<name> ...]
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle.dirac import WilsonClover  # noqa: E402
+from paper_2004_08146_gb300 import synth  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workloads.json")
+
+SPECS = {
+    "c3_32x16c3": dict(dims=(32, 16, 16, 16), eps=0.6, csw=1.7, seed=1003, target=5e-3),
+    "c4_64x32c3": dict(dims=(64, 32, 32, 32), eps=0.6, csw=1.9, seed=1004, target=1e-3),
+}
+PROXIES = [(4, 4, 4, 4), (8, 4, 4, 4)]
+GRID = [round(-0.60 - 0.05 * i, 2) for i in range(13)]     # -0.60 ... -1.20
+
+
+def min_abs_lambda(dims, eps, csw, m0, seed):
+    U = synth.gauge_field(dims, eps, seed)
+    w = np.linalg.eigvalsh(WilsonClover(U, m0, csw).dense('Q'))
+    return float(np.min(np.abs(w)))
+
+
+def tune(name):
+    s = SPECS[name]
+    seeds = [s["seed"], s["seed"] + 100]
+    table = []
+    for m0 in GRID:
+        row = {"m0": m0}
+        for dims in PROXIES:
+            t = time.time()
+            vals = [min_abs_lambda(dims, s["eps"], s["csw"], m0, sd) for sd in seeds]
+            row["x".join(map(str, dims))] = float(np.mean(vals))
+            print(f"{name}: m0={m0:+.2f} {dims} min|lambda| = {np.mean(vals):.4e} ({time.time() - t:.0f}s)",
+                  flush=True)
+        table.append(row)
+    key = "x".join(map(str, PROXIES[-1]))
+    best = min(table, key=lambda r: abs(np.log(r[key] / s["target"])))
+    return dict(dims=list(s["dims"]), eps=s["eps"], csw=s["csw"], seed=s["seed"], m0=best["m0"],
+                target=s["target"], proxy_lattices=["x".join(map(str, d)) for d in PROXIES],
+                proxy_seeds=seeds, proxy_min_abs_lambda=best[key], grid=table)
+
+
+if __name__ == "__main__":
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for name in sys.argv[1:]:
+        data[name] = tune(name)
+        with open(OUT, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
+    print(json.dumps({k: {kk: v for kk, v in d.items() if kk != "grid"} for k, d in data.items()}, indent=1))

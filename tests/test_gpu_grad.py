@@ -114,3 +114,76 @@ def test_autograd_adjoint_is_the_operator():
     pr = torch.from_numpy(p0.copy()).requires_grad_(True)
     torch.vdot(torch.from_numpy(g), torch.from_numpy(op.dense('Q', tau)) @ pr).real.backward()
     assert np.max(np.abs(host(psi.grad) - pr.grad.numpy())) < 1e-12 * np.max(np.abs(pr.grad.numpy()))
+
+
+@pytest.mark.parametrize("dims,antip,csw", [((4, 4, 2, 2), True, 1.5), ((2, 4, 4, 2), False, 1.5),
+                                            ((4, 2, 2, 4), True, 0.0)])
+def test_bilinear_force_matches_oracle(dims, antip, csw):
+    """Force of Re <g, Q psi> for distinct g, psi (the link adjoint of the
+    autograd wrapper), element by element against the oracle (1e-12 of the
+    largest entry); the gradient form equals i F U."""
+    torch = torch_cuda()
+    from oracle.dirac import bilinear_force
+    U = synth.gauge_field(dims, 0.5, 171)
+    op = WilsonClover(U, -0.3, csw, antiperiodic_t=antip)
+    ctx = make_ctx(U, dims, -0.3, csw, antiperiodic_t=int(antip))
+    g = synth.spinor(dims, 172, nvec=3)
+    psi = synth.spinor(dims, 173, nvec=3)
+    nl = 36 * int(np.prod(dims))
+    F = torch.zeros(3 * nl, dtype=torch.complex128, device="cuda")
+    Gr = torch.zeros_like(F)
+    ctx.qcd_bilinear_force(3, dev(g), dev(psi), 0, F)
+    ctx.qcd_bilinear_force(3, dev(g), dev(psi), 1, Gr)
+    got = host(F).reshape((3,) + dims + (4, 3, 3))
+    gr = host(Gr).reshape((3,) + dims + (4, 3, 3))
+    for j in range(3):
+        ref = bilinear_force(op, g[j], psi[j])
+        assert np.max(np.abs(got[j] - ref)) < 1e-12 * np.max(np.abs(ref)), j
+        assert np.max(np.abs(gr[j] - 1j * (ref @ U))) < 1e-12 * np.max(np.abs(ref)), j
+
+
+def test_autograd_links_central_differences_16c4():
+    """The differentiation workload: 16^4 field (eps 0.5, c_sw 1.5), 8 random
+    complex128 spinors psi_j and cotangents g_j, L = sum_j Re <g_j, (Q - tau)
+    psi_j> through the autograd wrapper with the links as an input.  The links'
+    gradient contracted with dU = i X U matches the central difference
+    (h = 1e-5) of L under U -> exp(i eps X) U along 16 random su(3) directions
+    to 1e-6 relative; the spinor gradient is (Q - tau) g."""
+    torch = torch_cuda()
+    from paper_2004_08146_gb300 import autograd
+    dims, tau, m0, csw = (16, 16, 16, 16), 0.05, -0.85, 1.5
+    U = synth.gauge_field(dims, 0.5, 1007)
+    ctx = make_ctx(U, dims, m0, csw)
+    nrhs = 8
+    g = dev(synth.spinor(dims, 181, nvec=nrhs))
+    psi = dev(synth.spinor(dims, 182, nvec=nrhs)).requires_grad_(True)
+    links = torch.from_numpy(U.copy()).requires_grad_(True)
+    L = torch.vdot(g, autograd.apply_Q(ctx, psi, tau, links=links, lattice=(dims, m0, csw))).real
+    L.backward()
+    Gl = links.grad.numpy()
+    # spinor gradient
+    Qg = torch.empty_like(g)
+    ctx.qcd_apply(1, 0, nrhs, g, Qg, [tau] * nrhs)
+    assert (psi.grad - Qg).abs().max().item() < 1e-12 * Qg.abs().max().item()
+    out = torch.empty_like(g)
+    h = 1e-5
+
+    def loss(Um):
+        ctx.qcd_set_gauge(Um, dims, m0, csw)
+        ctx.qcd_apply(1, 0, nrhs, psi.detach(), out, [tau] * nrhs)
+        torch.cuda.synchronize()
+        return torch.vdot(g, out).real.item()
+
+    def moved(X, eps):   # exp(i eps X) U to O(eps^4) ~ 1e-20
+        X2 = np.einsum('...ab,...bc->...ac', X, X)
+        X3 = np.einsum('...ab,...bc->...ac', X2, X)
+        E = np.eye(3) + 1j * eps * X - 0.5 * eps * eps * X2 - 1j * eps ** 3 / 6 * X3
+        return np.einsum('...ab,...bc->...ac', E, U)
+
+    for d in range(16):
+        X = synth.su3_directions(dims, 2000 + d, 1)[0]
+        dU = 1j * np.einsum('...ab,...bc->...ac', X, U)
+        got = np.real(np.vdot(Gl, dU))
+        fd = (loss(moved(X, h)) - loss(moved(X, -h))) / (2 * h)
+        assert abs(got - fd) <= 1e-6 * abs(fd), (d, got, fd)
+    ctx.close()

@@ -37,7 +37,9 @@ def setting(request):
                       smoother='sap', sap_block_iters=CYCLE["sap_block_iters"], sap_block_tol=0.0)
     h.set_vectors(vecs)
     ctx = make_ctx(U, DIMS, m0, csw, sap_block=SAP, sap_block_tol=-1.0, coarse_tol=0.0, precision=0,
-                   coarse_maxiter=CYCLE["coarse_maxiter"], nu=CYCLE["nu"], sap_block_iters=CYCLE["sap_block_iters"])
+                   coarse_maxiter=CYCLE["coarse_maxiter"], nu=CYCLE["nu"], sap_block_iters=CYCLE["sap_block_iters"],
+                   setup_iters=1)
+    ctx.qcd_mg_setup(nv, agg)                    # fixes the aggregate shape
     ctx.qcd_mg_update_from_eigvecs(dev(vecs), nv)
     b = synth.spinor(DIMS, 158, nvec=1)
     ref = h.cycle(b[0], 0.07)
@@ -90,9 +92,11 @@ def test_two_level_cycle_every_coarse_layout(setting, layout, prec, tol):
     fits only in the FP32 run on 128 coarse sites)."""
     from paper_2004_08146_gb300 import qcd
     dt = np.complex128 if prec == 0 else np.complex64
-    ctx = make_ctx(setting["U"], DIMS, setting["m0"], setting["csw"], sap_block=SAP, sap_block_tol=-1.0,
-                   coarse_tol=0.0, precision=0, coarse_layout=layout, **CYCLE)
+    kw = dict(sap_block=SAP, sap_block_tol=-1.0, coarse_tol=0.0, precision=0, setup_iters=1, **CYCLE)
+    ctx = make_ctx(setting["U"], DIMS, setting["m0"], setting["csw"], **kw)
+    ctx.qcd_mg_setup(setting["nv"], setting["agg"])
     ctx.qcd_mg_update_from_eigvecs(dev(setting["vecs"]), setting["nv"])
+    ctx.qcd_set_params(qcd.default_params(coarse_layout=layout, **kw))
     b = setting["b"]
     x = dev(b, dt)
     fits = layout != 1 or (prec == 1 and setting["agg"] == (4, 2, 2, 2))

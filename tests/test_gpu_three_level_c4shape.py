@@ -34,7 +34,8 @@ def setting():
                         sap_block_tol=0.0)
     h.set_vectors(vecs)
     ctx = make_ctx(U, DIMS, m0, csw, sap_block=SAP, sap_block_tol=-1.0, precision=0, levels=3, nv2=NV2,
-                   agg2=AGG2, **KC)
+                   agg2=AGG2, setup_iters=1, **KC)
+    ctx.qcd_mg_setup(NV, AGG)                    # fixes the aggregate shape
     ctx.qcd_mg_update_from_eigvecs(dev(vecs), NV)
     b = synth.spinor(DIMS, 168, nvec=1)
     ref = h.cycle(b[0], 0.05)

@@ -308,3 +308,50 @@ def test_force_single_link_central_difference():
         fd = (rq(h) - rq(-h)) / (2 * h)
         got = np.real(np.trace(X[site + (mu,)] @ F[site + (mu,)]))
         assert abs(got - fd) < 1e-8 * max(abs(fd), 1e-3), (site, mu, got, fd)
+
+
+@pytest.mark.parametrize("dims,antip,csw", [((2, 2, 2, 2), True, 1.5), ((4, 2, 2, 4), True, 1.5),
+                                            ((2, 4, 2, 2), False, 0.0), ((4, 4, 2, 2), False, 1.2)])
+def test_bilinear_force_contracts_to_directional_derivative(dims, antip, csw):
+    """Force of Re <g, Q psi> for distinct random g, psi: sum tr(X F) equals
+    Re <g, Gamma5 (dD/deps) psi> of the product-rule tangent (pinned by
+    central differences above); F is traceless Hermitian."""
+    from oracle.dirac import bilinear_force, operator_tangent
+    U = synth.gauge_field(dims, 0.5, 27)
+    op = WilsonClover(U, -0.3, csw, antiperiodic_t=antip)
+    g = synth.spinor(dims, 28)
+    psi = synth.spinor(dims, 29)
+    F = bilinear_force(op, g, psi)
+    assert np.max(np.abs(F - np.conj(np.swapaxes(F, -1, -2)))) < 1e-14
+    assert np.max(np.abs(np.trace(F, axis1=-2, axis2=-1))) < 1e-14
+    for X in synth.su3_directions(dims, 30, 2):
+        con = np.sum(X * np.swapaxes(F, -1, -2))
+        ref = np.real(np.vdot(g, WilsonClover.g5(operator_tangent(op, X)(psi))))
+        assert abs(con.imag) < 1e-13 and abs(con.real - ref) < 1e-12 * abs(ref)
+
+
+def test_bilinear_force_single_link_central_difference():
+    """One link moved alone: tr(X F) against the central difference of
+    Re <g, Q(U(+-h)) psi> (h = 1e-5), across the antiperiodic boundary and on a
+    spatial link; and the diagonal case g = psi is v^H v times the eigenvalue
+    force."""
+    from oracle.dirac import bilinear_force, eigenvalue_force
+    dims = (4, 2, 2, 2)
+    U = synth.gauge_field(dims, 0.5, 37)
+    op = WilsonClover(U, -0.3, 1.5)
+    g = synth.spinor(dims, 38)
+    psi = synth.spinor(dims, 39)
+    F = bilinear_force(op, g, psi)
+    Xall = synth.su3_directions(dims, 40, 1)[0]
+    h = 1e-5
+    for site, mu in [((3, 1, 0, 1), 0), ((1, 0, 1, 1), 2)]:
+        X = np.zeros_like(Xall)
+        X[site + (mu,)] = Xall[site + (mu,)]
+
+        def bl(eps):
+            return np.real(np.vdot(g, WilsonClover(_moved_links(U, X, eps), -0.3, 1.5).Q(psi)))
+        fd = (bl(h) - bl(-h)) / (2 * h)
+        got = np.real(np.trace(X[site + (mu,)] @ F[site + (mu,)]))
+        assert abs(got - fd) < 1e-8 * max(abs(fd), 1e-3), (site, mu, got, fd)
+    Fd = bilinear_force(op, psi, psi)
+    assert np.max(np.abs(Fd - np.real(np.vdot(psi, psi)) * eigenvalue_force(op, psi))) < 1e-12 * np.max(np.abs(Fd))
