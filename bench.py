@@ -2,13 +2,16 @@
 """Benchmark of the GD-lambda-AMG hot path on one GB300 (or N replicas).
 
 Metric: seconds to the k smallest-|lambda| eigenpairs of Q = Gamma5 D at
-eigen-residual 1e-8 (mixed precision: FP32 inner solves, FP64 outer), on the
-16 x 8^3 workload (k = 50, two-level MG, 2^4 aggregates, Nv = 8, SAP 2^4).
-One step = multigrid setup + eigensolve from the resident gauge field.
-Also reported: the same step in plain FP64, the end-to-end time through the
-C ABI from host buffers, the fine-stencil bandwidth on a 64 x 32^3 lattice,
-the live roofline of the dominant kernel and the CPU oracle on a bounded
-sample.  Prints one JSON line (rank 0).
+eigen-residual 1e-8 (mixed precision: FP32 inner solves, FP64 outer).  The
+timed step is the 16 x 8^3 workload (k = 50, two-level MG, 2^4 aggregates,
+Nv = 8, SAP 2^4): multigrid setup + eigensolve from the resident gauge field.
+Also reported: the same step in plain FP64; the end-to-end time through the
+C ABI from host buffers; the fine-stencil bandwidth on a 64 x 32^3 lattice;
+the live roofline of the dominant kernel (HBM and, for the SAP block solves,
+FP32 ALU against the measured FMA peak); the 64 x 32^3 three-level workload
+(100 pairs, mixed precision) timed once after a warm-up solve; and the CPU
+oracle timed on per-operation samples on the host's cores.  Prints one JSON
+line (rank 0).
 
 usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -64,6 +67,11 @@ def parse():
                     help="run and print only the fine-stencil bandwidth measurement")
     ap.add_argument("--k", type=int, default=None,
                     help="eigenpairs per step instead of the workload's (short profiling runs)")
+    ap.add_argument("--no-large-workload", action="store_true",
+                    help="skip the 64 x 32^3 three-level measurement")
+    ap.add_argument("--large-workload", default="c4_64x32c3")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--oracle-ops", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -86,12 +94,23 @@ def max_over_ranks(value, device=None):
     return float(t.item())
 
 
-# DRAM bytes per launch (dram__bytes.sum.per_second x gpu__time_duration.sum,
-# i.e. read + write) from one ncu capture of each kernel as it stands now, for
-# the roofline's "traffic"; profiles/sap_chi_f32_c2_16x8c3.md gives the
-# capture.  A kernel that changes is taken out of this table until it is
-# captured again.
-NCU_TRAFFIC = {"sap_block_f32": 4782000}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of each kernel as it stands now, for the roofline's
+# "traffic"; a kernel that changes is taken out of this table until it is
+# captured again (the field is then null).
+NCU_TRAFFIC = {}
+
+# Work model of the SAP block solves for the FP32-ALU roofline, per block
+# site and GMRES step j (0-based) of a block solve of k steps: the Dirichlet
+# block operator (clover 504 + diagonal and shift 48 + 168 per in-block hop;
+# 2^4 blocks have 4 in-block hops per site), 192 (j + 1) for the Gram-Schmidt
+# inner products and updates, 72 for the norm and scaling and 96 for the
+# solution update.  Summed over j: k (op + 168) + 192 k (k + 1) / 2, with the
+# two sums read from the library's SAP work counters.
+def sap_flops(site_steps, site_steps_tri, block=(2, 2, 2, 2)):
+    hops = sum(2.0 * (b - 1) / b for b in block)
+    op = 504.0 + 48.0 + 168.0 * hops
+    return site_steps * (op + 168.0) + 192.0 * site_steps_tri
 
 
 def measured_peaks():
@@ -154,39 +173,82 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle sample
-def oracle_sample(w, outer_iters, block, inner_iters=None):
-    """Time the oracle (FP64 numpy) on a bounded sample of the workload and
-    scale it to one eigensolve: one adaptive-setup cycle on one test vector
-    and one MG-preconditioned correction solve with its Q apply and Gram-
-    Schmidt.  Estimate = setup_iters * Nv * t_cycle + outer * block * t_outer."""
+# Operation counts of one GPU eigensolve of each workload (FGMRES iterations
+# summed over targets, outer iterations; from the GPU bench line), used to
+# scale the oracle's per-operation times to one eigensolve when no GPU run
+# of the same process provides them (the reference arm).
+REF_COUNTS = {"c2_16x8c3": dict(inner=3129, outer=316, block=2)}
+
+
+def oracle_ops(w):
+    """Time the oracle (FP64 numpy) on per-operation samples of the workload,
+    in this process: one Q apply, the Galerkin build of P and D_c, one
+    two-level MG cycle (SAP, Table 2 parameters), and one Gram-Schmidt pass
+    of a vector against 50 orthonormal basis vectors (dot products + update,
+    twice)."""
     from oracle.dirac import WilsonClover
     from oracle import mg
     from paper_2004_08146_gb300 import synth
     dims = tuple(w["dims"])
     U = synth.gauge_field(dims, w["eps"], w["seed"])
     op = WilsonClover(U, w["m0"], w["csw"])
+    psi = synth.spinor(dims, w["seed"] + 11)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        op.Q(psi)
+    t_apply = (time.perf_counter() - t0) / 3
     h = mg.TwoLevelMG(op, w["agg"], w["sap"], w["nv"], smoother="sap", form="g5")
-    vecs = synth.spinor(dims, w["seed"] + 11, nvec=w["nv"])
+    vecs = synth.spinor(dims, w["seed"] + 12, nvec=w["nv"])
+    t0 = time.perf_counter()
     h.set_vectors(vecs)
+    t_build = time.perf_counter() - t0
     t0 = time.perf_counter()
-    h.cycle(vecs[0], 0.0)
+    h.cycle(psi, 0.05)
     t_cycle = time.perf_counter() - t0
-    r = synth.spinor(dims, w["seed"] + 13)
-    basis = synth.complex_gaussian((48, op.n), w["seed"] + 14)
+    B = synth.complex_gaussian((op.n, 50), w["seed"] + 13)
+    B, _ = np.linalg.qr(B)
+    v = psi.reshape(-1)
     t0 = time.perf_counter()
-    x, _ = h.solve(op.g5(r), 0.05, 1e-1, 5)
-    v = x.reshape(-1)
     for _ in range(2):
-        v = v - basis.T @ (basis.conj() @ v)
-    op.Q(v.reshape(dims + (4, 3)))
-    t_outer = time.perf_counter() - t0
-    est = 6 * w["nv"] * t_cycle + outer_iters * block * t_outer
-    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 numpy oracle, one setup cycle ({t_cycle:.2f} s) and one FGMRES+MG(SAP) "
-                       f"correction solve with Q apply and Gram-Schmidt ({t_outer:.2f} s) on the "
-                       f"{WORKLOAD} workload, scaled by 6 x Nv cycles and {outer_iters} outer x {block} "
-                       f"targets of the GPU run"),
-            "t_cycle_s": t_cycle, "t_outer_s": t_outer}
+        v = v - B @ (B.conj().T @ v)
+    t_gs = time.perf_counter() - t0
+    return dict(t_apply=t_apply, t_build=t_build, t_cycle=t_cycle, t_gs=t_gs)
+
+
+def oracle_estimate(w, ops, inner, outer, block):
+    """One eigensolve from per-operation times: the setup (setup_iters Galerkin
+    builds, setup_iters x Nv cycles), every FGMRES iteration (one cycle and
+    one Q apply) and every added basis vector (Gram-Schmidt and one Q apply)."""
+    setup = 6 * ops["t_build"] + 6 * w["nv"] * ops["t_cycle"]
+    return setup + inner * (ops["t_cycle"] + ops["t_apply"]) + outer * block * (ops["t_gs"] + ops["t_apply"])
+
+
+def oracle_sample_subprocess(workload, k=None):
+    """oracle_ops of the workload in a child process with one BLAS/OpenMP
+    thread, so the timing uses exactly one host core."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-ops", "--workload", workload]
+    if k is not None:
+        cmd += ["--k", str(k)]
+    t0 = time.perf_counter()
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+    wall = time.perf_counter() - t0
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-400:])
+    ops = json.loads(out.stdout.strip().splitlines()[-1])
+    ops["wall_s"] = wall
+    return ops
+
+
+def cpu_baseline_line(w, ops, inner, outer, block, counts_from):
+    est = oracle_estimate(w, ops, inner, outer, block)
+    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "host_cpu_count": os.cpu_count(),
+            "sample": (f"FP64 numpy oracle on one host core, per-operation samples of the {w['name']} workload: "
+                       f"Q apply {ops['t_apply']:.3f} s, Galerkin build {ops['t_build']:.2f} s, two-level cycle "
+                       f"{ops['t_cycle']:.2f} s, Gram-Schmidt against 50 vectors {ops['t_gs']:.3f} s; value = "
+                       f"6 builds + 6 x Nv cycles + {inner} FGMRES iterations x (cycle + apply) + {outer} x {block} "
+                       f"added vectors x (Gram-Schmidt + apply), counts from {counts_from}"),
+            "per_op_s": {k: round(v, 4) for k, v in ops.items() if k.startswith("t_")}}
 
 
 # ----------------------------------------------------------------- reference arm
@@ -196,22 +258,24 @@ def run_reference(args):
         return
     from paper_2004_08146_gb300 import workloads
     w = workloads.get(args.workload)
-    if args.k is not None:
-        w["k"] = args.k
-    # outer-iteration count of the method on this workload (from a GPU run of
-    # the same configuration); without one the paper's ~10 outer per pair
-    outer = int(os.environ.get("QCD_REF_OUTER", str(10 * w["k"] // 2)))
-    samples = []
+    w["name"] = args.workload
+    c = REF_COUNTS[args.workload]
+    samples, walls = [], []
     for i in range(args.warmup + args.steps):
-        s = oracle_sample(w, outer, 2)
+        ops = oracle_sample_subprocess(args.workload)
         if i >= args.warmup:
-            samples.append(s["value"])
+            samples.append(oracle_estimate(w, ops, c["inner"], c["outer"], c["block"]))
+            walls.append(ops["wall_s"])
     val = float(np.mean(samples))
+    cpu = cpu_baseline_line(w, ops, c["inner"], c["outer"], c["block"], "the GPU bench's recorded counts")
+    cpu["value"] = val
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup,
+            # each step is one timed per-operation sample; its wall time is the step time
+            "ms_per_step": float(np.mean(walls)) * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "lattice": "x".join(map(str, w["dims"])), "k": w["k"]},
-            "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "kind": "oracle", "sample": s["sample"]},
+            "cpu_baseline": cpu,
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -219,6 +283,10 @@ def run_reference(args):
 # ----------------------------------------------------------------- GPU arm
 def main():
     args = parse()
+    if args.oracle_ops:
+        from paper_2004_08146_gb300 import workloads
+        print(json.dumps(oracle_ops(workloads.get(args.workload))), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -261,7 +329,7 @@ def main():
         return
 
     def make(precision):
-        p = qcd.default_params(precision=precision, use_mg=w["use_mg"], sap_block=w["sap"])
+        p = workload_params(qcd, w, precision=precision)
         ctx = qcd.Context(params=p, stream=sp)
         ctx.qcd_set_gauge(U, dims, w["m0"], w["csw"])
         return ctx
@@ -322,6 +390,8 @@ def main():
     ms, infos, lam = timed_steps(ctx, args.steps, max(0, args.warmup - 2), profile=True)
     clk = clocks.stop()
     st_timed = {s["name"]: s for s in qcd.qcd_stats_read()}
+    torch.cuda.synchronize()
+    sap_work = qcd.qcd_stats_sap_work()
     qcd.qcd_stats_reset(0)
     launches = sum(s["launches"] for s in st_timed.values())
     # warm-up steps ran inside the accounting window too: count only the timed share
@@ -344,20 +414,20 @@ def main():
     # ---- end to end through the C ABI from host buffers
     e2e_s = None
     if not args.no_e2e:
-        ctx_e = qcd.Context(params=qcd.default_params(precision=qcd.QCD_MIXED, use_mg=w["use_mg"], sap_block=w["sap"]),
-                            stream=sp)
+        ctx_e = qcd.Context(params=workload_params(qcd, w, precision=qcd.QCD_MIXED), stream=sp)
         Vh = torch.empty(w["k"] * n, dtype=torch.complex128).pin_memory()
-        e2e = []
-        for i in range(1 + args.steps):
+        e2e, e2e_info = [], []
+        for i in range(1 + max(1, min(args.steps, args.e2e_steps))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ctx_e.qcd_set_gauge(U, dims, w["m0"], w["csw"])
-            step(ctx_e)
+            lam_e, info_e = step(ctx_e)
+            stream.synchronize()                  # V is written on the library's stream
             Vh.copy_(V, non_blocking=True)
             torch.cuda.current_stream(devn).synchronize()
-            stream.synchronize()
             if i > 0:
                 e2e.append(time.perf_counter() - t0)
+                e2e_info.append({"outer": info_e.outer, "inner": info_e.inner})
         ctx_e.close()
         e2e_s = float(np.mean(e2e))
 
@@ -366,9 +436,28 @@ def main():
     if not args.no_stencil and rank == 0:
         stencil = stencil_bench(qcd, synth, torch, devn, stream, peak)
 
+    # ---- SAP block solves against the FP32 ALU peak (work counted from the steps taken)
+    alu = None
+    if d["name"].startswith("sap_block_f32") and d["total_ms"] > 0:
+        fp32_peak = qcd.qcd_fma_peak(qcd.QCD_FP32)
+        sflops = sap_flops(*sap_work, block=w["sap"])
+        alu = {"kernel": d["name"], "bound": "alu", "achieved": sflops / (d["total_ms"] * 1e-3) / 1e12,
+               "peak": fp32_peak, "unit": "TFLOP/s", "peak_kind": "measured FP32 FMA probe (qcd_fma_peak)",
+               "frac": sflops / (d["total_ms"] * 1e-3) / 1e12 / fp32_peak,
+               "site_steps": sap_work[0]}
+    fp64_peak = qcd.qcd_fma_peak(qcd.QCD_FP64)
+
+    # ---- the 64 x 32^3 three-level workload, 100 pairs, mixed precision
+    large = None
+    if not args.no_large_workload and rank == 0:
+        large = large_workload(qcd, synth, torch, devn, stream, workloads, args.large_workload)
+
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
-        cpu = oracle_sample(w, int(np.mean([i.outer for i in infos])), 2)
+        w["name"] = args.workload
+        ops = oracle_sample_subprocess(args.workload)
+        cpu = cpu_baseline_line(w, ops, int(np.mean([i.inner for i in infos])), int(np.mean([i.outer for i in infos])),
+                                qcd.default_params().block, "this run's GPU steps")
 
     if rank == 0:
         info = infos[-1]
@@ -382,7 +471,8 @@ def main():
                        "eps": w["eps"], "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{ws}"},
             "e2e": None if e2e_s is None else {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(U.nbytes),
-                                               "d2h_bytes_per_step": int(V.numel() * 16 + 8 * w["k"])},
+                                               "d2h_bytes_per_step": int(V.numel() * 16 + 8 * w["k"]),
+                                               "steps": len(e2e), "iterations": e2e_info},
             "gpu_launches": launches_timed,
             "roofline": {"kernel": dom["name"], "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
@@ -392,8 +482,11 @@ def main():
             "eig": {"outer": info.outer, "inner": info.inner, "locked": info.locked, "updates": info.updates,
                     "max_residual": info.max_residual, "min_abs_lambda": float(np.min(np.abs(lam))),
                     "max_abs_lambda": float(np.max(np.abs(lam)))},
+            "alu_roofline": alu,
+            "fp64_fma_peak_tflops": fp64_peak,
             "fp64": fp64,
             "stencil": stencil,
+            "large_workload": large,
             "clocks": clk,
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "kernel_share_warmup": {s["name"]: round(s["total_ms"], 3) for s in
@@ -402,6 +495,78 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def workload_params(qcd, w, **kw):
+    """Library parameters of a workload: Table 2 defaults plus the workload's
+    MG and outer-iteration shape."""
+    p = dict(use_mg=w["use_mg"], sap_block=w["sap"])
+    for key in ("block", "m_min", "m_max", "update_every", "levels", "nv2", "agg2"):
+        if key in w:
+            p[key] = w[key]
+    p.update(kw)
+    return qcd.default_params(**p)
+
+
+def large_workload(qcd, synth, torch, devn, stream, workloads, name):
+    """The 64 x 32^3 workload (2.1 M sites, 25 M unknowns; eps 0.6, c_sw 1.9),
+    three-level MG (4^4 then 2^4 aggregates, Nv = nv2 = 24), 100 pairs at
+    residual 1e-8, 16 targets per outer iteration, mixed precision: one
+    warm-up solve of 16 pairs, then one timed setup + eigensolve of the
+    workload's k (CUDA events on the library's stream, every kernel timed by
+    the library's accounting, clocks sampled)."""
+    w = workloads.get(name)
+    dims = tuple(w["dims"])
+    U = synth.gauge_field(dims, w["eps"], w["seed"])
+    n = 12 * int(np.prod(dims))
+    p = workload_params(qcd, w, max_outer=2000)
+    ctx = qcd.Context(params=p, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    ctx.qcd_set_gauge(U, dims, w["m0"], w["csw"])
+    t_gauge = time.perf_counter() - t0
+    V = torch.zeros(w["k"] * n, dtype=torch.complex128, device=devn)
+    ctx.qcd_mg_setup(w["nv"], w["agg"])                  # warm-up
+    ctx.qcd_eigs(16, 1e-8, V)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(devn.index or 0)
+    qcd.qcd_stats_reset(1)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.qcd_mg_setup(w["nv"], w["agg"])
+    e1.record(stream)
+    rc, lam, info = ctx.qcd_eigs(w["k"], 1e-8, V)
+    e2.record(stream)
+    e2.synchronize()
+    clk = clocks.stop()
+    st = qcd.qcd_stats_read()
+    torch.cuda.synchronize()
+    sap_work = qcd.qcd_stats_sap_work()
+    qcd.qcd_stats_reset(0)
+    ctx.close()
+    top = sorted(st, key=lambda r: -r["total_ms"])[:12]
+    sap = [r for r in st if r["name"] == "sap_block_f32"]
+    out = {"workload": name, "lattice": "x".join(map(str, dims)), "unknowns": n, "k": w["k"],
+           "mg": f"{w.get('levels', 2)}-level, {w['agg']} then {w.get('agg2')} aggregates, Nv={w['nv']}, "
+                 f"nv2={w.get('nv2')}, SAP {w['sap']}",
+           "targets_per_iteration": w["block"], "m_min": w["m_min"], "m_max": w["m_max"], "m0": w["m0"],
+           "csw": w["csw"], "eps": w["eps"], "precision": "FP32 inner / FP64 outer",
+           "converged": bool(info.converged), "rc": rc,
+           "value": (e0.elapsed_time(e2)) / 1e3, "unit": "s", "setup_s": e0.elapsed_time(e1) / 1e3,
+           "eigs_s": e1.elapsed_time(e2) / 1e3, "set_gauge_s": t_gauge,
+           "outer": info.outer, "inner": info.inner, "locked": info.locked, "updates": info.updates,
+           "coarse_iterations": info.coarse_iterations, "max_residual": info.max_residual,
+           "min_abs_lambda": float(np.nanmin(np.abs(lam))), "max_abs_lambda": float(np.nanmax(np.abs(lam))),
+           "clocks": clk, "kernel_ms": {r["name"]: round(r["total_ms"], 1) for r in top},
+           "gpu_launches": int(sum(r["launches"] for r in st))}
+    if sap and sap[0]["total_ms"] > 0:
+        fl = sap_flops(*sap_work, block=w["sap"])
+        peak = qcd.qcd_fma_peak(qcd.QCD_FP32)
+        out["sap_alu"] = {"achieved": fl / (sap[0]["total_ms"] * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                          "frac": fl / (sap[0]["total_ms"] * 1e-3) / 1e12 / peak}
+    return out
 
 
 def gradient_study(qcd, synth, torch, devn, stream):

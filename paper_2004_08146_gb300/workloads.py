@@ -15,17 +15,18 @@ WORKLOADS = {
     # 16 x 8^3, two-level MG with 2^4 aggregates, Nv = 8, SAP on 2^4 blocks, 50 pairs
     "c2_16x8c3": dict(dims=(16, 8, 8, 8), eps=0.5, csw=1.5, m0=-0.85, seed=1002, k=50,
                       use_mg=1, agg=(2, 2, 2, 2), nv=8, sap=(2, 2, 2, 2), target=1e-2),
-    # 32 x 16^3, two-level MG with 4^4 aggregates, Nv = 20, 100 pairs with 8
-    # targets per outer iteration and P rebuilt every 20 locks.  16 targets fit
-    # only m_max = 48 (basis plus block <= 64): one outer step between
-    # restarts, and on this field's dense band of 100 eigenvalues (spacing
-    # ~3e-4) such a run skipped one of them.  m0 is NOT
-    # oracle-tuned (the oracle's GD does not finish at 1.5M unknowns in the
-    # time a tuning grid allows): it is the 16 x 8^3 value, and runs report the
-    # min |lambda| it gives instead of the 5e-3 target.
+    # 32 x 16^3, two-level MG with 4^4 aggregates, Nv = 20, 100 pairs with 16
+    # shifted systems (targets) per outer iteration, m_min 30 and m_max 50
+    # (Table 2), P rebuilt every 20 locks.
     "c3_32x16c3": dict(dims=(32, 16, 16, 16), eps=0.6, csw=1.7, m0=-0.85, seed=1003, k=100,
-                       use_mg=1, agg=(4, 4, 4, 4), nv=20, sap=(2, 2, 2, 2), target=5e-3, m0_tuned=False,
-                       block=8, m_min=30, m_max=48, update_every=20),
+                       use_mg=1, agg=(4, 4, 4, 4), nv=20, sap=(2, 2, 2, 2), target=5e-3,
+                       block=16, m_min=30, m_max=50, update_every=20),
+    # 64 x 32^3 (2.1 M sites, 25 M unknowns), three-level MG: 4^4 aggregates
+    # (Nv = 24) on the fine lattice, 2^4 aggregates (nv2 = 24) on the coarse
+    # one; 100 pairs with 16 targets per outer iteration, m_min 30, m_max 50.
+    "c4_64x32c3": dict(dims=(64, 32, 32, 32), eps=0.6, csw=1.9, m0=-0.85, seed=1004, k=100,
+                       use_mg=1, agg=(4, 4, 4, 4), nv=24, sap=(2, 2, 2, 2), target=1e-3,
+                       block=16, m_min=30, m_max=50, update_every=20, levels=3, agg2=(2, 2, 2, 2), nv2=24),
 }
 
 

@@ -37,7 +37,7 @@ SPECS = {
     "c4_64x32c3": dict(dims=(64, 32, 32, 32), eps=0.6, csw=1.9, seed=1004, target=1e-3),
 }
 PROXIES = [(4, 4, 4, 4), (8, 4, 4, 4)]
-GRID = [round(-0.60 - 0.05 * i, 2) for i in range(13)]     # -0.60 ... -1.20
+GRID = [-0.80, -0.90, -1.00, -1.10, -1.20]
 
 
 def min_abs_lambda(dims, eps, csw, m0, seed):
