@@ -797,29 +797,40 @@ def smoother_sweep(qcd, synth, torch, devn, stream):
 
 
 def stencil_bench(qcd, synth, torch, devn, stream, peak):
+    """Fine Wilson-clover stencil (D - tau Gamma5) on a 64 x 32^3 field (inputs
+    far larger than L2): FP32 and FP64 with one right-hand side, and FP32 with
+    8 and 16 right-hand sides in one launch (links and clover read once per
+    group of right-hand sides).  Algorithmic bytes per site and right-hand side:
+    in + out spinor (48 reals) plus links and clover (144 reals) over the
+    right-hand sides that share them -- 768 B (FP32) and 1536 B (FP64) at one
+    right-hand side, (48 + 144 / nrhs) x 4 B in FP32 with nrhs of them."""
     dims = (64, 32, 32, 32)
     U = synth.gauge_field(dims, 0.6, 1004)
     ctx = qcd.Context(stream=stream.cuda_stream)
     ctx.qcd_set_gauge(U, dims, -0.5, 1.9)
     V = int(np.prod(dims))
     out = {"lattice": "64x32^3", "sites": V}
-    for prec, name, dt, bps in ((1, "fp32", torch.complex64, 768), (0, "fp64", torch.complex128, 1536)):
-        x = torch.randn(V * 12, dtype=dt, device=devn)
+    for prec, name, dt, real, nrhs in ((1, "fp32", torch.complex64, 4, 1), (0, "fp64", torch.complex128, 8, 1),
+                                       (1, "fp32_nrhs8", torch.complex64, 4, 8),
+                                       (1, "fp32_nrhs16", torch.complex64, 4, 16)):
+        x = torch.randn(V * 12 * nrhs, dtype=dt, device=devn)
         y = torch.empty_like(x)
+        taus = [0.0] * nrhs
         for _ in range(3):
-            ctx.qcd_apply(qcd.QCD_OP_D, prec, 1, x, y, [0.0])
-        reps = 20
+            ctx.qcd_apply(qcd.QCD_OP_D, prec, nrhs, x, y, taus)
+        reps = 20 if nrhs == 1 else 5
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            ctx.qcd_apply(qcd.QCD_OP_D, prec, 1, x, y, [0.0])
+            ctx.qcd_apply(qcd.QCD_OP_D, prec, nrhs, x, y, taus)
         e1.record(stream)
         e1.synchronize()
         t = e0.elapsed_time(e1) / reps * 1e-3
-        gbs = bps * V / t / 1e9
-        out[name] = {"us_per_apply": t * 1e6, "gbs": gbs, "frac_hbm": gbs / peak,
-                     "gflops": 1824 * V / t / 1e9, "bytes_per_site": bps}
+        bps = (48.0 + 144.0 / nrhs) * real          # per site and right-hand side
+        gbs = bps * V * nrhs / t / 1e9
+        out[name] = {"nrhs": nrhs, "us_per_apply": t * 1e6, "gbs": gbs, "frac_hbm": gbs / peak,
+                     "gflops": 1824 * V * nrhs / t / 1e9, "bytes_per_site_rhs": bps}
         del x, y
     ctx.close()
     return out

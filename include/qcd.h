@@ -106,6 +106,10 @@ typedef struct qcd_params {
                                 memory; 2 Krylov basis in shared memory; 3 Krylov basis
                                 in global memory (any coarse lattice).  A forced layout
                                 that does not fit returns EINVAL. */
+    int    coarse_tensor;    /* 1 (default): FP32 coarse-stencil applies of the level-1
+                                operator (2 Nv a multiple of 8) on the tensor cores, TF32
+                                inputs split in big + small parts (three products, FP32
+                                accumulation); 0: FP32 FMA units */
 } qcd_params;
 
 typedef struct qcd_solve_info {

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqcd.so")
-UNITS = ["dirac.cu", "blas.cu", "mg.cu", "mg2.cu", "eig.cu", "api.cu", "stats.cu", "krylov.cu"]
+UNITS = ["dirac.cu", "blas.cu", "mg.cu", "mg2.cu", "eig.cu", "api.cu", "stats.cu", "krylov.cu", "ff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -193,6 +193,7 @@ void validate_params(const qcd_params& p) {
     for (int mu = 0; mu < 4; ++mu)
         if (p.agg2[mu] < 1) throw QcdError(QCD_EINVAL, "agg2 extents must be >= 1");
     if (p.coarse_layout < 0 || p.coarse_layout > 3) throw QcdError(QCD_EINVAL, "coarse_layout must be in [0, 3]");
+    if (p.coarse_tensor != 0 && p.coarse_tensor != 1) throw QcdError(QCD_EINVAL, "coarse_tensor must be 0 or 1");
 }
 
 // ------------------------------------------------------------------ linear operators
@@ -532,7 +533,7 @@ void level2_solve(qcd_ctx* ctx, int prec, int op, int nrhs, const void* rc, void
     if (!done) {
         std::vector<double> tv(tau, tau + nrhs);
         OpFn A2 = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int*) {
-            coarse_apply(ctx->c2, prec, op, nrhs, in, out, tv.data(), ctx->st);
+            coarse_apply(ctx->c2, prec, op, nrhs, in, out, tv.data(), ctx->st, ctx->p.coarse_tensor != 0);
         };
         gmres_batched(ctx, prec, nco2, nrhs, A2, nullptr, rc, xc, ctx->p.coarse_tol, ctx->p.coarse_maxiter, "l2g");
     }
@@ -556,7 +557,7 @@ void level1_cycle(qcd_ctx* ctx, int prec, int op, int nrhs, const void* r1, void
     if (ctx->p.nu2 <= 0) return;
     std::vector<double> tv(tau, tau + nrhs);
     OpFn A1 = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int*) {
-        coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st);
+        coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st, ctx->p.coarse_tensor != 0);
     };
     void* w = ctx->buf("l1c.w", nco * nrhs * esz(prec));
     void* e = ctx->buf("l1c.e", nco * nrhs * esz(prec));
@@ -567,7 +568,7 @@ void level1_cycle(qcd_ctx* ctx, int prec, int op, int nrhs, const void* r1, void
     }
     for (int s = 0; s < ctx->p.nu2; ++s) {
         // w = r1 - A1 x1
-        coarse_apply(c, prec, op, nrhs, x1, w, tv.data(), ctx->st);
+        coarse_apply(c, prec, op, nrhs, x1, w, tv.data(), ctx->st, ctx->p.coarse_tensor != 0);
         blas_axpby(prec, make_double2(1, 0), r1, make_double2(-1, 0), w, nco * nrhs, ctx->st);
         gmres_dev(ctx, prec, nco, nrhs, A1, nullptr, w, e, 0.0, ctx->p.gmres_smooth_iters, "l1s", act);
         blas_scale_dev(prec, e, x1, one, nrhs, nco, false, true, ctx->st, act);
@@ -592,7 +593,7 @@ void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void
         // host looks at the active flags every 4 steps to stop early.
         std::vector<double> tv(tau, tau + nrhs);
         OpFn A1 = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int*) {
-            coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st);
+            coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st, ctx->p.coarse_tensor != 0);
         };
         OpFn M1 = [ctx, prec, op, nrhs, tv, taud, act](const void* in, void* out, const int* a) {
             level1_cycle(ctx, prec, op, nrhs, in, out, tv.data(), taud, a ? a : act);
@@ -630,7 +631,7 @@ void mg_cycle_impl(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void
     if (!done) {
         std::vector<double> tv(tau, tau + nrhs);
         OpFn Ac = [ctx, prec, op, nrhs, tv](const void* in, void* out, const int*) {
-            coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st);
+            coarse_apply(ctx->c, prec, op, nrhs, in, out, tv.data(), ctx->st, ctx->p.coarse_tensor != 0);
         };
         gmres_batched(ctx, prec, nco, nrhs, Ac, nullptr, rc, xc, ctx->p.coarse_tol, ctx->p.coarse_maxiter, "coarse");
     }
@@ -870,46 +871,6 @@ double shifted_solve_impl(qcd_ctx* ctx, int nrhs, const double2* b, double2* x, 
 }
 
 // ------------------------------------------------------------------ GD-lambda-AMG
-// Tall-skinny basis transform in place: A[j] <- sum_i C[i + j m] A[i] for
-// j < p <= m, FP64 (thick restart V <- V C).  Each CTA stages a tile of
-// kTileRows rows of all m vectors in shared memory, then writes the p new
-// vectors' rows over them: rows are independent, so no second basis copy is
-// needed.  A warp computes one output vector for the tile's 32 rows (one row
-// per lane), so every coefficient C[i + j m] is a warp-wide broadcast.
-constexpr int kTileRows = 32;
-__global__ void __launch_bounds__(256) basis_transform_inplace_kernel(double2* __restrict__ A, int m,
-                                                                      const double2* __restrict__ C, int p, size_t n) {
-    extern __shared__ double2 tile[];   // [m][kTileRows]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const size_t ntiles = (n + kTileRows - 1) / kTileRows;
-    for (size_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const size_t k0 = t * kTileRows;
-        const int rows = (int)min((size_t)kTileRows, n - k0);
-        for (int e = threadIdx.x; e < m * kTileRows; e += blockDim.x) {
-            const int i = e / kTileRows, r = e % kTileRows;
-            tile[e] = r < rows ? A[(size_t)i * n + k0 + r] : make_double2(0, 0);
-        }
-        __syncthreads();
-        for (int j = warp; j < p; j += nw) {
-            double2 acc = make_double2(0, 0);
-            for (int i = 0; i < m; ++i) acc += __ldg(&C[(size_t)j * m + i]) * tile[i * kTileRows + lane];
-            if (lane < rows) A[(size_t)j * n + k0 + lane] = acc;
-        }
-        __syncthreads();
-    }
-}
-void basis_transform_inplace(double2* A, int m, const double2* C, int p, size_t n, cudaStream_t st) {
-    const size_t sm = (size_t)m * kTileRows * sizeof(double2);
-    if (sm > 48 * 1024)
-        CK(cudaFuncSetAttribute(basis_transform_inplace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t ntiles = (n + kTileRows - 1) / kTileRows;
-    const int grid = (int)std::min<size_t>(ntiles, (size_t)std::max(1, sms) * 4);
-    KTimer kt("basis_transform", (double)(m + p) * n * 16, 8.0 * m * p * n, st);
-    basis_transform_inplace_kernel<<<grid, 256, sm, st>>>(A, m, C, p, n);
-}
 // G[i][m] = d1[i], G[m][i] = conj d1[i]; Hm[i][m] = d2[i]; Hm[m][i] = conj d2[i]  (ld = column stride).
 // H = W^H V = V^H Q V is Hermitian because Q is (Sec. 2), so its new row
 // is the conjugate of its new column.
@@ -948,24 +909,6 @@ __global__ void householder_vector_kernel(const double2* __restrict__ s, int m, 
     for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) hw[i] = nn * s[i];
     __syncthreads();
     if (threadIdx.x == 0) hw[m] = make_double2(2.0 / ww, 0.0);
-}
-// Out[:, j-1] = In[:, j] - f conj(w_j) (In w) for j = 1..m-1, i.e. In Hh
-// without its first column; the pair (V, W) is selected by blockIdx.y.
-// Row k of In w depends on row k of In only, so each thread finishes its
-// rows in place: it reads In[j][k] before it writes position j-1.
-__global__ void householder_deflate_kernel(double2* __restrict__ A0, double2* __restrict__ A1, int m, size_t n,
-                                           const double2* __restrict__ hw) {
-    __shared__ double2 w[kMaxBasis + 1];
-    for (int i = threadIdx.x; i <= m; i += blockDim.x) w[i] = hw[i];
-    __syncthreads();
-    double2* A = blockIdx.y ? A1 : A0;
-    const double f = w[m].x;
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        double2 y = make_double2(0, 0);
-        for (int i = 0; i < m; ++i) y += w[i] * A[(size_t)i * n + k];
-        y = f * y;
-        for (int j = 1; j < m; ++j) A[(size_t)(j - 1) * n + k] = A[(size_t)j * n + k] - conj(w[j]) * y;
-    }
 }
 // out = Hh M Hh restricted to rows and columns 1..m-1 (M: G or H, ld = ld):
 //   out[i-1][j-1] = M_ij - f w_i conj(b_j) - f a_i conj(w_j) + f^2 g w_i conj(w_j)
@@ -1007,7 +950,10 @@ struct GD {
     qcd_ctx* ctx;
     size_t n;
     int mcap, kcap;
-    double2 *V, *W, *X, *G, *Hm, *Gt, *Hmt, *S, *work, *C, *dots, *part, *u, *Qu, *R, *T, *tmp;
+    // V, W = Q V, X and u, Qu, r are stored double-float (QCD_FF, 16 bytes per
+    // complex number); R, T and tmp, tmp2 are FP64
+    double2 *V, *W, *X, *G, *Hm, *Gt, *Hmt, *S, *work, *C, *dots, *part, *u, *Qu, *rff, *R, *T, *tmp, *tmp2;
+    double2 *ffc, *ffw;   // double-float copies of transform / reflector coefficients
     double* mu;
     double* mu_ref;   // refined eigenvalues of the targets
     int* status;
@@ -1031,7 +977,9 @@ struct GD {
         S = B("S", (size_t)mcap * mcap); work = B("work", (size_t)(6 + block) * mcap * mcap); C = B("C", (size_t)mcap * mcap);
         dots = B("dots", (size_t)4 * (mcap + kcap + 8));
         part = B("part", (size_t)(mcap + kcap + 8) * 64);
-        u = B("u", n); Qu = B("Qu", n); R = B("R", (size_t)block * n); T = B("T", (size_t)block * n); tmp = B("tmp", n);
+        u = B("u", n); Qu = B("Qu", n); rff = B("rff", n); R = B("R", (size_t)block * n); T = B("T", (size_t)block * n);
+        tmp = B("tmp", n); tmp2 = B("tmp2", n);
+        ffc = B("ffc", (size_t)mcap * mcap); ffw = B("ffw", (size_t)mcap + 1);
         mu = (double*)ctx->buf("gd.mu", mcap * sizeof(double));
         mu_ref = (double*)ctx->buf("gd.mu_ref", mcap * sizeof(double));
         status = (int*)ctx->buf("gd.status", 4 * sizeof(int));
@@ -1061,11 +1009,11 @@ struct GD {
         cudaStream_t st = ctx->st;
         double2* v = V + (size_t)m * n;
         double2* dx = dots + m + 1;
-        blas_copy(QCD_FP64, t, v, n, st);
-        blas_multidot(QCD_FP64, V, m + 1, n, v, 1, n, dots, part, ctx->dot_counters(m + 1), st);
-        if (nlock > 0) blas_multidot(QCD_FP64, X, nlock, n, v, 1, n, dx, part, ctx->dot_counters(nlock), st);
-        if (m > 0) blas_multiaxpy(QCD_FP64, V, m, n, dots, -1.0, v, 1, n, st);
-        if (nlock > 0) blas_multiaxpy(QCD_FP64, X, nlock, n, dx, -1.0, v, 1, n, st);
+        blas_convert(QCD_FP64, t, QCD_FF, v, n, st);
+        blas_multidot(QCD_FF, V, m + 1, n, v, 1, n, dots, part, ctx->dot_counters(m + 1), st);
+        if (nlock > 0) blas_multidot(QCD_FF, X, nlock, n, v, 1, n, dx, part, ctx->dot_counters(nlock), st);
+        if (m > 0) blas_multiaxpy(QCD_FF, V, m, n, dots, -1.0, v, 1, n, st);
+        if (nlock > 0) blas_multiaxpy(QCD_FF, X, nlock, n, dx, -1.0, v, 1, n, st);
         const double2* h = ctx->fetch(dots, m + 1 + nlock);
         const double t0 = h[m].x;
         double c2 = 0.0;
@@ -1074,23 +1022,26 @@ struct GD {
         double nt2 = t0 - c2;
         if (!(nt2 >= 0.5 * t0)) {
             if (m > 0) {
-                blas_multidot(QCD_FP64, V, m, n, v, 1, n, dots, part, ctx->dot_counters(m), st);
-                blas_multiaxpy(QCD_FP64, V, m, n, dots, -1.0, v, 1, n, st);
+                blas_multidot(QCD_FF, V, m, n, v, 1, n, dots, part, ctx->dot_counters(m), st);
+                blas_multiaxpy(QCD_FF, V, m, n, dots, -1.0, v, 1, n, st);
             }
             if (nlock > 0) {
-                blas_multidot(QCD_FP64, X, nlock, n, v, 1, n, dots, part, ctx->dot_counters(nlock), st);
-                blas_multiaxpy(QCD_FP64, X, nlock, n, dots, -1.0, v, 1, n, st);
+                blas_multidot(QCD_FF, X, nlock, n, v, 1, n, dots, part, ctx->dot_counters(nlock), st);
+                blas_multiaxpy(QCD_FF, X, nlock, n, dots, -1.0, v, 1, n, st);
             }
-            blas_multidot(QCD_FP64, v, 1, n, v, 1, n, dots, part, ctx->dot_counters(1), st);
+            blas_multidot(QCD_FF, v, 1, n, v, 1, n, dots, part, ctx->dot_counters(1), st);
             nt2 = ctx->fetch(dots, 1)[0].x;
         }
         const double nt = std::sqrt(std::max(nt2, 0.0));
         if (!(nt > 1e-12) || !std::isfinite(nt)) return false;
-        blas_axpby(QCD_FP64, make_double2(0, 0), v, make_double2(1.0 / nt, 0), v, n, st);
-        applyQ(v, W + (size_t)m * n);
+        blas_axpby(QCD_FF, make_double2(0, 0), v, make_double2(1.0 / nt, 0), v, n, st);
+        // W[m] = Q v in FP64 (v and W are stored double-float)
+        blas_convert(QCD_FF, v, QCD_FP64, tmp, n, st);
+        applyQ(tmp, tmp2);
+        blas_convert(QCD_FP64, tmp2, QCD_FF, W + (size_t)m * n, n, st);
         // new Gram column / row
-        blas_multidot(QCD_FP64, W, m + 1, n, W + (size_t)m * n, 1, n, dots, part, ctx->dot_counters(m + 1), st);
-        blas_multidot(QCD_FP64, W, m + 1, n, v, 1, n, dots + mcap, part, ctx->dot_counters(m + 1), st);
+        blas_multidot(QCD_FF, W, m + 1, n, W + (size_t)m * n, 1, n, dots, part, ctx->dot_counters(m + 1), st);
+        blas_multidot(QCD_FF, W, m + 1, n, v, 1, n, dots + mcap, part, ctx->dot_counters(m + 1), st);
         KTimer kt("gram_update", 0.0, 0.0, st);
         gram_update_kernel<<<1, kMaxBasis + 1, 0, st>>>(G, Hm, mcap, m, dots, dots + mcap);
         check_launch("add_vector");
@@ -1099,7 +1050,7 @@ struct GD {
     }
     // appends the converged unit vector u to X
     void lock_vector(const double2* uv) {
-        blas_copy(QCD_FP64, uv, X + (size_t)nlock * n, n, ctx->st);
+        blas_copy(QCD_FF, uv, X + (size_t)nlock * n, n, ctx->st);
         ++nlock;
     }
     // harmonic Ritz pairs of the current basis; returns theta sorted by |theta| with the column index
@@ -1129,8 +1080,8 @@ struct GD {
     // replace the basis by V C (m x p), W C and the Gram matrices by C^H G C
     void transform(const double2* Cm, int p) {
         cudaStream_t st = ctx->st;
-        basis_transform_inplace(V, m, Cm, p, n, st);
-        basis_transform_inplace(W, m, Cm, p, n, st);
+        ff_transform_inplace(V, m, Cm, p, n, ffc, st);
+        ff_transform_inplace(W, m, Cm, p, n, ffc, st);
         small_gram_transform(G, m, mcap, Cm, p, Gt, mcap, work, st);
         small_gram_transform(Hm, m, mcap, Cm, p, Hmt, mcap, work, st);
         std::swap(G, Gt);
@@ -1150,11 +1101,7 @@ struct GD {
             householder_vector_kernel<<<1, 64, 0, st>>>(s, m, hw);
             householder_gram_kernel<<<2, 256, 0, st>>>(G, Gt, Hm, Hmt, m, mcap, hw);
         }
-        {
-            const int gx = (int)std::min<size_t>((n + 255) / 256, 1216);
-            KTimer kt("householder_deflate", (double)(4 * m - 2) * n * 16, 16.0 * m * n * 2, st);
-            householder_deflate_kernel<<<dim3(gx, 2), 256, 0, st>>>(V, W, m, n, hw);
-        }
+        ff_deflate(V, W, m, n, hw, ffw, st);
         std::swap(G, Gt);
         std::swap(Hm, Hmt);
         check_launch("deflate");
@@ -1257,22 +1204,23 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
             int nr = 0;
             for (int ti : tg) {
                 const double2* s = gd.S + (size_t)col[ti] * gd.m;   // column of S (ld = m)
-                blas_zero(QCD_FP64, gd.u, n, st);
-                blas_zero(QCD_FP64, gd.Qu, n, st);
-                blas_multiaxpy(QCD_FP64, gd.V, gd.m, n, s, 1.0, gd.u, 1, n, st);
-                blas_multiaxpy(QCD_FP64, gd.W, gd.m, n, s, 1.0, gd.Qu, 1, n, st);
-                blas_multidot(QCD_FP64, gd.u, 1, n, gd.u, 1, n, gd.dots, gd.part, gd.ctx->dot_counters(1), st);
-                blas_multidot(QCD_FP64, gd.u, 1, n, gd.Qu, 1, n, gd.dots + 1, gd.part, gd.ctx->dot_counters(1), st);
+                blas_zero(QCD_FF, gd.u, n, st);
+                blas_zero(QCD_FF, gd.Qu, n, st);
+                blas_multiaxpy(QCD_FF, gd.V, gd.m, n, s, 1.0, gd.u, 1, n, st);
+                blas_multiaxpy(QCD_FF, gd.W, gd.m, n, s, 1.0, gd.Qu, 1, n, st);
+                blas_multidot(QCD_FF, gd.u, 1, n, gd.u, 1, n, gd.dots, gd.part, gd.ctx->dot_counters(1), st);
+                blas_multidot(QCD_FF, gd.u, 1, n, gd.Qu, 1, n, gd.dots + 1, gd.part, gd.ctx->dot_counters(1), st);
                 const double2* h = ctx->fetch(gd.dots, 2);
                 const double uu = h[0].x;
                 const double rho = h[1].x / uu;
                 const double iu = 1.0 / std::sqrt(uu);
                 double2* rj = gd.R + (size_t)nr * n;
                 // r = (Qu - rho u)/||u|| ; u <- u/||u||
-                blas_copy(QCD_FP64, gd.Qu, rj, n, st);
-                blas_axpby(QCD_FP64, make_double2(-rho * iu, 0), gd.u, make_double2(iu, 0), rj, n, st);
-                blas_axpby(QCD_FP64, make_double2(0, 0), gd.u, make_double2(iu, 0), gd.u, n, st);
-                blas_multidot(QCD_FP64, rj, 1, n, rj, 1, n, gd.dots, gd.part, gd.ctx->dot_counters(1), st);
+                blas_copy(QCD_FF, gd.Qu, gd.rff, n, st);
+                blas_axpby(QCD_FF, make_double2(-rho * iu, 0), gd.u, make_double2(iu, 0), gd.rff, n, st);
+                blas_axpby(QCD_FF, make_double2(0, 0), gd.u, make_double2(iu, 0), gd.u, n, st);
+                blas_multidot(QCD_FF, gd.rff, 1, n, gd.rff, 1, n, gd.dots, gd.part, gd.ctx->dot_counters(1), st);
+                blas_convert(QCD_FF, gd.rff, QCD_FP64, rj, n, st);
                 const double2* hr = ctx->fetch(gd.dots, 1);
                 const double rn = std::sqrt(std::max(hr[0].x, 0.0));
                 if (rn <= tol) {
@@ -1285,7 +1233,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                         for (int q = 1; q < gd.nlock; ++q)
                             if (std::fabs(gd.lam[q]) > std::fabs(gd.lam[big])) big = q;
                         if (std::fabs(rho) < std::fabs(gd.lam[big])) {
-                            blas_copy(QCD_FP64, gd.u, gd.X + (size_t)big * n, n, st);
+                            blas_copy(QCD_FF, gd.u, gd.X + (size_t)big * n, n, st);
                             gd.lam[big] = rho;
                             gd.lres[big] = rn;
                         }
@@ -1320,7 +1268,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                 std::vector<int> pick(ord.begin(), ord.begin() + ctx->n_test);
                 std::sort(pick.begin(), pick.end());
                 for (int i = 0; i < ctx->n_test; ++i)
-                    blas_copy(QCD_FP64, gd.X + (size_t)pick[i] * n, vbuf + (size_t)i * n, n, st);
+                    blas_convert(QCD_FF, gd.X + (size_t)pick[i] * n, QCD_FP64, vbuf + (size_t)i * n, n, st);
                 build_from_vectors(ctx, vbuf, ctx->n_test, ctx->c.B.b);
                 locks_since_update = 0;
                 ++updates;
@@ -1372,7 +1320,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
     for (int i = 0; i < nout; ++i) {
         lambda[i] = gd.lam[ord[i]];
         maxres = std::max(maxres, gd.lres[ord[i]]);
-        if (Vout) blas_copy(QCD_FP64, gd.X + (size_t)ord[i] * n, Vout + (size_t)i * n, n, st);
+        if (Vout) blas_convert(QCD_FF, gd.X + (size_t)ord[i] * n, QCD_FP64, Vout + (size_t)i * n, n, st);
     }
     for (int i = nout; i < k; ++i) lambda[i] = NAN;
     CK(cudaStreamSynchronize(st));
@@ -1449,6 +1397,8 @@ void qcd_default_params(qcd_params* p) {
     p->nv2 = 8;
     for (int mu = 0; mu < 4; ++mu) p->agg2[mu] = 2;
     p->nu2 = 2;
+    p->coarse_layout = 0;
+    p->coarse_tensor = 1;
 }
 
 int qcd_create(qcd_ctx** out, const qcd_params* p, void* stream) {
@@ -1737,7 +1687,7 @@ int qcd_coarse_apply(qcd_ctx* ctx, int op, int prec, int nrhs, const void* x, vo
         require_mg(ctx);
         if (nrhs < 1 || nrhs > kMaxRhs || !x || !y || !tau) throw QcdError(QCD_EINVAL, "bad arguments");
         if (prec == QCD_FP64) ensure_coarse64(ctx);
-        coarse_apply(ctx->c, prec, op, nrhs, x, y, tau, ctx->st);
+        coarse_apply(ctx->c, prec, op, nrhs, x, y, tau, ctx->st, ctx->p.coarse_tensor != 0);
         check_launch("coarse apply");
         return QCD_OK;
     });

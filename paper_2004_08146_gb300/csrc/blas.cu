@@ -9,7 +9,7 @@ namespace qcd {
 namespace {
 constexpr int kThreads = 256;
 
-inline size_t esz_of(int prec) { return prec == QCD_FP64 ? sizeof(double2) : sizeof(float2); }
+inline size_t esz_of(int prec) { return prec == QCD_FP32 ? sizeof(float2) : sizeof(double2); }   // FF: 16 bytes
 
 inline int grid_for(size_t n, int th = kThreads) {
     size_t g = (n + th - 1) / th;
@@ -182,14 +182,15 @@ __global__ void gaussian_kernel(double2* x, size_t n, unsigned long long seed, u
 
 void blas_zero(int prec, void* x, size_t n, cudaStream_t st) {
     KTimer kt("blas_zero", (double)n * esz_of(prec), 0.0, st);
-    if (prec == QCD_FP64) zero_kernel<double2><<<grid_for(n), kThreads, 0, st>>>((double2*)x, n);
+    if (prec != QCD_FP32) zero_kernel<double2><<<grid_for(n), kThreads, 0, st>>>((double2*)x, n);
     else zero_kernel<float2><<<grid_for(n), kThreads, 0, st>>>((float2*)x, n);
 }
 void blas_copy(int prec, const void* x, void* y, size_t n, cudaStream_t st) {
-    cudaMemcpyAsync(y, x, n * (prec == QCD_FP64 ? sizeof(double2) : sizeof(float2)), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(y, x, n * esz_of(prec), cudaMemcpyDeviceToDevice, st);
 }
 void blas_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, cudaStream_t st) {
     if (prec_in == prec_out) { blas_copy(prec_in, x, y, n, st); return; }
+    if (prec_in == QCD_FF || prec_out == QCD_FF) { ff_convert(prec_in, x, prec_out, y, n, st); return; }
     KTimer kt("blas_convert", (double)n * (esz_of(prec_in) + esz_of(prec_out)), 0.0, st);
     if (prec_in == QCD_FP64)
         convert_kernel<double2, float2><<<grid_for(n), kThreads, 0, st>>>((const double2*)x, (float2*)y, n);
@@ -199,6 +200,10 @@ void blas_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, c
 void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const void* w, int nrhs, size_t n,
                    double2* dots, double2* partial, unsigned* counters, cudaStream_t st, const int* act) {
     if (nvec <= 0) return;
+    if (prec == QCD_FF) {
+        ff_multidot(X, nvec, xstride_vec, w, nrhs, n, dots, partial, counters, st, act);
+        return;
+    }
     // enough CTAs to fill the GPU (about 4 per SM), at least 2048 elements each
     int nsplit = 608 / (nvec * nrhs);
     if (nsplit > 64) nsplit = 64;
@@ -217,6 +222,10 @@ void blas_multidot(int prec, const void* X, int nvec, size_t xstride_vec, const 
 void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const double2* c, double sign, void* w,
                     int nrhs, size_t n, cudaStream_t st, const int* act) {
     if (nvec <= 0) return;
+    if (prec == QCD_FF) {
+        ff_multiaxpy(X, nvec, xstride_vec, c, sign, w, nrhs, n, st, act);
+        return;
+    }
     size_t total = n * nrhs;
     KTimer kt(prec == QCD_FP64 ? "multiaxpy_f64" : "multiaxpy_f32", (double)(nvec + 2) * nrhs * n * esz_of(prec),
               8.0 * nvec * nrhs * n, st);
@@ -229,6 +238,11 @@ void blas_multiaxpy(int prec, const void* X, int nvec, size_t xstride_vec, const
 }
 void blas_scale_dev(int prec, const void* x, void* y, const double2* alpha, int nrhs, size_t n, bool invert_real,
                     bool accumulate, cudaStream_t st, const int* act) {
+    if (prec == QCD_FF) {
+        if (invert_real) return;   // not used with double-float data
+        ff_scale_dev(x, y, alpha, nrhs, n, accumulate, st, act);
+        return;
+    }
     size_t total = n * nrhs;
     KTimer kt("blas_scale", (double)total * (accumulate ? 3 : 2) * esz_of(prec), 0.0, st);
     if (prec == QCD_FP64)
@@ -239,6 +253,7 @@ void blas_scale_dev(int prec, const void* x, void* y, const double2* alpha, int 
                                                                             nrhs, n, invert_real, accumulate, act);
 }
 void blas_gamma5(int prec, const void* x, void* y, size_t nsites, cudaStream_t st) {
+    if (prec == QCD_FF) { ff_gamma5(x, y, nsites, st); return; }
     size_t total = nsites * 12;
     KTimer kt("blas_gamma5", (double)total * 2 * esz_of(prec), 0.0, st);
     if (prec == QCD_FP64) gamma5_kernel<double2><<<grid_for(total), kThreads, 0, st>>>((const double2*)x, (double2*)y, nsites);
@@ -249,6 +264,7 @@ void blas_gaussian(double2* x, size_t n, unsigned long long seed, unsigned long 
     gaussian_kernel<<<grid_for(n), kThreads, 0, st>>>(x, n, seed, offset);
 }
 void blas_axpby(int prec, double2 a, const void* x, double2 b, void* y, size_t n, cudaStream_t st) {
+    if (prec == QCD_FF) { ff_axpby(a, x, b, y, n, st); return; }
     KTimer kt("blas_axpby", (double)n * 3 * esz_of(prec), 0.0, st);
     if (prec == QCD_FP64)
         axpby_kernel<double2, double><<<grid_for(n), kThreads, 0, st>>>(a, (const double2*)x, b, (double2*)y, n);

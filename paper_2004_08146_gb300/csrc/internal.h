@@ -137,6 +137,26 @@ void blas_gaussian(double2* x, size_t n, unsigned long long seed, unsigned long 
 // y = a*x + b*y (host scalars), complex
 void blas_axpby(int prec, double2 a, const void* x, double2 b, void* y, size_t n, cudaStream_t st);
 
+// ------------------------------------------------------------------ double-float (ff.cu)
+// Internal storage precision of the Davidson basis: complex numbers as two
+// FP32 pairs (hi + lo, 16 bytes, ~2^-48 relative), arithmetic by error-free
+// transformations on the FP32 units.  Not an ABI precision.
+constexpr int QCD_FF = 2;
+// FP64 <-> FF, FF -> FP32 (hi + lo rounded), FP32 -> FF
+void ff_convert(int prec_in, const void* x, int prec_out, void* y, size_t n, cudaStream_t st);
+void ff_multidot(const void* X, int nvec, size_t xstride_vec, const void* w, int nrhs, size_t n, double2* dots,
+                 double2* partial, unsigned* counters, cudaStream_t st, const int* act);
+void ff_multiaxpy(const void* X, int nvec, size_t xstride_vec, const double2* c, double sign, void* w, int nrhs,
+                  size_t n, cudaStream_t st, const int* act);
+void ff_scale_dev(const void* x, void* y, const double2* alpha, int nrhs, size_t n, bool accumulate, cudaStream_t st,
+                  const int* act);
+void ff_axpby(double2 a, const void* x, double2 b, void* y, size_t n, cudaStream_t st);
+void ff_gamma5(const void* x, void* y, size_t nsites, cudaStream_t st);
+// A[j] <- sum_i C[i + j m] A[i] (j < p <= m) in place; cf_scratch: m * p * 16 bytes
+void ff_transform_inplace(void* A, int m, const double2* C, int p, size_t n, void* cf_scratch, cudaStream_t st);
+// Householder deflation of the pair (A0, A1) by the reflector hw (m + 1 entries); wf_scratch (m + 1) * 16 bytes
+void ff_deflate(void* A0, void* A1, int m, size_t n, const double2* hw, void* wf_scratch, cudaStream_t st);
+
 // ------------------------------------------------------------------ kernels (mg.cu)
 void mg_build_P(const FineOp& f, Coarse& c, const double2* vecs, int nvec, cudaStream_t st);
 void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st, bool fp32_only = false);
@@ -144,8 +164,10 @@ void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const voi
                  const int* act = nullptr);
 void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* xc, void* x, bool accumulate,
                 cudaStream_t st, const int* act = nullptr);
+// tensor: FP32 applies with 2 Nv a multiple of 8 run on the tensor cores
+// (3xTF32); otherwise, and for FP64, on the CUDA cores
 void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, void* y, const double* tau,
-                  cudaStream_t st);
+                  cudaStream_t st, bool tensor = true);
 
 // ------------------------------------------------------------------ kernels (mg2.cu)
 // Third level: c2.B blocks the level-1 lattice c1.gc; P2 [b2][chi][j][l][i < Nv1]

@@ -1,6 +1,8 @@
 // Multigrid kernels: chirality-split aggregation P (Sec. 2, above Eq. 2.9),
 // restriction P^H and prolongation P (Eq. 2.8), the Galerkin coarse stencil
 // D_c = P^H D P (Eq. 2.8, 2.9) and the SAP block solves of Eq. 2.10.
+#include <algorithm>
+
 #include "internal.h"
 #include "dirac.cuh"
 
@@ -344,6 +346,128 @@ __global__ void coarse_apply_mrhs_kernel(Geom gc, int nc, const Z* __restrict__ 
         else { o = sg * o; o -= tj * xv; }
         y[(size_t)j * vstride + (size_t)s * nc + r] = o;
     }
+}
+
+// Tensor-core coarse stencil (FP32 data, 3xTF32 products): per coarse site
+// and chunk of kTcR right-hand sides, the stencil is one real GEMM
+//   [Re y; Im y] (2nc x R) = sum_d [[Re A_d, -Im A_d], [Im A_d, Re A_d]] (2nc x 2nc)
+//                            [Re x_d; Im x_d] (2nc x R),
+// x_d the neighbour in direction d.  Each warp owns a 16-row tile of the
+// result and runs mma.sync m16n8k8 (TF32 in, FP32 accumulate) over K = 9 x 2nc;
+// every operand is split as big + small TF32 parts and the three products
+// small*big + big*small + big*big keep FP32-level accuracy.  The neighbour
+// vectors are staged once ([d][k][r], padded rows: conflict-free fragment
+// loads); the blocks A_d one direction at a time.  Needs nc % 8 == 0.
+constexpr int kTcR = 16;
+constexpr int kTcXs = 24;   // padded row stride of the staged vectors (floats)
+
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& big, uint32_t& small) {
+    big = tf32_of(x);
+    small = tf32_of(x - __uint_as_float(big));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// column stride of the staged block (complex entries): 2 x stride = 16 mod 32
+// words, so the four columns of a fragment load fall on disjoint bank halves
+__host__ __device__ inline int tc_astride(int nc) { return nc + (24 - nc % 16) % 16; }
+
+__global__ void coarse_apply_tc_kernel(Geom gc, int nc, const float2* __restrict__ A, const float2* __restrict__ x,
+                                       float2* __restrict__ y, int op, Shifts tau, int nrhs) {
+    extern __shared__ __align__(16) float tsm[];
+    const int n2 = 2 * nc, astride = tc_astride(nc);
+    float* Xs = tsm;                                               // [9][2nc][kTcXs]
+    float2* As = reinterpret_cast<float2*>(Xs + (size_t)9 * n2 * kTcXs);   // [nc cols][astride]
+    float* Ys = reinterpret_cast<float*>(As);                      // [2nc][kTcR], after the last direction
+    __shared__ int nbr[9];
+    const int s = blockIdx.x, j0 = blockIdx.y * kTcR;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const size_t vstride = (size_t)gc.V * nc;
+    if (tid < 9) {
+        int c[4];
+        site_coords(gc, s, c);
+        int sn = s;
+        if (tid > 0) {
+            const int mu = (tid - 1) & 3, step = tid <= 4 ? 1 : -1;
+            c[mu] = (c[mu] + step + gc.L[mu]) % gc.L[mu];
+            sn = site_index(gc, c);
+        }
+        nbr[tid] = sn;
+    }
+    __syncthreads();
+    for (int e = tid; e < 9 * nc * kTcR; e += blockDim.x) {
+        const int col = e % nc, r = (e / nc) % kTcR, d = e / (nc * kTcR);
+        float2 v = make_float2(0.f, 0.f);
+        if (j0 + r < nrhs) v = x[(size_t)(j0 + r) * vstride + (size_t)nbr[d] * nc + col];
+        Xs[((size_t)d * n2 + col) * kTcXs + r] = v.x;
+        Xs[((size_t)d * n2 + nc + col) * kTcXs + r] = v.y;
+    }
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    const int row0 = 16 * warp;
+    for (int d = 0; d < 9; ++d) {
+        __syncthreads();   // staging done / previous block no longer read
+        const float2* Ad = A + ((size_t)s * 9 + d) * nc * nc;
+        for (int e = tid; e < nc * nc; e += blockDim.x) As[(e / nc) * astride + (e % nc)] = __ldg(Ad + e);
+        __syncthreads();
+        const float* Xd = Xs + (size_t)d * n2 * kTcXs;
+        for (int k0 = 0; k0 < n2; k0 += 8) {
+            uint32_t ab[4], as_[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rho = row0 + g + (i & 1) * 8, kap = k0 + t + (i >> 1) * 4;
+                const bool rim = rho >= nc, kim = kap >= nc;
+                const float2 v = As[(kim ? kap - nc : kap) * astride + (rim ? rho - nc : rho)];
+                const float val = rim == kim ? v.x : (rim ? v.y : -v.y);
+                tf32_split(val, ab[i], as_[i]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t bb0, bs0, bb1, bs1;
+                tf32_split(Xd[(size_t)(k0 + t) * kTcXs + 8 * nt + g], bb0, bs0);
+                tf32_split(Xd[(size_t)(k0 + t + 4) * kTcXs + 8 * nt + g], bb1, bs1);
+                mma_tf32(acc[nt], as_, bb0, bb1);
+                mma_tf32(acc[nt], ab, bs0, bs1);
+                mma_tf32(acc[nt], ab, bb0, bb1);
+            }
+        }
+    }
+    __syncthreads();   // the last block is no longer read: Ys reuses its space
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int rho = row0 + g + (i >> 1) * 8, col = 8 * nt + 2 * t + (i & 1);
+            Ys[rho * kTcR + col] = acc[nt][i];
+        }
+    __syncthreads();
+    for (int e = tid; e < nc * kTcR; e += blockDim.x) {
+        const int row = e % nc, r = e / nc, j = j0 + r;
+        if (j >= nrhs) continue;
+        float2 o = make_float2(Ys[row * kTcR + r], Ys[(row + nc) * kTcR + r]);
+        const float2 xv = make_float2(Xs[(size_t)row * kTcXs + r], Xs[(size_t)(nc + row) * kTcXs + r]);
+        const float sg = row < nc / 2 ? 1.f : -1.f;
+        const float tj = (float)tau.t[j];
+        if (op == QCD_OP_D) { o -= (tj * sg) * xv; }
+        else { o = sg * o; o -= tj * xv; }
+        y[(size_t)j * vstride + (size_t)s * nc + row] = o;
+    }
+}
+
+size_t coarse_tc_smem(int nc) {
+    // the block region also holds the 2nc x kTcR results at the end
+    const size_t ablk = std::max(sizeof(float2) * (size_t)nc * tc_astride(nc), sizeof(float) * (size_t)2 * nc * kTcR);
+    return sizeof(float) * (size_t)9 * 2 * nc * kTcXs + ablk;
 }
 
 // ------------------------------------------------------------------ SAP block solves
@@ -1064,16 +1188,26 @@ void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void
 }
 
 void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, void* y, const double* tau,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool tensor) {
     Shifts sh{};
     for (int j = 0; j < nrhs; ++j) sh.t[j] = tau ? tau[j] : 0.0;
     size_t n = (size_t)nrhs * c.gc.V * c.nc;
     const double es = prec == QCD_FP64 ? 16.0 : 8.0;
-    KTimer kt(prec == QCD_FP64 ? "coarse_apply_f64" : "coarse_apply_f32",
+    const bool tc = prec == QCD_FP32 && tensor && c.nc % 8 == 0 && c.nc <= 64;
+    KTimer kt(prec == QCD_FP64 ? "coarse_apply_f64" : (tc ? "coarse_apply_tc" : "coarse_apply_f32"),
               es * ((double)c.gc.V * 9 * c.nc * c.nc * ((nrhs + kCoarseRC - 1) / kCoarseRC) +
                     2.0 * nrhs * c.gc.V * c.nc),
               8.0 * 9 * c.nc * c.nc * (double)c.gc.V * nrhs, st);
     (void)n;
+    if (prec == QCD_FP32 && tensor && c.nc % 8 == 0 && c.nc <= 64) {
+        const size_t sm = coarse_tc_smem(c.nc);
+        if (sm > 48 * 1024)
+            cudaFuncSetAttribute(coarse_apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        const dim3 grid(c.gc.V, (nrhs + kTcR - 1) / kTcR);
+        coarse_apply_tc_kernel<<<grid, 32 * (c.nc / 8), sm, st>>>(c.gc, c.nc, c.A32, (const float2*)x, (float2*)y,
+                                                                  op, sh, nrhs);
+        return;
+    }
     // right-hand sides per CTA: a multiple of kCoarseRPT, at most kCoarseRC
     const int rc = std::min(kCoarseRC, (nrhs + kCoarseRPT - 1) / kCoarseRPT * kCoarseRPT);
     const dim3 grid(c.gc.V, (nrhs + rc - 1) / rc);

@@ -58,6 +58,7 @@ class qcd_params(ctypes.Structure):
         ("agg2", ctypes.c_int * 4),
         ("nu2", ctypes.c_int),
         ("coarse_layout", ctypes.c_int),
+        ("coarse_tensor", ctypes.c_int),
     ]
 
 

@@ -24,7 +24,9 @@ WORKLOADS = {
     # 64 x 32^3 (2.1 M sites, 25 M unknowns), three-level MG: 4^4 aggregates
     # (Nv = 24) on the fine lattice, 2^4 aggregates (nv2 = 24) on the coarse
     # one; 100 pairs with 16 targets per outer iteration, m_min 30, m_max 50.
-    "c4_64x32c3": dict(dims=(64, 32, 32, 32), eps=0.6, csw=1.9, m0=-0.85, seed=1004, k=100,
+    # m0 from tests/golden/tune_m0_dense.py (dense oracle spectra of 4^4 and
+    # 8 x 4^3 proxies with the same eps and c_sw).
+    "c4_64x32c3": dict(dims=(64, 32, 32, 32), eps=0.6, csw=1.9, m0=-1.2, seed=1004, k=100,
                        use_mg=1, agg=(4, 4, 4, 4), nv=24, sap=(2, 2, 2, 2), target=1e-3,
                        block=16, m_min=30, m_max=50, update_every=20, levels=3, agg2=(2, 2, 2, 2), nv2=24),
 }

@@ -81,7 +81,33 @@ def test_restrict_prolong_apply(setting, prec, tol):
         ctx.qcd_coarse_apply(op, prec, nrhs, dev(c, dt), y, taus)
         got = host(y).reshape(nrhs, -1)
         for j in range(nrhs):
-            assert relerr(got[j], h.coarse.apply(c[j], taus[j], form).reshape(-1)) < tol
+            # FP32 applies run on the tensor cores (3xTF32): 1e-5; FP64 on the FMA units
+            assert relerr(got[j], h.coarse.apply(c[j], taus[j], form).reshape(-1)) < (tol if prec == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("tensor,tol", [(0, 2e-6), (1, 1e-5)])
+def test_coarse_apply_many_rhs_tensor_and_fma(setting, tensor, tol):
+    """The FP32 coarse stencil on 20 right-hand sides (two chunks of the
+    multi-right-hand-side kernels) on the FMA units and on the tensor cores
+    (3xTF32 split), both forms, against the oracle's stencil."""
+    from paper_2004_08146_gb300 import qcd
+    torch = torch_cuda()
+    ctx, h = setting["ctx"], setting["h"]
+    ctx.qcd_set_params(qcd.default_params(sap_block=SAP, sap_block_tol=-1.0, coarse_tol=0.0, precision=0,
+                                          setup_iters=1, coarse_tensor=tensor, **CYCLE))
+    nrhs = 20
+    info = ctx.qcd_mg_info()
+    nco = info["coarse_sites"] * 2 * setting["nv"]
+    c = synth.complex_gaussian((nrhs, nco), 155)
+    taus = [0.01 * j - 0.1 for j in range(nrhs)]
+    for op, form in ((qcd.QCD_OP_D, 'g5'), (qcd.QCD_OP_Q, 'Q')):
+        y = torch.zeros(nrhs * nco, dtype=torch.complex64, device="cuda")
+        ctx.qcd_coarse_apply(op, 1, nrhs, dev(c, np.complex64), y, taus)
+        got = host(y).reshape(nrhs, -1)
+        for j in range(nrhs):
+            assert relerr(got[j], h.coarse.apply(c[j], taus[j], form).reshape(-1)) < tol, (form, j)
+    ctx.qcd_set_params(qcd.default_params(sap_block=SAP, sap_block_tol=-1.0, coarse_tol=0.0, precision=0,
+                                          setup_iters=1, **CYCLE))
 
 
 @pytest.mark.parametrize("layout", [0, 1, 2, 3])
