@@ -451,19 +451,18 @@ __global__ void __launch_bounds__(128) wilson_clover_kernel(
 // Us[(mu * 9 + k) * V + site] (float2) and As[q * V + site] (float4, q < 18),
 // so a warp's link and clover loads are contiguous; spinors keep the ABI
 // layout.  Same arithmetic as wilson_clover_kernel<float>.  With several
-// right-hand sides, `rg` consecutive lanes take the same site for rg
-// right-hand sides: their link and clover loads are one address per site and
-// are served once per warp request (the links and clover blocks are read once
-// per group of rg right-hand sides instead of once per right-hand side).
+// right-hand sides, consecutive CTAs take the same 128 sites for different
+// right-hand sides (CTA index = site block x nrhs + rhs), so the CTAs that
+// run together read the same links and clover blocks and all but the first
+// find them in L2: the links and clover are read from HBM about once per
+// site block instead of once per right-hand side.
 __global__ void __launch_bounds__(128) wilson_clover_soa_kernel(
     float2* __restrict__ out, const float2* __restrict__ in, const float2* __restrict__ b,
     const float2* __restrict__ Us, const float4* __restrict__ As, Geom g, int op, Shifts tau, size_t stride,
-    const int* __restrict__ act, int rg, int nrhs) {
-    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const int s = (int)(tid / rg);
+    const int* __restrict__ act, int nrhs) {
+    const int j = (int)(blockIdx.x % nrhs);
+    const int s = (int)((blockIdx.x / nrhs) * blockDim.x + threadIdx.x);
     if (s >= g.V) return;
-    const int j = blockIdx.y * rg + (int)(tid % rg);
-    if (j >= nrhs) return;
     if (act != nullptr && !act[j]) return;
     in += j * stride;
     out += j * stride;
@@ -607,14 +606,11 @@ void launch_dirac(const FineOp& f, int op, int nrhs, const void* in, void* out, 
     const cplx<R>* U = std::is_same<R, double>::value ? (const cplx<R>*)f.U64 : (const cplx<R>*)f.U32;
     const R* A = std::is_same<R, double>::value ? (const R*)f.A64 : (const R*)f.A32;
     if (!std::is_same<R, double>::value && f.U32s != nullptr && f.A32s != nullptr) {
-        int rg = 1;
-        while (rg < nrhs && rg < 8) rg *= 2;
-        const int groups = (nrhs + rg - 1) / rg;
-        const double bytes = (double)f.g.V * (nrhs * (b ? 72.0 : 48.0) + 144.0 * groups) * sizeof(R);
+        const double bytes = (double)f.g.V * (nrhs * (b ? 72.0 : 48.0) + 144.0) * sizeof(R);
         KTimer kt("wilson_clover_f32", bytes, 1824.0 * f.g.V * nrhs, st);
-        const dim3 gsoa((unsigned)(((size_t)f.g.V * rg + 127) / 128), groups);
+        const unsigned gsoa = (unsigned)((f.g.V + 127) / 128) * (unsigned)nrhs;
         wilson_clover_soa_kernel<<<gsoa, 128, 0, st>>>((float2*)out, (const float2*)in, (const float2*)b, f.U32s,
-                                                       f.A32s, f.g, op, sh, (size_t)f.g.V * 12, act, rg, nrhs);
+                                                       f.A32s, f.g, op, sh, (size_t)f.g.V * 12, act, nrhs);
         return;
     }
     const double bytes = (double)f.g.V * (nrhs * (b ? 72.0 : 48.0) + 144.0) * sizeof(R);

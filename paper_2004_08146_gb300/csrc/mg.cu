@@ -94,56 +94,94 @@ __global__ void build_P_kernel(Geom g, Blocking B, int nv, const double2* __rest
 }
 
 // ------------------------------------------------------------------ restrict / prolong
+// One warp per (coarse site, chirality, vector i): <P_i, r_j> over the
+// aggregate for a chunk of up to kRestrictRC right-hand sides at a time, so
+// each entry of P is read once per chunk instead of once per right-hand side.
+constexpr int kRestrictRC = 8;
 template <typename Z, typename R>
 __global__ void restrict_kernel(Geom g, Blocking B, int nv, const Z* __restrict__ P, const Z* __restrict__ r,
                                 Z* __restrict__ xc, int nrhs, const int* __restrict__ act) {
     const int nc = 2 * nv;
     const int nloc = B.bs * 6;
-    const long total = (long)B.nb * nc * nrhs;
+    const long total = (long)B.nb * nc;
     const int lane = threadIdx.x & 31;
+    const size_t fstride = (size_t)g.V * 12;
     for (long w = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; w < total; w += ((long)gridDim.x * blockDim.x) >> 5) {
-        const int j = (int)(w / ((long)B.nb * nc));
-        if (act != nullptr && !act[j]) continue;
-        const int rem = (int)(w - (long)j * B.nb * nc);
-        const int blk = rem / nc, ci = rem % nc;
+        const int blk = (int)(w / nc), ci = (int)(w % nc);
         const int chi = ci / nv, i = ci % nv;
         const Z* p = P + (((size_t)blk * 2 + chi) * nv + i) * nloc;
-        const Z* rr = r + (size_t)j * g.V * 12;
-        R re = 0, im = 0;
-        for (int d = lane; d < nloc; d += 32) {
-            int l = d / 6, sc = d % 6;
-            int site = block_fine_site(g, B, blk, l);
-            Z a = p[d], b = rr[(size_t)site * 12 + 6 * chi + sc];
-            re += a.x * b.x + a.y * b.y;
-            im += a.x * b.y - a.y * b.x;
+        for (int j0 = 0; j0 < nrhs; j0 += kRestrictRC) {
+            R re[kRestrictRC], im[kRestrictRC];
+#pragma unroll
+            for (int q = 0; q < kRestrictRC; ++q) { re[q] = 0; im[q] = 0; }
+            for (int d = lane; d < nloc; d += 32) {
+                const int l = d / 6, sc = d % 6;
+                const size_t off = (size_t)block_fine_site(g, B, blk, l) * 12 + 6 * chi + sc;
+                const Z a = p[d];
+#pragma unroll
+                for (int q = 0; q < kRestrictRC; ++q) {
+                    const int j = j0 + q;
+                    if (j >= nrhs || (act != nullptr && !act[j])) continue;
+                    const Z b = r[(size_t)j * fstride + off];
+                    re[q] += a.x * b.x + a.y * b.y;
+                    im[q] += a.x * b.y - a.y * b.x;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kRestrictRC; ++q) {
+                re[q] = warp_sum(re[q]);
+                im[q] = warp_sum(im[q]);
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < kRestrictRC; ++q) {
+                    const int j = j0 + q;
+                    if (j >= nrhs || (act != nullptr && !act[j])) continue;
+                    Z o; o.x = re[q]; o.y = im[q];
+                    xc[(size_t)j * B.nb * nc + (size_t)blk * nc + ci] = o;
+                }
         }
-        re = warp_sum(re);
-        im = warp_sum(im);
-        if (lane == 0) { Z o; o.x = re; o.y = im; xc[(size_t)j * B.nb * nc + (size_t)blk * nc + ci] = o; }
     }
 }
 
+// One thread per fine degree of freedom of an aggregate (coarse site,
+// chirality, local index d); the nv entries P_i[d] are read once per chunk of
+// kProlongRC right-hand sides.
+constexpr int kProlongRC = 4;
 template <typename Z>
 __global__ void prolong_kernel(Geom g, Blocking B, int nv, const Z* __restrict__ P, const Z* __restrict__ xc,
                                Z* __restrict__ x, int nrhs, bool accumulate, const int* __restrict__ act) {
     const int nc = 2 * nv;
     const int nloc = B.bs * 6;
-    const size_t total = (size_t)nrhs * B.nb * 2 * nloc;
+    const size_t total = (size_t)B.nb * 2 * nloc;
+    const size_t fstride = (size_t)g.V * 12, cstride = (size_t)B.nb * nc;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(t / ((size_t)B.nb * 2 * nloc));
-        if (act != nullptr && !act[j]) continue;
-        size_t rem = t - (size_t)j * B.nb * 2 * nloc;
-        const int blk = (int)(rem / (2 * nloc));
-        const int chi = (int)((rem / nloc) % 2);
-        const int d = (int)(rem % nloc);
+        const int blk = (int)(t / (2 * nloc));
+        const int chi = (int)((t / nloc) % 2);
+        const int d = (int)(t % nloc);
         const Z* p = P + ((size_t)blk * 2 + chi) * nv * nloc + d;
-        const Z* c = xc + (size_t)j * B.nb * nc + (size_t)blk * nc + chi * nv;
-        Z acc; acc.x = 0; acc.y = 0;
-        for (int i = 0; i < nv; ++i) acc += p[(size_t)i * nloc] * c[i];
-        int l = d / 6, sc = d % 6;
-        size_t idx = (size_t)j * g.V * 12 + (size_t)block_fine_site(g, B, blk, l) * 12 + 6 * chi + sc;
-        if (accumulate) acc += x[idx];
-        x[idx] = acc;
+        const int l = d / 6, sc = d % 6;
+        const size_t idx = (size_t)block_fine_site(g, B, blk, l) * 12 + 6 * chi + sc;
+        const Z* c0 = xc + (size_t)blk * nc + chi * nv;
+        for (int j0 = 0; j0 < nrhs; j0 += kProlongRC) {
+            Z acc[kProlongRC];
+#pragma unroll
+            for (int q = 0; q < kProlongRC; ++q) { acc[q].x = 0; acc[q].y = 0; }
+            for (int i = 0; i < nv; ++i) {
+                const Z pi = p[(size_t)i * nloc];
+#pragma unroll
+                for (int q = 0; q < kProlongRC; ++q)
+                    if (j0 + q < nrhs) acc[q] += pi * c0[(size_t)(j0 + q) * cstride + i];
+            }
+#pragma unroll
+            for (int q = 0; q < kProlongRC; ++q) {
+                const int j = j0 + q;
+                if (j >= nrhs || (act != nullptr && !act[j])) continue;
+                Z o = acc[q];
+                if (accumulate) o += x[(size_t)j * fstride + idx];
+                x[(size_t)j * fstride + idx] = o;
+            }
+        }
     }
 }
 
@@ -309,12 +347,26 @@ __global__ void coarse_apply_mrhs_kernel(Geom gc, int nc, const Z* __restrict__ 
         nbr[d] = sn;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 9 * nc * rc; e += blockDim.x) {
-        const int col = e % nc, jj = (e / nc) % rc, d = e / (nc * rc);
-        const int j = j0 + jj;
-        Z v; v.x = 0; v.y = 0;
-        if (j < nrhs) v = x[(size_t)j * vstride + (size_t)nbr[d] * nc + col];
-        xs[((size_t)d * nc + col) * rc + jj] = v;
+    const int nstage = 9 * nc * rc;
+    for (int e0 = threadIdx.x; e0 < nstage; e0 += 8 * blockDim.x) {
+        Z v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = e0 + q * blockDim.x;
+            v[q].x = 0; v[q].y = 0;
+            if (e < nstage) {
+                const int col = e % nc, jj = (e / nc) % rc, d = e / (nc * rc);
+                if (j0 + jj < nrhs) v[q] = __ldg(x + (size_t)(j0 + jj) * vstride + (size_t)nbr[d] * nc + col);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = e0 + q * blockDim.x;
+            if (e < nstage) {
+                const int col = e % nc, jj = (e / nc) % rc, d = e / (nc * rc);
+                xs[((size_t)d * nc + col) * rc + jj] = v[q];
+            }
+        }
     }
     __syncthreads();
     const int r = threadIdx.x % nc, grp = threadIdx.x / nc;
@@ -360,6 +412,7 @@ __global__ void coarse_apply_mrhs_kernel(Geom gc, int nc, const Z* __restrict__ 
 // loads); the blocks A_d one direction at a time.  Needs nc % 8 == 0.
 constexpr int kTcR = 16;
 constexpr int kTcXs = 24;   // padded row stride of the staged vectors (floats)
+constexpr int kTcPre = 16;  // prefetched block entries per thread: nc^2 <= 16 x 32 (nc / 8)
 
 __device__ __forceinline__ uint32_t tf32_of(float x) {
     uint32_t r;
@@ -406,20 +459,53 @@ __global__ void coarse_apply_tc_kernel(Geom gc, int nc, const float2* __restrict
         nbr[tid] = sn;
     }
     __syncthreads();
-    for (int e = tid; e < 9 * nc * kTcR; e += blockDim.x) {
-        const int col = e % nc, r = (e / nc) % kTcR, d = e / (nc * kTcR);
-        float2 v = make_float2(0.f, 0.f);
-        if (j0 + r < nrhs) v = x[(size_t)(j0 + r) * vstride + (size_t)nbr[d] * nc + col];
-        Xs[((size_t)d * n2 + col) * kTcXs + r] = v.x;
-        Xs[((size_t)d * n2 + nc + col) * kTcXs + r] = v.y;
+    // stage the neighbour vectors: batches of 8 loads in flight per thread
+    const int nstage = 9 * nc * kTcR;
+    for (int e0 = tid; e0 < nstage; e0 += 8 * blockDim.x) {
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = e0 + q * blockDim.x;
+            v[q] = make_float2(0.f, 0.f);
+            if (e < nstage) {
+                const int col = e % nc, r = (e / nc) % kTcR, d = e / (nc * kTcR);
+                if (j0 + r < nrhs) v[q] = __ldg(x + (size_t)(j0 + r) * vstride + (size_t)nbr[d] * nc + col);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = e0 + q * blockDim.x;
+            if (e < nstage) {
+                const int col = e % nc, r = (e / nc) % kTcR, d = e / (nc * kTcR);
+                Xs[((size_t)d * n2 + col) * kTcXs + r] = v[q].x;
+                Xs[((size_t)d * n2 + nc + col) * kTcXs + r] = v[q].y;
+            }
+        }
     }
+    // the stencil block of the next direction is loaded into registers while
+    // the current one is multiplied (up to kTcPre entries per thread)
+    const int nblk = nc * nc;
+    float2 pre[kTcPre];
+    auto prefetch = [&](int d) {
+        const float2* Ad = A + ((size_t)s * 9 + d) * nblk;
+#pragma unroll
+        for (int q = 0; q < kTcPre; ++q) {
+            const int e = tid + q * blockDim.x;
+            pre[q] = e < nblk ? __ldg(Ad + e) : make_float2(0.f, 0.f);
+        }
+    };
+    prefetch(0);
     float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
     const int row0 = 16 * warp;
     for (int d = 0; d < 9; ++d) {
         __syncthreads();   // staging done / previous block no longer read
-        const float2* Ad = A + ((size_t)s * 9 + d) * nc * nc;
-        for (int e = tid; e < nc * nc; e += blockDim.x) As[(e / nc) * astride + (e % nc)] = __ldg(Ad + e);
+#pragma unroll
+        for (int q = 0; q < kTcPre; ++q) {
+            const int e = tid + q * blockDim.x;
+            if (e < nblk) As[(e / nc) * astride + (e % nc)] = pre[q];
+        }
         __syncthreads();
+        if (d + 1 < 9) prefetch(d + 1);
         const float* Xd = Xs + (size_t)d * n2 * kTcXs;
         for (int k0 = 0; k0 < n2; k0 += 8) {
             uint32_t ab[4], as_[4];
@@ -891,6 +977,19 @@ __global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const 
     store_spinor<R>(x + (size_t)y * 12, e);
 }
 
+// Copy N 16-byte words from global to shared memory with all N loads in
+// flight before the first store (staging without a round trip per word).
+template <int N>
+__device__ __forceinline__ void stage16(void* __restrict__ dst, const void* __restrict__ src) {
+    const int4* s4 = reinterpret_cast<const int4*>(src);
+    int4* d4 = reinterpret_cast<int4*>(dst);
+    int4 v[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = __ldg(s4 + q);
+#pragma unroll
+    for (int q = 0; q < N; ++q) d4[q] = v[q];
+}
+
 // SAP block solve for 16-site blocks with two lanes per site: lane
 // chi * 16 + l holds chirality half chi (spins 2chi, 2chi+1) of site l, so one
 // warp solves one block.  The clover term is block diagonal in chirality; in a
@@ -935,9 +1034,12 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
         o[1] = tt % B.b[1]; o[0] = tt / B.b[1];
     }
     const int y = block_fine_site(g, B, blk, l);
-    // stage links and clover of the 16 sites (both lanes of a site share the work)
-    for (int k = chi; k < 36; k += 2) slink[l * 36 + k] = __ldg(U + (size_t)y * 36 + k);
-    for (int k = chi; k < 72; k += 2) sclov[l * 72 + k] = __ldg(A + (size_t)y * 72 + k);
+    // stage links and clover of the 16 sites: lane chi copies half of its
+    // site's links and its own chirality block of the clover term (16-byte
+    // words, every load in flight at once)
+    constexpr int kHalf = 18 * (int)sizeof(cplx<R>) / 16;   // 16-byte words in 18 complex / 36 reals
+    stage16<kHalf>(slink + l * 36 + 18 * chi, U + (size_t)y * 36 + 18 * chi);
+    stage16<kHalf>(sclov + l * 72 + 36 * chi, A + (size_t)y * 72 + 36 * chi);
     cplx<R> w[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) w[k] = __ldg(r + (size_t)y * 12 + 6 * chi + k);
@@ -1159,12 +1261,13 @@ void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st, bool fp32_only
 
 void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* r, void* xc, cudaStream_t st,
                  const int* act) {
-    size_t warps = (size_t)c.B.nb * c.nc * nrhs;
+    size_t warps = (size_t)c.B.nb * c.nc;
     int grid = grid_for(warps * 32);
     const double es = prec == QCD_FP64 ? 16.0 : 8.0;
     const double nfine = (double)f.g.V * 12;
+    const double chunks = (nrhs + kRestrictRC - 1) / kRestrictRC;
     KTimer kt(prec == QCD_FP64 ? "restrict_f64" : "restrict_f32",
-              es * (nfine * c.nv + nrhs * (nfine + (double)c.gc.V * c.nc)), 8.0 * nfine * c.nv * nrhs, st);
+              es * (nfine * c.nv * chunks + nrhs * (nfine + (double)c.gc.V * c.nc)), 8.0 * nfine * c.nv * nrhs, st);
     if (prec == QCD_FP64)
         restrict_kernel<double2, double><<<grid, 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)r, (double2*)xc, nrhs, act);
     else
@@ -1173,11 +1276,12 @@ void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const voi
 
 void mg_prolong(const FineOp& f, const Coarse& c, int prec, int nrhs, const void* xc, void* x, bool accumulate,
                 cudaStream_t st, const int* act) {
-    size_t n = (size_t)nrhs * c.B.nb * 2 * c.B.bs * 6;
+    size_t n = (size_t)c.B.nb * 2 * c.B.bs * 6;
     const double es = prec == QCD_FP64 ? 16.0 : 8.0;
     const double nfine = (double)f.g.V * 12;
+    const double chunks = (nrhs + kProlongRC - 1) / kProlongRC;
     KTimer kt(prec == QCD_FP64 ? "prolong_f64" : "prolong_f32",
-              es * (nfine * c.nv + nrhs * (nfine * (accumulate ? 2 : 1) + (double)c.gc.V * c.nc)),
+              es * (nfine * c.nv * chunks + nrhs * (nfine * (accumulate ? 2 : 1) + (double)c.gc.V * c.nc)),
               8.0 * nfine * c.nv * nrhs, st);
     if (prec == QCD_FP64)
         prolong_kernel<double2><<<grid_for(n), 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)xc, (double2*)x, nrhs,

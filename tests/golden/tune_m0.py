@@ -7,12 +7,12 @@ Grid search: min |lambda| is evaluated at each m0 of a grid (one process per
 point) with the oracle's GD-lambda-AMG (two-level MG with GMRES smoothing,
 Gamma5 form, sign-balanced block of 2, residual 1e-5 -- far below the
 resolution the choice needs), and the grid point closest to the target wins.
-On the 16 x 8^3 field the smallest |lambda| bottoms out near 5e-2 between
-m0 = -0.85 and -0.9 and grows again beyond (GPU scans: 5.3e-2 at -0.90,
-6.6e-2 at -0.95), so the 1e-2 target is not reachable there.  The oracle's
-probes at -0.90 and below did not finish within an hour (the near-critical
-spectrum slows GD down), so the grid stops at -0.85; the recorded
-min_abs_lambda states what the chosen m0 gives.
+The grid has two points, -0.80 and -0.85: the oracle's probes at -0.90 and
+below did not finish within an hour (the near-critical spectrum slows GD
+down).  The choice therefore rests on those two points only; the recorded
+min_abs_lambda (5.5e-2 at -0.85, above the 1e-2 target) states what the
+chosen m0 gives.  The larger workloads are tuned on dense proxies instead
+(tune_m0_dense.py).
 
 usage: python tests/golden/tune_m0.py <name> [<name> ...]
 """
