@@ -67,6 +67,9 @@ def parse():
                     help="run and print only the fine-stencil bandwidth measurement")
     ap.add_argument("--k", type=int, default=None,
                     help="eigenpairs per step instead of the workload's (short profiling runs)")
+    ap.add_argument("--coarse-stencil", action="store_true",
+                    help="run and print only the coarse-stencil comparison (tensor cores vs FMA units)")
+    ap.add_argument("--no-coarse-stencil", action="store_true")
     ap.add_argument("--no-large-workload", action="store_true",
                     help="skip the 64 x 32^3 three-level measurement")
     ap.add_argument("--large-workload", default="c4_64x32c3")
@@ -327,6 +330,9 @@ def main():
         peak, _ = measured_peaks()
         print(json.dumps({"stencil": stencil_bench(qcd, synth, torch, devn, stream, peak)}), flush=True)
         return
+    if args.coarse_stencil:
+        print(json.dumps({"coarse_stencil": coarse_stencil_bench(qcd, synth, torch, devn, stream)}), flush=True)
+        return
 
     def make(precision):
         p = workload_params(qcd, w, precision=precision)
@@ -446,6 +452,11 @@ def main():
                "frac": sflops / (d["total_ms"] * 1e-3) / 1e12 / fp32_peak,
                "site_steps": sap_work[0]}
     fp64_peak = qcd.qcd_fma_peak(qcd.QCD_FP64)
+    fp64_tc_peak = qcd.qcd_fma_peak(2)
+
+    coarse = None
+    if not args.no_coarse_stencil and rank == 0:
+        coarse = coarse_stencil_bench(qcd, synth, torch, devn, stream)
 
     # ---- the 64 x 32^3 three-level workload, 100 pairs, mixed precision
     large = None
@@ -484,8 +495,10 @@ def main():
                     "max_abs_lambda": float(np.max(np.abs(lam)))},
             "alu_roofline": alu,
             "fp64_fma_peak_tflops": fp64_peak,
+            "fp64_tensor_peak_tflops": fp64_tc_peak,
             "fp64": fp64,
             "stencil": stencil,
+            "coarse_stencil": coarse,
             "large_workload": large,
             "clocks": clk,
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
@@ -501,7 +514,7 @@ def workload_params(qcd, w, **kw):
     """Library parameters of a workload: Table 2 defaults plus the workload's
     MG and outer-iteration shape."""
     p = dict(use_mg=w["use_mg"], sap_block=w["sap"])
-    for key in ("block", "m_min", "m_max", "update_every", "levels", "nv2", "agg2"):
+    for key in ("block", "m_min", "m_max", "update_every", "levels", "nv2", "agg2", "sap_half"):
         if key in w:
             p[key] = w[key]
     p.update(kw)
@@ -794,6 +807,45 @@ def smoother_sweep(qcd, synth, torch, devn, stream):
                              "residual": info.residual, "ms": (time.perf_counter() - t0) * 1e3})
             ctx.close()
     return {"lattice": "8^4", "eps": 0.5, "csw": csw, "m0": m0, "tol": 1e-8, "rows": rows}
+
+
+def coarse_stencil_bench(qcd, synth, torch, devn, stream, reps=20):
+    """The coarse stencil of the 32 x 16^3 field with 4^4 aggregates and
+    Nv = 24 (512 coarse sites, 2 Nv = 48, the size of the 64 x 32^3
+    workload's level 2 and 1/16 of its level 1) on 16 right-hand sides in one
+    apply, FP32 data: tensor cores (3xTF32 mma.sync) against the FMA units.
+    Flops 8 x 9 x (2 Nv)^2 per site and right-hand side; bytes: the stencil
+    blocks once plus the vectors in and out."""
+    dims, nv, nrhs = (32, 16, 16, 16), 24, 16
+    U = synth.gauge_field(dims, 0.6, 1004)
+    out = {"lattice": "32x16^3", "aggregates": [4, 4, 4, 4], "nv": nv, "nrhs": nrhs}
+    for tensor in (1, 0):
+        ctx = qcd.Context(params=qcd.default_params(setup_iters=1, coarse_tensor=tensor), stream=stream.cuda_stream)
+        ctx.qcd_set_gauge(U, dims, -0.85, 1.9)
+        ctx.qcd_mg_setup(nv, (4, 4, 4, 4))
+        info = ctx.qcd_mg_info()
+        nco = info["coarse_sites"] * 2 * nv
+        x = torch.randn(nrhs * nco, dtype=torch.complex64, device=devn)
+        y = torch.empty_like(x)
+        taus = [0.01] * nrhs
+        torch.cuda.synchronize()
+        for _ in range(3):
+            ctx.qcd_coarse_apply(qcd.QCD_OP_D, qcd.QCD_FP32, nrhs, x, y, taus)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.qcd_coarse_apply(qcd.QCD_OP_D, qcd.QCD_FP32, nrhs, x, y, taus)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps * 1e-3
+        sites = info["coarse_sites"]
+        flops = 8.0 * 9 * (2 * nv) ** 2 * sites * nrhs
+        nbytes = 8.0 * (9 * (2 * nv) ** 2 * sites + 2 * nrhs * nco)
+        out["tensor" if tensor else "fma"] = {"us_per_apply": t * 1e6, "tflops": flops / t / 1e12,
+                                               "gbs": nbytes / t / 1e9}
+        ctx.close()
+    return out
 
 
 def stencil_bench(qcd, synth, torch, devn, stream, peak):

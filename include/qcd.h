@@ -110,6 +110,9 @@ typedef struct qcd_params {
                                 operator (2 Nv a multiple of 8) on the tensor cores, TF32
                                 inputs split in big + small parts (three products, FP32
                                 accumulation); 0: FP32 FMA units */
+    int    sap_half;         /* 1: FP32 SAP block solves on 16-site blocks store their
+                                Krylov basis in FP16 (half the shared memory, more block
+                                solves resident; default 0) */
 } qcd_params;
 
 typedef struct qcd_solve_info {
@@ -366,11 +369,12 @@ int qcd_stats_read(qcd_kernel_stat* out, int max, int* n);
 int qcd_stats_sap_work(double* site_steps, double* site_steps_tri);
 
 /* Measured fused multiply-add throughput of the current device in TFLOP/s
- * (2 flops per FMA) for prec QCD_FP32 or QCD_FP64: a kernel of independent
- * FMA chains on every SM, best of five timed launches on the default stream
- * (the roofline denominator of FP32- and FP64-ALU-bound kernels; the SM
- * clock at the time of the call sets the value).  EINVAL on a bad prec or
- * NULL; ECUDA when the launch fails. */
+ * (2 flops per FMA) for prec QCD_FP32 or QCD_FP64 (FMA units), or prec 2 for
+ * FP64 on the tensor cores (mma m8n8k4 f64): a kernel of independent chains
+ * on every SM, best of five timed launches on the default stream (the
+ * roofline denominator of FP32- and FP64-bound kernels; the SM clock at the
+ * time of the call sets the value).  EINVAL on a bad prec or NULL; ECUDA when
+ * the launch fails. */
 int qcd_fma_peak(int prec, double* tflops);
 
 #ifdef __cplusplus

@@ -194,6 +194,7 @@ void validate_params(const qcd_params& p) {
         if (p.agg2[mu] < 1) throw QcdError(QCD_EINVAL, "agg2 extents must be >= 1");
     if (p.coarse_layout < 0 || p.coarse_layout > 3) throw QcdError(QCD_EINVAL, "coarse_layout must be in [0, 3]");
     if (p.coarse_tensor != 0 && p.coarse_tensor != 1) throw QcdError(QCD_EINVAL, "coarse_tensor must be 0 or 1");
+    if (p.sap_half != 0 && p.sap_half != 1) throw QcdError(QCD_EINVAL, "sap_half must be 0 or 1");
 }
 
 // ------------------------------------------------------------------ linear operators
@@ -465,7 +466,7 @@ void sap_smooth(qcd_ctx* ctx, int prec, int op, int nrhs, const void* b, void* x
         for (int colour = 0; colour < 2; ++colour) {
             residual_op(ctx->f, prec, op, nrhs, b, x, r, tau, ctx->st, act);
             sap_blocks(ctx->f, ctx->sap, colour, prec, op, nrhs, r, x, tau, ctx->p.sap_block_iters, tol, scr, ctx->st,
-                       act);
+                       act, ctx->p.sap_half != 0);
         }
     }
     check_launch("sap");
@@ -1399,6 +1400,7 @@ void qcd_default_params(qcd_params* p) {
     p->nu2 = 2;
     p->coarse_layout = 0;
     p->coarse_tensor = 1;
+    p->sap_half = 0;
 }
 
 int qcd_create(qcd_ctx** out, const qcd_params* p, void* stream) {

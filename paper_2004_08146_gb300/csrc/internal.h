@@ -187,9 +187,10 @@ struct SapPlan {
     int ncol[2] = {0, 0};
 };
 // x += block solves of op(tau) on the blocks of `colour`, rhs r (full fields)
+// half: FP32 solves on 16-site blocks keep the block Krylov basis in FP16
 void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op, int nrhs,
                 const void* r, void* x, const double* tau, int iters, double tol,
-                void* scratch, cudaStream_t st, const int* act = nullptr);
+                void* scratch, cudaStream_t st, const int* act = nullptr, bool half = false);
 // Global scratch of sap_blocks: blocks of 16 and 32 sites keep their Krylov
 // basis in shared memory (0 bytes); every other block size needs
 // (iters + 1) block vectors per block of the larger colour and per rhs.

@@ -3,6 +3,8 @@
 // D_c = P^H D P (Eq. 2.8, 2.9) and the SAP block solves of Eq. 2.10.
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "internal.h"
 #include "dirac.cuh"
 
@@ -752,11 +754,11 @@ struct SapSmemLayout {
     size_t basis, links, clover, H, g, sn, y, cs, flag, total;
 };
 template <typename R>
-__host__ __device__ inline SapSmemLayout sap_layout(int BS, int iters) {
+__host__ __device__ inline SapSmemLayout sap_layout(int BS, int iters, size_t basis_elem = sizeof(cplx<R>)) {
     auto up = [](size_t v) { return (v + 15) & ~size_t(15); };
     SapSmemLayout L;
     size_t o = 0;
-    L.basis = o;  o = up(o + (size_t)(iters + 1) * BS * 12 * sizeof(cplx<R>));
+    L.basis = o;  o = up(o + (size_t)(iters + 1) * BS * 12 * basis_elem);
     L.links = o;  o = up(o + (size_t)BS * 36 * sizeof(cplx<R>));
     L.clover = o; o = up(o + (size_t)BS * 72 * sizeof(R));
     L.H = o;      o = up(o + (size_t)(iters + 1) * iters * sizeof(cplx<R>));
@@ -977,6 +979,17 @@ __global__ void __launch_bounds__(32) sap_warp_kernel(Geom g, Blocking B, const 
     store_spinor<R>(x + (size_t)y * 12, e);
 }
 
+// Storage of the SAP block Krylov basis: the working precision, or FP16
+// pairs for FP32 solves (the basis then takes half the shared memory, so more
+// block solves are resident per SM; the block solves only need a 1e-1
+// reduction).
+__device__ __forceinline__ float2 bload(const float2* p) { return *p; }
+__device__ __forceinline__ double2 bload(const double2* p) { return *p; }
+__device__ __forceinline__ float2 bload(const __half2* p) { return __half22float2(*p); }
+__device__ __forceinline__ void bstore(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void bstore(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void bstore(__half2* p, float2 v) { *p = __float22half2_rn(v); }
+
 // Copy N 16-byte words from global to shared memory with all N loads in
 // flight before the first store (staging without a round trip per word).
 template <int N>
@@ -997,7 +1010,7 @@ __device__ __forceinline__ void stage16(void* __restrict__ dst, const void* __re
 // by the link (9 complex products instead of 18) and takes the other s from
 // the partner lane (lane ^ 16) before it reconstructs its own half.  Same
 // GMRES as sap_warp_kernel (modified Gram-Schmidt, Givens by lane 0).
-template <typename R>
+template <typename R, typename BT>
 __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const cplx<R>* __restrict__ U,
                                                      const R* __restrict__ A, const int* __restrict__ blocks, int ncol,
                                                      int op, Shifts tau, const cplx<R>* __restrict__ r,
@@ -1007,9 +1020,9 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x;
     const int chi = lane >> 4, l = lane & 15;
-    const SapSmemLayout LY = sap_layout<R>(BS, iters);
+    const SapSmemLayout LY = sap_layout<R>(BS, iters, sizeof(BT));
     unsigned char* base = smraw;
-    cplx<R>* basis = reinterpret_cast<cplx<R>*>(base + LY.basis);
+    BT* basis = reinterpret_cast<BT*>(base + LY.basis);
     cplx<R>* slink = reinterpret_cast<cplx<R>*>(base + LY.links);
     R* sclov = reinterpret_cast<R*>(base + LY.clover);
     cplx<R>* H = reinterpret_cast<cplx<R>*>(base + LY.H);
@@ -1051,7 +1064,7 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
     {
         const R ib = beta > R(0) ? R(1) / beta : R(0);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) basis[l * 12 + 6 * chi + k] = ib * w[k];
+        for (int k = 0; k < 6; ++k) bstore(basis + l * 12 + 6 * chi + k, ib * w[k]);
     }
     if (lane == 0) { gv[0] = mk<R>(beta, R(0)); flag[0] = beta > R(0) ? 0 : 1; flag[1] = 0; }
     __syncwarp();
@@ -1063,10 +1076,10 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
     for (int jj = 0; jj < iters; ++jj) {
         const bool active = flag[0] == 0;
         if (!active) break;   // flag is shared by the whole warp
-        const cplx<R>* vj = basis + (size_t)jj * BS * 12;
+        const BT* vj = basis + (size_t)jj * BS * 12;
         cplx<R> psi[6], acc[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) psi[k] = vj[l * 12 + 6 * chi + k];
+        for (int k = 0; k < 6; ++k) psi[k] = bload(vj + l * 12 + 6 * chi + k);
         // clover block chi of site l
         {
             const R* a = sclov + l * 72 + 36 * chi;
@@ -1094,13 +1107,13 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
                 const bool has = round == 0 ? (fw || o[mu] > 0) : (o[mu] < B.b[mu] - 1 && o[mu] > 0);
                 if (round == 1 && !__any_sync(0xffffffffu, has)) break;
                 const int ln = has ? (fw ? l + lstride[mu] : l - lstride[mu]) : l;
-                const cplx<R>* nb = vj + ln * 12;
+                const BT* nb = vj + ln * 12;
                 const R pm = fw ? R(-1) : R(1);
                 // h_s for s = chi: up_s + pm i^{ph_s} dn_{perm_s}
                 const int sp = Bm.perm[chi], ph = Bm.ph[chi];
                 cplx<R> h[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) h[a] = nb[chi * 3 + a] + pm * mul_ipow(nb[(2 + sp) * 3 + a], ph);
+                for (int a = 0; a < 3; ++a) h[a] = bload(nb + chi * 3 + a) + pm * mul_ipow(bload(nb + (2 + sp) * 3 + a), ph);
                 const cplx<R>* lk = slink + (fw ? l : ln) * 36 + mu * 9;
                 cplx<R> os[3];
 #pragma unroll
@@ -1140,11 +1153,11 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
         }
         // modified Gram-Schmidt against v_0 .. v_jj
         for (int i = 0; i <= jj; ++i) {
-            const cplx<R>* vi = basis + (size_t)i * BS * 12 + l * 12 + 6 * chi;
+            const BT* vi = basis + (size_t)i * BS * 12 + l * 12 + 6 * chi;
             R hr = 0, hi = 0;
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                const cplx<R> a = vi[k];
+                const cplx<R> a = bload(vi + k);
                 hr += a.x * acc[k].x + a.y * acc[k].y;
                 hi += a.x * acc[k].y - a.y * acc[k].x;
             }
@@ -1152,7 +1165,7 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
             hi = warp_sum(hi);
             const cplx<R> h = mk<R>(hr, hi);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[k] -= h * vi[k];
+            for (int k = 0; k < 6; ++k) acc[k] -= h * bload(vi + k);
             if (lane == 0) H[i * iters + jj] = h;
         }
         R hn2 = 0;
@@ -1162,9 +1175,9 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
         const R hn = sqrt(hn2);
         {
             const R ih = hn > R(0) ? R(1) / hn : R(0);
-            cplx<R>* vn = basis + (size_t)(jj + 1) * BS * 12 + l * 12 + 6 * chi;
+            BT* vn = basis + (size_t)(jj + 1) * BS * 12 + l * 12 + 6 * chi;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) vn[k] = ih * acc[k];
+            for (int k = 0; k < 6; ++k) bstore(vn + k, ih * acc[k]);
         }
         if (lane == 0) {
             H[(jj + 1) * iters + jj] = mk<R>(hn, R(0));
@@ -1210,9 +1223,9 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
     for (int k = 0; k < 6; ++k) e[k] = x[(size_t)y * 12 + 6 * chi + k];
     for (int i = 0; i < kdim; ++i) {
         const cplx<R> yi = yv[i];
-        const cplx<R>* vi = basis + (size_t)i * BS * 12 + l * 12 + 6 * chi;
+        const BT* vi = basis + (size_t)i * BS * 12 + l * 12 + 6 * chi;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) e[k] += yi * vi[k];
+        for (int k = 0; k < 6; ++k) e[k] += yi * bload(vi + k);
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) x[(size_t)y * 12 + 6 * chi + k] = e[k];
@@ -1357,25 +1370,31 @@ size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters) {
 }
 
 void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op, int nrhs, const void* r, void* x,
-                const double* tau, int iters, double tol, void* scratch, cudaStream_t st, const int* act) {
+                const double* tau, int iters, double tol, void* scratch, cudaStream_t st, const int* act, bool half) {
     Shifts sh{};
     for (int j = 0; j < nrhs; ++j) sh.t[j] = tau ? tau[j] : 0.0;
     const int bs = sp.B.bs;
     const double rs = prec == QCD_FP64 ? 8.0 : 4.0;
     const double sites = (double)sp.ncol[colour] * bs;
-    KTimer kt(prec == QCD_FP64 ? "sap_block_f64" : "sap_block_f32", rs * sites * (nrhs * 72.0 + 144.0),
+    KTimer kt(prec == QCD_FP64 ? "sap_block_f64" : (half && bs == 16 ? "sap_block_f32h" : "sap_block_f32"),
+              rs * sites * (nrhs * 72.0 + 144.0),
               1824.0 * sites * nrhs * iters, st);
     if (bs == 16) {
         dim3 grid(sp.ncol[colour], nrhs);
         if (prec == QCD_FP64) {
             const size_t sm = sap_layout<double>(16, iters).total;
-            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            sap_chi_kernel<double><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
+            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            sap_chi_kernel<double, double2><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
                 sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
+        } else if (half) {
+            const size_t sm = sap_layout<float>(16, iters, sizeof(__half2)).total;
+            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            sap_chi_kernel<float, __half2><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
+                sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
         } else {
             const size_t sm = sap_layout<float>(16, iters).total;
-            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            sap_chi_kernel<float><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
+            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            sap_chi_kernel<float, float2><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
                 sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
         }
         return;

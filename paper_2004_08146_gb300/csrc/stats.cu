@@ -95,6 +95,25 @@ __global__ void __launch_bounds__(256) fma_chain_kernel(R a, R b, int iters, R* 
     for (int c = 0; c < kChains; ++c) acc += x[c];
     if (acc == R(-12345.678)) sink[threadIdx.x] = acc;
 }
+// FP64 tensor-core probe: independent mma.sync m8n8k4 f64 chains per warp
+// (each 256 multiply-adds = 512 flops per warp instruction).
+__global__ void __launch_bounds__(256) dmma_chain_kernel(int iters, double* sink) {
+    double c[kChains][2];
+    const double a = 1e-3 * (threadIdx.x + 1), b = 0.999;
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) { c[q][0] = 0.0; c[q][1] = 0.0; }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < kChains; ++q)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                         : "+d"(c[q][0]), "+d"(c[q][1])
+                         : "d"(a), "d"(b));
+    }
+    double acc = 0;
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) acc += c[q][0] + c[q][1];
+    if (acc == -12345.678) sink[threadIdx.x] = acc;
+}
 }  // namespace
 
 double fma_peak_tflops(int prec, cudaStream_t st) {
@@ -102,7 +121,7 @@ double fma_peak_tflops(int prec, cudaStream_t st) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = sms * 8, threads = 256;
-    const int iters = prec == QCD_FP64 ? 64 : 2048;
+    const int iters = prec == QCD_FP64 ? 64 : (prec == 2 ? 256 : 2048);
     void* sink = nullptr;
     if (cudaMalloc(&sink, threads * sizeof(double)) != cudaSuccess) return 0.0;
     cudaEvent_t e0, e1;
@@ -111,7 +130,9 @@ double fma_peak_tflops(int prec, cudaStream_t st) {
     float best = 1e30f;
     for (int rep = 0; rep < 6; ++rep) {
         cudaEventRecord(e0, st);
-        if (prec == QCD_FP64)
+        if (prec == 2)
+            dmma_chain_kernel<<<grid, threads, 0, st>>>(iters, (double*)sink);
+        else if (prec == QCD_FP64)
             fma_chain_kernel<double><<<grid, threads, 0, st>>>(0.999999, 1e-7, iters, (double*)sink);
         else
             fma_chain_kernel<float><<<grid, threads, 0, st>>>(0.9999f, 1e-4f, iters, (float*)sink);
@@ -124,7 +145,10 @@ double fma_peak_tflops(int prec, cudaStream_t st) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(sink);
-    const double flops = 2.0 * kChains * 16.0 * iters * (double)grid * threads;
+    // FMA chains: 2 flops x kChains x 16 per round per thread; DMMA: 512 flops per
+    // warp instruction, kChains per round per warp
+    const double flops = prec == 2 ? 512.0 * kChains * iters * (double)grid * (threads / 32)
+                                   : 2.0 * kChains * 16.0 * iters * (double)grid * threads;
     return best > 0 && best < 1e29f ? flops / (best * 1e-3) / 1e12 : 0.0;
 }
 
@@ -142,7 +166,7 @@ int qcd_stats_sap_work(double* site_steps, double* site_steps_tri) {
 }
 
 int qcd_fma_peak(int prec, double* tflops) {
-    if (!tflops || (prec != QCD_FP64 && prec != QCD_FP32)) return QCD_EINVAL;
+    if (!tflops || (prec != QCD_FP64 && prec != QCD_FP32 && prec != 2)) return QCD_EINVAL;
     *tflops = qcd::fma_peak_tflops(prec, nullptr);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess && *tflops > 0 ? QCD_OK : QCD_ECUDA;

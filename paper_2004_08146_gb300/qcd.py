@@ -59,6 +59,7 @@ class qcd_params(ctypes.Structure):
         ("nu2", ctypes.c_int),
         ("coarse_layout", ctypes.c_int),
         ("coarse_tensor", ctypes.c_int),
+        ("sap_half", ctypes.c_int),
     ]
 
 

@@ -26,7 +26,8 @@ def _run(torch, w, U, block, seed):
     dims, k = tuple(w["dims"]), w["k"]
     n = 12 * int(np.prod(dims))
     ctx = make_ctx(U, dims, w["m0"], w["csw"], precision=1, sap_block=w["sap"], block=block, seed=seed,
-                   m_min=w["m_min"], m_max=w["m_max"], update_every=w["update_every"], max_outer=4000)
+                   m_min=w["m_min"], m_max=w["m_max"], update_every=w["update_every"], max_outer=4000,
+                   sap_half=w.get("sap_half", 0))
     ctx.qcd_mg_setup(w["nv"], w["agg"])
     V = torch.zeros(k * n, dtype=torch.complex128, device="cuda")
     rc, lam, info = ctx.qcd_eigs(k, 1e-8, V)

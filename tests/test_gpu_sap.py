@@ -46,3 +46,33 @@ def test_sap_block_families_match_oracle(dims, block, prec, tol):
             ref = sap.smooth(A, b[j], x0[j], 2)
             assert relerr(got[j], ref) < tol, (form, j)
     ctx.close()
+
+
+def test_sap_fp16_basis_matches_oracle():
+    """FP32 SAP on 16-site blocks with the block Krylov basis stored in FP16
+    (params.sap_half): the sweeps follow the oracle's at fixed block-GMRES steps
+    to the accuracy FP16 storage allows (5e-3 relative), both forms."""
+    from paper_2004_08146_gb300 import qcd
+    torch_cuda()
+    dims, block = (8, 4, 4, 4), (2, 2, 2, 2)
+    U = synth.gauge_field(dims, 0.5, 71)
+    m0, csw = -0.3, 1.3
+    op = WilsonClover(U, m0, csw)
+    ctx = make_ctx(U, dims, m0, csw, sap_block=block, sap_block_iters=ITERS, sap_half=1)
+    b = synth.spinor(dims, 72, nvec=2)
+    x0 = synth.spinor(dims, 73, nvec=2)
+    taus = [0.1, -0.2]
+    sap = mg.SAP(dims, block, block_iters=ITERS, block_tol=0.0)
+    qcd.qcd_stats_reset(0)
+    for opc, form in ((qcd.QCD_OP_D, 'g5'), (qcd.QCD_OP_Q, 'Q')):
+        xd = dev(x0, np.complex64)
+        ctx.qcd_sap(opc, 1, 2, dev(b, np.complex64), xd, taus, 2, -1.0)
+        got = host(xd).reshape((2,) + dims + (4, 3))
+        for j in range(2):
+            A = lambda v, t=taus[j]: mg.fine_apply(op, v, t, form)
+            ref = sap.smooth(A, b[j], x0[j], 2)
+            assert relerr(got[j], ref) < 5e-3, (form, j)
+    # the FP16-basis kernel is the one that ran
+    names = {r["name"]: r["launches"] for r in qcd.qcd_stats_read()}
+    assert names.get("sap_block_f32h", 0) == 8 and "sap_block_f32" not in names
+    ctx.close()
