@@ -113,6 +113,13 @@ typedef struct qcd_params {
     int    sap_half;         /* 1: FP32 SAP block solves on 16-site blocks store their
                                 Krylov basis in FP16 (half the shared memory, more block
                                 solves resident; default 0) */
+    int    confirm;          /* completion check of qcd_eigs: once k pairs are locked
+                                and no harmonic Ritz value lies below the k-th
+                                smallest locked |lambda|, this many further outer
+                                iterations (corrections for the smallest values above
+                                that bound) must leave none below it before the call
+                                returns; a value below it resets the count.  0 returns
+                                at the first such check (default 2, <= 64) */
 } qcd_params;
 
 typedef struct qcd_solve_info {

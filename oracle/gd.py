@@ -125,7 +125,8 @@ def select_targets(theta, b, candidates=None):
 
 def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
                   n_tv=None, on_update=None, update_every=1, max_outer=100000,
-                  random_vector=None, n_guard=0, block=1, shift='rho', extraction='harmonic'):
+                  random_vector=None, n_guard=0, block=1, shift='rho', extraction='harmonic',
+                  confirm=0):
     """Algorithm 2 (GD-lambda-AMG) on flat complex vectors.
 
     Q            : callable, v (N,) -> Q v
@@ -147,6 +148,12 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
                    Ritz value (Algorithm 2 as printed)
     extraction   : 'harmonic' (Theorem 1, the method's default) or 'rr' for
                    the Rayleigh-Ritz pairs (the comparison of Sec. 4)
+    confirm      : completion check (the paper states no stopping rule beyond
+                   the number of pairs): once n pairs are locked and no
+                   harmonic Ritz value lies below the n-th smallest locked
+                   |lambda|, this many further outer iterations correct the
+                   smallest values above that bound; a value below it resets
+                   the count, and the run ends when the count is reached
     """
     extract = harmonic_ritz if extraction == 'harmonic' else rayleigh_ritz
     n_want = n
@@ -166,6 +173,7 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
     inner = 0
     locks_since_update = 0
     finished = False
+    confirm_done = 0
     while not finished and outer < max_outer:
         outer += 1
         added = 0
@@ -186,15 +194,21 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
             T = rnd(outer)[:, None]
             continue
         finished = False
+        confirming = False
         while True:
             theta, S = extract(V, W)
             cand = None
             if len(lam) >= n:
                 lim = np.sort(np.abs(lam))[n - 1]
                 cand = np.nonzero(np.abs(theta) < lim)[0]
-                if cand.size == 0:
-                    finished = True
-                    break
+                confirming = cand.size == 0
+                if confirming:
+                    if confirm_done >= confirm:
+                        finished = True
+                        break
+                    cand = None
+                else:
+                    confirm_done = 0
             tg = select_targets(theta, block, cand)
             pairs = []
             locked = False
@@ -237,6 +251,8 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
             t, it = correction(th, r)
             T[:, j] = t
             inner += int(it)
+        if confirming:
+            confirm_done += 1
         if V.shape[1] + T.shape[1] > m_max:
             theta, S = extract(V, W)
             Qs, _ = np.linalg.qr(S[:, :m_min])

@@ -195,6 +195,7 @@ void validate_params(const qcd_params& p) {
     if (p.coarse_layout < 0 || p.coarse_layout > 3) throw QcdError(QCD_EINVAL, "coarse_layout must be in [0, 3]");
     if (p.coarse_tensor != 0 && p.coarse_tensor != 1) throw QcdError(QCD_EINVAL, "coarse_tensor must be 0 or 1");
     if (p.sap_half != 0 && p.sap_half != 1) throw QcdError(QCD_EINVAL, "sap_half must be 0 or 1");
+    if (p.confirm < 0 || p.confirm > 64) throw QcdError(QCD_EINVAL, "confirm must be in [0, 64]");
 }
 
 // ------------------------------------------------------------------ linear operators
@@ -1158,6 +1159,12 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
     int nT = block;
     int outer = 0, inner = 0, updates = 0, locks_since_update = 0;
     bool finished = false;
+    // completion: once k pairs are locked and no harmonic Ritz value lies
+    // below the k-th smallest locked |lambda|, P.confirm further outer
+    // iterations expand the space towards the smallest values above that
+    // bound; a value that falls below it restarts the count
+    int confirm_done = 0;
+    bool confirming = false;
     // interpolation updates stage their vectors in the test-vector buffer
     // (the setup vectors are in the start basis already)
     double2* vbuf = ctx->test_vectors;
@@ -1185,7 +1192,13 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
                 double lim = al[k - 1];
                 int cnt = 0;
                 for (size_t i = 0; i < theta.size(); ++i) { allowed[i] = std::fabs(theta[i]) < lim; cnt += allowed[i]; }
-                if (cnt == 0) { finished = true; break; }
+                confirming = cnt == 0;
+                if (confirming) {
+                    if (confirm_done >= P.confirm) { finished = true; break; }
+                    std::fill(allowed.begin(), allowed.end(), 1);
+                } else {
+                    confirm_done = 0;
+                }
             }
             tg = select_targets(theta, block, allowed);
             // FP64 refinement of the targeted pairs (the full decomposition is FP32)
@@ -1292,6 +1305,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
         for (int v : g.iters) inner += v;
         blas_convert(prec, tl, QCD_FP64, gd.T, (size_t)nb * n, st);
         nT = nb;
+        if (confirming) ++confirm_done;
         // thick restart
         if (gd.m + nT > P.m_max) {
             std::vector<double> th;
@@ -1401,6 +1415,7 @@ void qcd_default_params(qcd_params* p) {
     p->coarse_layout = 0;
     p->coarse_tensor = 1;
     p->sap_half = 0;
+    p->confirm = 2;
 }
 
 int qcd_create(qcd_ctx** out, const qcd_params* p, void* stream) {

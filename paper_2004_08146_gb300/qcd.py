@@ -60,6 +60,7 @@ class qcd_params(ctypes.Structure):
         ("coarse_layout", ctypes.c_int),
         ("coarse_tensor", ctypes.c_int),
         ("sap_half", ctypes.c_int),
+        ("confirm", ctypes.c_int),
     ]
 
 
