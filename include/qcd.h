@@ -67,7 +67,7 @@ typedef struct qcd_params {
     int    smoother;         /* QCD_SMOOTHER_SAP (default) or QCD_SMOOTHER_GMRES */
     int    nu;               /* post-smoothing steps (Table 2: 4) */
     int    sap_block[4];     /* SAP block extents (default 2,2,2,2) */
-    int    sap_block_iters;  /* GMRES steps per SAP block solve (Sec. 4: 10) */
+    int    sap_block_iters;  /* GMRES steps per SAP block solve (Sec. 4: 10; 1..32) */
     double sap_block_tol;    /* block residual reduction (Sec. 4: 1e-1) */
     int    gmres_smooth_iters; /* GMRES smoother steps per smoothing step (4) */
     double inner_tol;        /* FGMRES relative residual (Table 2: 1e-1) */
@@ -106,10 +106,13 @@ typedef struct qcd_params {
                                 memory; 2 Krylov basis in shared memory; 3 Krylov basis
                                 in global memory (any coarse lattice).  A forced layout
                                 that does not fit returns EINVAL. */
-    int    coarse_tensor;    /* 1 (default): FP32 coarse-stencil applies of the level-1
-                                operator (2 Nv a multiple of 8) on the tensor cores, TF32
-                                inputs split in big + small parts (three products, FP32
-                                accumulation); 0: FP32 FMA units */
+    int    coarse_tensor;    /* FP32 coarse-stencil applies of the level-1 operator:
+                                0 (default) on the FMA units, stencil blocks and vectors
+                                staged into shared memory by bulk asynchronous copies
+                                (16-byte aligned vectors; plain loads otherwise); 1 on the
+                                tensor cores (mma.sync, 2 Nv a multiple of 8), TF32 inputs
+                                split in big + small parts (three products, FP32
+                                accumulation) -- 3x slower than 0 on 16 right-hand sides */
     int    sap_half;         /* 1: FP32 SAP block solves on 16-site blocks store their
                                 Krylov basis in FP16 (half the shared memory, more block
                                 solves resident; default 0) */
@@ -374,6 +377,12 @@ int qcd_stats_read(qcd_kernel_stat* out, int max, int* n);
  * (operator applies plus Gram-Schmidt) turns them into the flops actually
  * executed.  Waits for nothing: read after synchronising.  EINVAL on NULL. */
 int qcd_stats_sap_work(double* site_steps, double* site_steps_tri);
+
+/* Number of bounded device-side waits that gave up since the library was
+ * loaded (a kernel waiting on its own asynchronous shared-memory copies gives
+ * up after about half a second, skips its output and counts itself here; 0
+ * in every correct run).  ECUDA if the read fails, EINVAL on NULL. */
+int qcd_stats_wait_timeouts(unsigned long long* n);
 
 /* Measured fused multiply-add throughput of the current device in TFLOP/s
  * (2 flops per FMA) for prec QCD_FP32 or QCD_FP64 (FMA units), or prec 2 for

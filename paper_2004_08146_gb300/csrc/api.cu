@@ -1413,7 +1413,7 @@ void qcd_default_params(qcd_params* p) {
     for (int mu = 0; mu < 4; ++mu) p->agg2[mu] = 2;
     p->nu2 = 2;
     p->coarse_layout = 0;
-    p->coarse_tensor = 1;
+    p->coarse_tensor = 0;
     p->sap_half = 0;
     p->confirm = 2;
 }

@@ -409,7 +409,7 @@ void small_harmonic_eig_inc(const double2* G, const double2* H, int m, int ld, i
                             double2* state, int* status, cudaStream_t st) {
     KTimer kt(m0 == 0 ? "harmonic_eig_full" : "harmonic_eig_inc", 0.0, 0.0, st);
     const size_t sm = (size_t)2 * m * m * sizeof(float2);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(harmonic_eig_inc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(harmonic_eig_inc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     harmonic_eig_inc_kernel<<<1, kTE, sm, st>>>(G, H, m, ld, m0, mu, S, state, status);
 }
 void small_refine_targets(const double2* state, int m, int ld, double2* S, const double* mu, double* mu_out,

@@ -407,7 +407,7 @@ void ff_transform_inplace(void* A, int m, const double2* C, int p, size_t n, voi
     float4* Cf = (float4*)cf_scratch;
     ff_split_kernel<<<(m * p + 255) / 256, 256, 0, st>>>(C, Cf, m * p, 1.0);
     const size_t sm = (size_t)m * kTile * sizeof(float4);
-    if (sm > 48 * 1024)
+    if (sm + 1024 > 48 * 1024)
         cudaFuncSetAttribute(ff_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const size_t ntiles = (n + kTile - 1) / kTile;
     const int grid = (int)std::min<size_t>(ntiles, (size_t)sm_count() * 4);

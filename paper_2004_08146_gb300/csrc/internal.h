@@ -199,6 +199,8 @@ bool sap_needs_scratch(const Blocking& B);
 // [sum bs k, sum bs k (k + 1) / 2] over the block solves since the reset.
 void sap_work_reset();
 void sap_work_read(double out[2]);
+// bounded shared-memory waits that gave up (since the library was loaded)
+unsigned long long wait_timeouts_read();
 // FP32 / FP64 fused multiply-add throughput of the current device (TFLOP/s)
 double fma_peak_tflops(int prec, cudaStream_t st);
 size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters);

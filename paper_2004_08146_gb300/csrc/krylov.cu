@@ -683,7 +683,7 @@ static int launch_coarse(const Coarse& c, int op, int nrhs, const void* b, void*
     cudaMemsetAsync(a.tot, 0, sizeof(double2) * 4 * npair, st);
     auto kern = coarse_gmres_kernel<Z, R>;
     const size_t sm = md.smem;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
     if (per_sm < 1) return -1;

@@ -146,6 +146,68 @@ __global__ void restrict_kernel(Geom g, Blocking B, int nv, const Z* __restrict_
     }
 }
 
+// One CTA per (aggregate, chirality, chunk of RC right-hand sides): the
+// aggregate's half of each fine vector (nloc = 6 x block sites entries) is
+// gathered into shared memory once ([rhs][d], conflict-free for consecutive
+// d), then the warps take the nv vectors P_i in turn, so every fine entry is
+// read from memory once and every entry of P once per chunk.
+template <typename Z, typename R, int RC>
+__global__ void __launch_bounds__(256) restrict_agg_kernel(Geom g, Blocking B, int nv, const Z* __restrict__ P,
+                                                           const Z* __restrict__ r, Z* __restrict__ xc, int nrhs,
+                                                           const int* __restrict__ act) {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    Z* rs = reinterpret_cast<Z*>(rsm);   // [RC][nloc]
+    const int nc = 2 * nv;
+    const int nloc = B.bs * 6;
+    const int blk = blockIdx.x >> 1, chi = blockIdx.x & 1;
+    const int j0 = blockIdx.y * RC;
+    const size_t fstride = (size_t)g.V * 12;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    for (int e = tid; e < nloc * RC; e += blockDim.x) {
+        const int q = e / nloc, d = e % nloc, j = j0 + q;
+        Z v;
+        v.x = 0;
+        v.y = 0;
+        if (j < nrhs && (act == nullptr || act[j])) {
+            const int l = d / 6, sc = d % 6;
+            v = r[(size_t)j * fstride + (size_t)block_fine_site(g, B, blk, l) * 12 + 6 * chi + sc];
+        }
+        rs[(size_t)q * nloc + d] = v;
+    }
+    __syncthreads();
+    for (int i = warp; i < nv; i += nwarp) {
+        const Z* p = P + (((size_t)blk * 2 + chi) * nv + i) * nloc;
+        R re[RC], im[RC];
+#pragma unroll
+        for (int q = 0; q < RC; ++q) { re[q] = 0; im[q] = 0; }
+        for (int d = lane; d < nloc; d += 32) {
+            const Z a = p[d];
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                const Z b = rs[(size_t)q * nloc + d];
+                re[q] += a.x * b.x + a.y * b.y;
+                im[q] += a.x * b.y - a.y * b.x;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RC; ++q) {
+            re[q] = warp_sum(re[q]);
+            im[q] = warp_sum(im[q]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                const int j = j0 + q;
+                if (j >= nrhs || (act != nullptr && !act[j])) continue;
+                Z o;
+                o.x = re[q];
+                o.y = im[q];
+                xc[(size_t)j * B.nb * nc + (size_t)blk * nc + chi * nv + i] = o;
+            }
+        }
+    }
+}
+
 // One thread per fine degree of freedom of an aggregate (coarse site,
 // chirality, local index d); the nv entries P_i[d] are read once per chunk of
 // kProlongRC right-hand sides.
@@ -396,6 +458,169 @@ __global__ void coarse_apply_mrhs_kernel(Geom gc, int nc, const Z* __restrict__ 
         const R tj = (R)tau.t[j];
         const Z xv = xs[(size_t)r * rc + jj];        // direction 0 is the site itself
         Z o = acc[k];
+        if (op == QCD_OP_D) { o -= (tj * sg) * xv; }
+        else { o = sg * o; o -= tj * xv; }
+        y[(size_t)j * vstride + (size_t)s * nc + r] = o;
+    }
+}
+
+// ---- asynchronous bulk copies (TMA engine) into shared memory, completion
+// tracked by an mbarrier.  Every wait is bounded in time: a wait that gives up
+// counts itself in g_wait_timeouts and the caller skips its work.
+__device__ unsigned long long g_wait_timeouts;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared copy of `bytes` (multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for phase `parity` of the barrier, giving up after ~0.5 s of clock
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > (1ll << 30)) {
+            atomicAdd(&g_wait_timeouts, 1ull);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// FP32 coarse stencil on up to kBulkR right-hand sides per CTA, one coarse
+// site per CTA.  The 9 stencil blocks A_d (nc x nc complex, contiguous) and
+// the matching neighbour vectors (nc complex per right-hand side) stream
+// through two shared-memory stages filled by bulk asynchronous copies, so
+// each block is read from HBM exactly once while the previous one is
+// multiplied.  Thread (row r, group q) accumulates row r of y for the 8
+// right-hand sides 8q .. 8q+7: per column one block entry and eight
+// broadcast vector entries feed 32 FMAs.
+constexpr int kBulkR = 16;
+constexpr int kBulkG = 8;   // right-hand sides per thread
+
+__host__ __device__ inline size_t coarse_bulk_stage_bytes(int nc) { return sizeof(float2) * ((size_t)nc * nc + (size_t)kBulkR * nc); }
+size_t coarse_bulk_smem(int nc) { return 2 * coarse_bulk_stage_bytes(nc); }
+
+__global__ void __launch_bounds__(128) coarse_apply_bulk_kernel(Geom gc, int nc, const float2* __restrict__ A,
+                                                                const float2* __restrict__ x,
+                                                                float2* __restrict__ y, int op, Shifts tau,
+                                                                int nrhs) {
+    extern __shared__ __align__(128) unsigned char bsm[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int nbr[9];
+    __shared__ int fail;
+    const int s = blockIdx.x, j0 = blockIdx.y * kBulkR;
+    const int nr = min(kBulkR, nrhs - j0);
+    const int tid = threadIdx.x;
+    const size_t vstride = (size_t)gc.V * nc;
+    const size_t stage = coarse_bulk_stage_bytes(nc);
+    if (tid < 9) {
+        int c[4];
+        site_coords(gc, s, c);
+        int sn = s;
+        if (tid > 0) {
+            const int mu = (tid - 1) & 3, step = tid <= 4 ? 1 : -1;
+            c[mu] = (c[mu] + step + gc.L[mu]) % gc.L[mu];
+            sn = site_index(gc, c);
+        }
+        nbr[tid] = sn;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const unsigned ablk = (unsigned)(sizeof(float2) * nc * nc), vseg = (unsigned)(sizeof(float2) * nc);
+    // stage d: block A_d and the neighbour vectors x_j(nbr[d]), j < nr
+    auto issue = [&](int d) {
+        unsigned char* buf = bsm + (d & 1) * stage;
+        if (tid == 0) {
+            fence_async_smem();
+            mbar_expect_tx(&bar[d & 1], ablk + (unsigned)nr * vseg);
+        }
+        __syncwarp();
+        if (tid < 32) {
+            if (tid == 0) bulk_g2s(buf, A + ((size_t)s * 9 + d) * nc * nc, ablk, &bar[d & 1]);
+            for (int j = tid; j < nr; j += 32)
+                bulk_g2s(buf + ablk + (size_t)j * vseg, x + (size_t)(j0 + j) * vstride + (size_t)nbr[d] * nc, vseg,
+                         &bar[d & 1]);
+        }
+    };
+    issue(0);
+    issue(1);
+    const int r = tid % nc, q = tid / nc;
+    const bool active = q * kBulkG < nr;
+    float2 acc[kBulkG], xself[kBulkG];
+#pragma unroll
+    for (int k = 0; k < kBulkG; ++k) { acc[k] = make_float2(0.f, 0.f); xself[k] = make_float2(0.f, 0.f); }
+    for (int d = 0; d < 9; ++d) {
+        const unsigned char* buf = bsm + (d & 1) * stage;
+        if (!mbar_wait(&bar[d & 1], (unsigned)((d >> 1) & 1))) fail = 1;
+        __syncthreads();
+        if (fail) {
+            // copies may still be in flight into this CTA's shared memory
+            // (stages d and d + 1): wait for them once more, bounded, then
+            // leave without writing y
+            if (tid == 0) {
+                mbar_wait(&bar[d & 1], (unsigned)((d >> 1) & 1));
+                if (d + 1 < 9) mbar_wait(&bar[(d + 1) & 1], (unsigned)(((d + 1) >> 1) & 1));
+            }
+            __syncthreads();
+            return;
+        }
+        const float2* As = reinterpret_cast<const float2*>(buf);
+        const float2* Xs = reinterpret_cast<const float2*>(buf + ablk) + (size_t)q * kBulkG * nc;
+        if (active) {
+            if (d == 0) {
+#pragma unroll
+                for (int k = 0; k < kBulkG; ++k) xself[k] = Xs[(size_t)k * nc + r];
+            }
+#pragma unroll 4
+            for (int col = 0; col < nc; ++col) {
+                const float2 a = As[(size_t)col * nc + r];
+#pragma unroll
+                for (int k = 0; k < kBulkG; ++k) {
+                    const float2 xv = Xs[(size_t)k * nc + col];
+                    acc[k].x = fmaf(a.x, xv.x, fmaf(-a.y, xv.y, acc[k].x));
+                    acc[k].y = fmaf(a.x, xv.y, fmaf(a.y, xv.x, acc[k].y));
+                }
+            }
+        }
+        __syncthreads();   // stage d & 1 no longer read
+        if (d + 2 < 9) issue(d + 2);
+    }
+    if (!active) return;
+    const float sg = r < nc / 2 ? 1.f : -1.f;
+#pragma unroll
+    for (int k = 0; k < kBulkG; ++k) {
+        const int j = j0 + q * kBulkG + k;
+        if (j >= nrhs) break;
+        const float tj = (float)tau.t[j];
+        float2 o = acc[k];
+        const float2 xv = xself[k];
         if (op == QCD_OP_D) { o -= (tj * sg) * xv; }
         else { o = sg * o; o -= tj * xv; }
         y[(size_t)j * vstride + (size_t)s * nc + r] = o;
@@ -1255,14 +1480,14 @@ void mg_build_coarse(const FineOp& f, Coarse& c, cudaStream_t st, bool fp32_only
     if (fp32_only) {
         // the FP32 operator straight from P32, U32 and the FP32 clover; the
         // FP64 one is rebuilt on demand (Coarse::a64_stale)
-        if (sm > 48 * 1024)
+        if (sm + 1024 > 48 * 1024)
             cudaFuncSetAttribute(build_coarse_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         KTimer kt("build_coarse_f32", 0.0, 0.0, st);
         build_coarse_kernel<float><<<grid, 256, sm, st>>>(f.g, c.B, c.nv, f.U32, f.A32, c.P32, c.A32, chunk);
         c.a64_stale = true;
         return;
     }
-    if (sm > 48 * 1024)
+    if (sm + 1024 > 48 * 1024)
         cudaFuncSetAttribute(build_coarse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     KTimer kt("build_coarse", 0.0, 0.0, st);
     build_coarse_kernel<double><<<grid, 256, sm, st>>>(f.g, c.B, c.nv, f.U64, f.A64, c.P64, c.A64, chunk);
@@ -1278,9 +1503,31 @@ void mg_restrict(const FineOp& f, const Coarse& c, int prec, int nrhs, const voi
     int grid = grid_for(warps * 32);
     const double es = prec == QCD_FP64 ? 16.0 : 8.0;
     const double nfine = (double)f.g.V * 12;
-    const double chunks = (nrhs + kRestrictRC - 1) / kRestrictRC;
+    const double chunks = (nrhs + (prec == QCD_FP64 ? 3 : 7)) / (prec == QCD_FP64 ? 4 : 8);
     KTimer kt(prec == QCD_FP64 ? "restrict_f64" : "restrict_f32",
               es * (nfine * c.nv * chunks + nrhs * (nfine + (double)c.gc.V * c.nc)), 8.0 * nfine * c.nv * nrhs, st);
+    // aggregate kernel while one chunk of the gathered fine vectors fits
+    // in shared memory (8 FP32 / 4 FP64 right-hand sides per chunk)
+    const int nloc = c.B.bs * 6;
+    const size_t sm = (size_t)nloc * 8 * sizeof(float2);
+    if (sm <= 160 * 1024) {
+        const int rcs = prec == QCD_FP64 ? 4 : 8;
+        const dim3 ag(c.B.nb * 2, (nrhs + rcs - 1) / rcs);
+        if (prec == QCD_FP64) {
+            if (sm + 1024 > 48 * 1024)
+                cudaFuncSetAttribute(restrict_agg_kernel<double2, double, 4>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            restrict_agg_kernel<double2, double, 4><<<ag, 256, sm, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)r,
+                                                                        (double2*)xc, nrhs, act);
+        } else {
+            if (sm + 1024 > 48 * 1024)
+                cudaFuncSetAttribute(restrict_agg_kernel<float2, float, 8>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            restrict_agg_kernel<float2, float, 8><<<ag, 256, sm, st>>>(f.g, c.B, c.nv, c.P32, (const float2*)r,
+                                                                      (float2*)xc, nrhs, act);
+        }
+        return;
+    }
     if (prec == QCD_FP64)
         restrict_kernel<double2, double><<<grid, 256, 0, st>>>(f.g, c.B, c.nv, c.P64, (const double2*)r, (double2*)xc, nrhs, act);
     else
@@ -1308,17 +1555,29 @@ void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, vo
                   cudaStream_t st, bool tensor) {
     Shifts sh{};
     for (int j = 0; j < nrhs; ++j) sh.t[j] = tau ? tau[j] : 0.0;
-    size_t n = (size_t)nrhs * c.gc.V * c.nc;
     const double es = prec == QCD_FP64 ? 16.0 : 8.0;
     const bool tc = prec == QCD_FP32 && tensor && c.nc % 8 == 0 && c.nc <= 64;
-    KTimer kt(prec == QCD_FP64 ? "coarse_apply_f64" : (tc ? "coarse_apply_tc" : "coarse_apply_f32"),
-              es * ((double)c.gc.V * 9 * c.nc * c.nc * ((nrhs + kCoarseRC - 1) / kCoarseRC) +
+    // bulk-copy kernel: FP32, 16-byte aligned vectors, 2 nc threads
+    const bool bulk = prec == QCD_FP32 && !tc && c.nc <= 64 && ((uintptr_t)x & 15) == 0 &&
+                      ((uintptr_t)c.A32 & 15) == 0;
+    const int rchunk = bulk ? kBulkR : (tc ? kTcR : kCoarseRC);
+    KTimer kt(prec == QCD_FP64 ? "coarse_apply_f64"
+                               : (tc ? "coarse_apply_tc" : (bulk ? "coarse_apply_bulk" : "coarse_apply_f32")),
+              es * ((double)c.gc.V * 9 * c.nc * c.nc * ((nrhs + rchunk - 1) / rchunk) +
                     2.0 * nrhs * c.gc.V * c.nc),
               8.0 * 9 * c.nc * c.nc * (double)c.gc.V * nrhs, st);
-    (void)n;
+    if (bulk) {
+        const size_t sm = coarse_bulk_smem(c.nc);
+        if (sm + 1024 > 48 * 1024)
+            cudaFuncSetAttribute(coarse_apply_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        const dim3 grid(c.gc.V, (nrhs + kBulkR - 1) / kBulkR);
+        coarse_apply_bulk_kernel<<<grid, 2 * c.nc, sm, st>>>(c.gc, c.nc, c.A32, (const float2*)x, (float2*)y, op, sh,
+                                                            nrhs);
+        return;
+    }
     if (prec == QCD_FP32 && tensor && c.nc % 8 == 0 && c.nc <= 64) {
         const size_t sm = coarse_tc_smem(c.nc);
-        if (sm > 48 * 1024)
+        if (sm + 1024 > 48 * 1024)
             cudaFuncSetAttribute(coarse_apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         const dim3 grid(c.gc.V, (nrhs + kTcR - 1) / kTcR);
         coarse_apply_tc_kernel<<<grid, 32 * (c.nc / 8), sm, st>>>(c.gc, c.nc, c.A32, (const float2*)x, (float2*)y,
@@ -1332,13 +1591,13 @@ void coarse_apply(const Coarse& c, int prec, int op, int nrhs, const void* x, vo
     const size_t ebytes = prec == QCD_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t sm = (size_t)9 * c.nc * rc * ebytes;
     if (prec == QCD_FP64) {
-        if (sm > 48 * 1024)
+        if (sm + 1024 > 48 * 1024)
             cudaFuncSetAttribute(coarse_apply_mrhs_kernel<double2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         coarse_apply_mrhs_kernel<double2, double><<<grid, threads, sm, st>>>(c.gc, c.nc, c.A64, (const double2*)x,
                                                                             (double2*)y, op, sh, nrhs, rc);
     } else {
-        if (sm > 48 * 1024)
+        if (sm + 1024 > 48 * 1024)
             cudaFuncSetAttribute(coarse_apply_mrhs_kernel<float2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         coarse_apply_mrhs_kernel<float2, float><<<grid, threads, sm, st>>>(c.gc, c.nc, c.A32, (const float2*)x,
@@ -1352,6 +1611,12 @@ void sap_work_reset() {
     static const unsigned long long zero[2][64] = {};
     cudaMemcpyToSymbol(g_sap_work, zero, sizeof(zero));
 }
+unsigned long long wait_timeouts_read() {
+    unsigned long long h = 0;
+    cudaMemcpyFromSymbol(&h, g_wait_timeouts, sizeof(h));
+    return h;
+}
+
 void sap_work_read(double out[2]) {
     unsigned long long h[2][64];
     cudaMemcpyFromSymbol(h, g_sap_work, sizeof(h));
@@ -1383,17 +1648,17 @@ void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op
         dim3 grid(sp.ncol[colour], nrhs);
         if (prec == QCD_FP64) {
             const size_t sm = sap_layout<double>(16, iters).total;
-            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             sap_chi_kernel<double, double2><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
                 sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
         } else if (half) {
             const size_t sm = sap_layout<float>(16, iters, sizeof(__half2)).total;
-            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             sap_chi_kernel<float, __half2><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
                 sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
         } else {
             const size_t sm = sap_layout<float>(16, iters).total;
-            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             sap_chi_kernel<float, float2><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
                 sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
         }
@@ -1404,12 +1669,12 @@ void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op
         dim3 grid(sp.ncol[colour], nrhs);
         if (prec == QCD_FP64) {
             const size_t sm = sap_layout<double>(32, iters).total;
-            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             sap_warp_kernel<double, 32><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
                 sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
         } else {
             const size_t sm = sap_layout<float>(32, iters).total;
-            if (sm > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_warp_kernel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             sap_warp_kernel<float, 32><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
                 sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
         }
@@ -1421,11 +1686,11 @@ void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op
                 sizeof(double) * iters + 4 * sizeof(int) +
                 (size_t)bs * 12 * (prec == QCD_FP64 ? sizeof(double2) : sizeof(float2));
     if (prec == QCD_FP64) {
-        if (sm > 48 * 1024) cudaFuncSetAttribute(sap_block_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_block_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         sap_block_kernel<double><<<grid, bs, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour], op, sh,
                                                        (const double2*)r, (double2*)x, iters, tol, (double2*)scratch, act);
     } else {
-        if (sm > 48 * 1024) cudaFuncSetAttribute(sap_block_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_block_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         sap_block_kernel<float><<<grid, bs, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour], op, sh,
                                                       (const float2*)r, (float2*)x, iters, tol, (float2*)scratch, act);
     }

@@ -165,6 +165,12 @@ int qcd_stats_sap_work(double* site_steps, double* site_steps_tri) {
     return QCD_OK;
 }
 
+int qcd_stats_wait_timeouts(unsigned long long* n) {
+    if (!n) return QCD_EINVAL;
+    *n = qcd::wait_timeouts_read();
+    return cudaGetLastError() == cudaSuccess ? QCD_OK : QCD_ECUDA;
+}
+
 int qcd_fma_peak(int prec, double* tflops) {
     if (!tflops || (prec != QCD_FP64 && prec != QCD_FP32 && prec != 2)) return QCD_EINVAL;
     *tflops = qcd::fma_peak_tflops(prec, nullptr);

@@ -123,6 +123,7 @@ _SIGS = {
     "qcd_stats_reset": (_I, [_I, ctypes.c_char_p]),
     "qcd_stats_read": (_I, [ctypes.POINTER(qcd_kernel_stat), _I, _IP]),
     "qcd_stats_sap_work": (_I, [_DP, _DP]),
+    "qcd_stats_wait_timeouts": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "qcd_fma_peak": (_I, [_I, _DP]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -175,6 +176,15 @@ def qcd_stats_sap_work():
     if rc != QCD_OK:
         raise QcdError(rc, "qcd_stats_sap_work")
     return a.value, b.value
+
+
+def qcd_stats_wait_timeouts():
+    """Bounded device-side waits that gave up since the library was loaded (0 in a correct run)."""
+    n = ctypes.c_ulonglong(0)
+    rc = _lib.qcd_stats_wait_timeouts(ctypes.byref(n))
+    if rc != QCD_OK:
+        raise QcdError(rc, "qcd_stats_wait_timeouts")
+    return n.value
 
 
 def qcd_fma_peak(prec):

@@ -78,7 +78,7 @@ def test_calls_without_gauge_fail_cleanly():
 
 
 @pytest.mark.parametrize("bad", [dict(extraction=2), dict(update_every=-1), dict(block=0), dict(block=33),
-                                 dict(m_max=106, block=8), dict(m_max=112), dict(sap_block_iters=0),
+                                 dict(m_max=106, block=8), dict(m_max=112), dict(sap_block_iters=0), dict(sap_block_iters=33),
                                  dict(levels=4), dict(levels=1), dict(nv2=0), dict(nv2=33),
                                  dict(agg2=(2, 0, 2, 2)), dict(nu2=-1), dict(coarse_layout=4),
                                  dict(coarse_layout=-1), dict(coarse_tensor=2), dict(sap_half=-1),

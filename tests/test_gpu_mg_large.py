@@ -81,15 +81,20 @@ def test_restrict_prolong_apply(setting, prec, tol):
         ctx.qcd_coarse_apply(op, prec, nrhs, dev(c, dt), y, taus)
         got = host(y).reshape(nrhs, -1)
         for j in range(nrhs):
-            # FP32 applies run on the tensor cores (3xTF32): 1e-5; FP64 on the FMA units
+            # FP32 applies: 1e-5 (FMA units, bulk-copy staging); FP64: the FP64 tolerance
             assert relerr(got[j], h.coarse.apply(c[j], taus[j], form).reshape(-1)) < (tol if prec == 0 else 1e-5)
 
 
-@pytest.mark.parametrize("tensor,tol", [(0, 2e-6), (1, 1e-5)])
-def test_coarse_apply_many_rhs_tensor_and_fma(setting, tensor, tol):
+@pytest.mark.parametrize("tensor,offset,kernel,tol", [(0, 0, "coarse_apply_bulk", 2e-6),
+                                                      (0, 1, "coarse_apply_f32", 2e-6),
+                                                      (1, 0, "coarse_apply_tc", 1e-5)])
+def test_coarse_apply_many_rhs_tensor_and_fma(setting, tensor, offset, kernel, tol):
     """The FP32 coarse stencil on 20 right-hand sides (two chunks of the
-    multi-right-hand-side kernels) on the FMA units and on the tensor cores
-    (3xTF32 split), both forms, against the oracle's stencil."""
+    multi-right-hand-side kernels), both forms, against the oracle's stencil:
+    FMA units with the stencil blocks and vectors staged by bulk asynchronous
+    copies (16-byte aligned vectors), FMA units with plain loads (vectors one
+    complex64 off a 16-byte boundary), and tensor cores (3xTF32 split).  No
+    bounded wait gives up."""
     from paper_2004_08146_gb300 import qcd
     torch = torch_cuda()
     ctx, h = setting["ctx"], setting["h"]
@@ -100,12 +105,19 @@ def test_coarse_apply_many_rhs_tensor_and_fma(setting, tensor, tol):
     nco = info["coarse_sites"] * 2 * setting["nv"]
     c = synth.complex_gaussian((nrhs, nco), 155)
     taus = [0.01 * j - 0.1 for j in range(nrhs)]
+    t0 = qcd.qcd_stats_wait_timeouts()
+    qcd.qcd_stats_reset(1)
     for op, form in ((qcd.QCD_OP_D, 'g5'), (qcd.QCD_OP_Q, 'Q')):
+        xin = torch.zeros(nrhs * nco + offset, dtype=torch.complex64, device="cuda")
+        xin[offset:] = dev(c, np.complex64)
         y = torch.zeros(nrhs * nco, dtype=torch.complex64, device="cuda")
-        ctx.qcd_coarse_apply(op, 1, nrhs, dev(c, np.complex64), y, taus)
+        ctx.qcd_coarse_apply(op, 1, nrhs, xin[offset:], y, taus)
         got = host(y).reshape(nrhs, -1)
         for j in range(nrhs):
             assert relerr(got[j], h.coarse.apply(c[j], taus[j], form).reshape(-1)) < tol, (form, j)
+    names = {r["name"]: r["launches"] for r in qcd.qcd_stats_read()}
+    assert names.get(kernel, 0) == 2, names
+    assert qcd.qcd_stats_wait_timeouts() == t0
     ctx.qcd_set_params(qcd.default_params(sap_block=SAP, sap_block_tol=-1.0, coarse_tol=0.0, precision=0,
                                           setup_iters=1, **CYCLE))
 
