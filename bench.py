@@ -9,9 +9,10 @@ Also reported: the same step in plain FP64; the end-to-end time through the
 C ABI from host buffers; the fine-stencil bandwidth on a 64 x 32^3 lattice;
 the live roofline of the dominant kernel (HBM and, for the SAP block solves,
 FP32 ALU against the measured FMA peak); the 64 x 32^3 three-level workload
-(100 pairs, mixed precision) timed once after a warm-up solve; and the CPU
-oracle timed on per-operation samples on the host's cores.  Prints one JSON
-line (rank 0).
+(mixed precision, timed once after a warm-up; 16 pairs by default so that the
+run ends within minutes, --large-k 100 for the workload's 100, --only-large
+for that measurement alone); and the CPU oracle timed on per-operation
+samples on the host's cores.  Prints one JSON line (rank 0).
 
 usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -73,6 +74,11 @@ def parse():
     ap.add_argument("--no-large-workload", action="store_true",
                     help="skip the 64 x 32^3 three-level measurement")
     ap.add_argument("--large-workload", default="c4_64x32c3")
+    ap.add_argument("--large-k", type=int, default=16,
+                    help="eigenpairs of the large-workload measurement (the workload lists 100; "
+                         "the default run times 16 so that it ends within minutes)")
+    ap.add_argument("--only-large", action="store_true",
+                    help="run only the large-workload measurement and print it")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--oracle-ops", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -100,8 +106,10 @@ def max_over_ranks(value, device=None):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of each kernel as it stands now, for the roofline's
 # "traffic"; a kernel that changes is taken out of this table until it is
-# captured again (the field is then null).
-NCU_TRAFFIC = {}
+# captured again (the field is then null).  sap_block_f32: two launches of
+# sap_chi_kernel<float, float2> in the 16 x 8^3 step (k = 4), 4.7834 and
+# 4.7839 MB read, 0 written (profiles/sap_chi_f32_c2_16x8c3.md).
+NCU_TRAFFIC = {"sap_block_f32": 4.7836e6}
 
 # Work model of the SAP block solves for the FP32-ALU roofline, per block
 # site and GMRES step j (0-based) of a block solve of k steps: the Dirichlet
@@ -333,6 +341,10 @@ def main():
     if args.coarse_stencil:
         print(json.dumps({"coarse_stencil": coarse_stencil_bench(qcd, synth, torch, devn, stream)}), flush=True)
         return
+    if args.only_large:
+        print(json.dumps({"large_workload": large_workload(qcd, synth, torch, devn, stream, workloads,
+                                                           args.large_workload, args.large_k)}), flush=True)
+        return
 
     def make(precision):
         p = workload_params(qcd, w, precision=precision)
@@ -461,7 +473,7 @@ def main():
     # ---- the 64 x 32^3 three-level workload, 100 pairs, mixed precision
     large = None
     if not args.no_large_workload and rank == 0:
-        large = large_workload(qcd, synth, torch, devn, stream, workloads, args.large_workload)
+        large = large_workload(qcd, synth, torch, devn, stream, workloads, args.large_workload, args.large_k)
 
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
@@ -521,14 +533,15 @@ def workload_params(qcd, w, **kw):
     return qcd.default_params(**p)
 
 
-def large_workload(qcd, synth, torch, devn, stream, workloads, name):
+def large_workload(qcd, synth, torch, devn, stream, workloads, name, k):
     """The 64 x 32^3 workload (2.1 M sites, 25 M unknowns; eps 0.6, c_sw 1.9),
-    three-level MG (4^4 then 2^4 aggregates, Nv = nv2 = 24), 100 pairs at
-    residual 1e-8, 16 targets per outer iteration, mixed precision: one
-    warm-up solve of 16 pairs, then one timed setup + eigensolve of the
-    workload's k (CUDA events on the library's stream, every kernel timed by
-    the library's accounting, clocks sampled)."""
+    three-level MG (4^4 then 2^4 aggregates, Nv = nv2 = 24), k pairs at
+    residual 1e-8 (the workload lists 100), 16 targets per outer iteration,
+    mixed precision: one warm-up setup and a 2-pair solve, then one timed
+    setup + eigensolve of k pairs (CUDA events on the library's stream, every
+    kernel timed by the library's accounting, clocks sampled)."""
     w = workloads.get(name)
+    w["k"] = int(k)
     dims = tuple(w["dims"])
     U = synth.gauge_field(dims, w["eps"], w["seed"])
     n = 12 * int(np.prod(dims))
@@ -539,7 +552,7 @@ def large_workload(qcd, synth, torch, devn, stream, workloads, name):
     t_gauge = time.perf_counter() - t0
     V = torch.zeros(w["k"] * n, dtype=torch.complex128, device=devn)
     ctx.qcd_mg_setup(w["nv"], w["agg"])                  # warm-up
-    ctx.qcd_eigs(16, 1e-8, V)
+    ctx.qcd_eigs(2, 1e-8, V)
     torch.cuda.synchronize()
     clocks = ClockSampler(devn.index or 0)
     qcd.qcd_stats_reset(1)

@@ -455,13 +455,26 @@ __global__ void __launch_bounds__(128) wilson_clover_kernel(
 // right-hand sides (CTA index = site block x nrhs + rhs), so the CTAs that
 // run together read the same links and clover blocks and all but the first
 // find them in L2: the links and clover are read from HBM about once per
-// site block instead of once per right-hand side.
+// site block instead of once per right-hand side.  With tb > 0 the site
+// blocks are visited time-fastest within bricks of tb time slices
+// (block u: t = (u / (tb ns)) tb + u % tb, spatial block (u / tb) % ns of
+// ns = L1 L2 L3 / 128), so the neighbours of a block in every direction are
+// read by CTAs a few hundred launches apart and still sit in L2; only the
+// time neighbours across a brick face are fetched from DRAM again.
 __global__ void __launch_bounds__(128) wilson_clover_soa_kernel(
     float2* __restrict__ out, const float2* __restrict__ in, const float2* __restrict__ b,
     const float2* __restrict__ Us, const float4* __restrict__ As, Geom g, int op, Shifts tau, size_t stride,
-    const int* __restrict__ act, int nrhs) {
+    const int* __restrict__ act, int nrhs, int tb) {
     const int j = (int)(blockIdx.x % nrhs);
-    const int s = (int)((blockIdx.x / nrhs) * blockDim.x + threadIdx.x);
+    const unsigned u = blockIdx.x / nrhs;
+    int s;
+    if (tb > 0) {
+        const unsigned vs = (unsigned)(g.L[1] * g.L[2] * g.L[3]), ns = vs / 128u;
+        const unsigned t = (u / (tb * ns)) * tb + u % tb, sb = (u / tb) % ns;
+        s = (int)(t * vs + sb * 128u + threadIdx.x);
+    } else {
+        s = (int)(u * blockDim.x + threadIdx.x);
+    }
     if (s >= g.V) return;
     if (act != nullptr && !act[j]) return;
     in += j * stride;
@@ -609,8 +622,12 @@ void launch_dirac(const FineOp& f, int op, int nrhs, const void* in, void* out, 
         const double bytes = (double)f.g.V * (nrhs * (b ? 72.0 : 48.0) + 144.0) * sizeof(R);
         KTimer kt("wilson_clover_f32", bytes, 1824.0 * f.g.V * nrhs, st);
         const unsigned gsoa = (unsigned)((f.g.V + 127) / 128) * (unsigned)nrhs;
+        // several right-hand sides: time-fastest bricks of 8 time slices
+        // (needs whole 128-site blocks per time slice and L0 a multiple of 8)
+        const int vs = f.g.L[1] * f.g.L[2] * f.g.L[3];
+        const int tb = (nrhs > 1 && vs % 128 == 0 && f.g.L[0] % 8 == 0) ? 8 : 0;
         wilson_clover_soa_kernel<<<gsoa, 128, 0, st>>>((float2*)out, (const float2*)in, (const float2*)b, f.U32s,
-                                                       f.A32s, f.g, op, sh, (size_t)f.g.V * 12, act, nrhs);
+                                                       f.A32s, f.g, op, sh, (size_t)f.g.V * 12, act, nrhs, tb);
         return;
     }
     const double bytes = (double)f.g.V * (nrhs * (b ? 72.0 : 48.0) + 144.0) * sizeof(R);

@@ -110,16 +110,31 @@ __global__ void ff_multidot_kernel(const float4* __restrict__ X, size_t xstride_
     const size_t chunk = (n + nsplit - 1) / nsplit;
     const size_t lo = (size_t)blockIdx.y * chunk;
     const size_t hi = lo + chunk < n ? lo + chunk : n;
-    acc_t re, im;
-    for (size_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-        const float4 a = x[k], b = y[k];
+    // two independent accumulator pairs (even / odd strides): twice the
+    // loads in flight and two interleaved error-free chains per thread
+    acc_t re, im, re1, im1;
+    const size_t bd = blockDim.x;
+    size_t k = lo + threadIdx.x;
+    for (; k + bd < hi; k += 2 * bd) {
+        const float4 a = x[k], b = y[k], a1 = x[k + bd], b1 = y[k + bd];
         // conj(a) b: re = ar br + ai bi, im = ar bi - ai br
+        re.mac(a.x, a.z, b.x, b.z);
+        re1.mac(a1.x, a1.z, b1.x, b1.z);
+        im.mac(a.x, a.z, b.y, b.w);
+        im1.mac(a1.x, a1.z, b1.y, b1.w);
+        re.mac(a.y, a.w, b.y, b.w);
+        re1.mac(a1.y, a1.w, b1.y, b1.w);
+        im.msub(a.y, a.w, b.x, b.z);
+        im1.msub(a1.y, a1.w, b1.x, b1.z);
+    }
+    if (k < hi) {
+        const float4 a = x[k], b = y[k];
         re.mac(a.x, a.z, b.x, b.z);
         re.mac(a.y, a.w, b.y, b.w);
         im.mac(a.x, a.z, b.y, b.w);
         im.msub(a.y, a.w, b.x, b.z);
     }
-    double dr = join(re.get()), di = join(im.get());
+    double dr = join(re.get()) + join(re1.get()), di = join(im.get()) + join(im1.get());
     dr = warp_sum(dr);
     di = warp_sum(di);
     __shared__ double sre[32], sim[32];

@@ -519,7 +519,15 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 constexpr int kBulkR = 16;
 constexpr int kBulkG = 8;   // right-hand sides per thread
 
-__host__ __device__ inline size_t coarse_bulk_stage_bytes(int nc) { return sizeof(float2) * ((size_t)nc * nc + (size_t)kBulkR * nc); }
+// stage: block A_d, then the vectors of right-hand sides 0..7, 16 bytes of
+// padding (the two thread groups' broadcast reads then fall in different
+// banks), then right-hand sides 8..15
+__host__ __device__ inline size_t coarse_bulk_stage_bytes(int nc) {
+    return sizeof(float2) * ((size_t)nc * nc + (size_t)kBulkR * nc) + 16;
+}
+__host__ __device__ inline size_t coarse_bulk_xoff(int nc, int j) {
+    return sizeof(float2) * ((size_t)nc * nc + (size_t)j * nc) + (j >= kBulkG ? 16 : 0);
+}
 size_t coarse_bulk_smem(int nc) { return 2 * coarse_bulk_stage_bytes(nc); }
 
 __global__ void __launch_bounds__(128) coarse_apply_bulk_kernel(Geom gc, int nc, const float2* __restrict__ A,
@@ -565,7 +573,7 @@ __global__ void __launch_bounds__(128) coarse_apply_bulk_kernel(Geom gc, int nc,
         if (tid < 32) {
             if (tid == 0) bulk_g2s(buf, A + ((size_t)s * 9 + d) * nc * nc, ablk, &bar[d & 1]);
             for (int j = tid; j < nr; j += 32)
-                bulk_g2s(buf + ablk + (size_t)j * vseg, x + (size_t)(j0 + j) * vstride + (size_t)nbr[d] * nc, vseg,
+                bulk_g2s(buf + coarse_bulk_xoff(nc, j), x + (size_t)(j0 + j) * vstride + (size_t)nbr[d] * nc, vseg,
                          &bar[d & 1]);
         }
     };
@@ -592,20 +600,23 @@ __global__ void __launch_bounds__(128) coarse_apply_bulk_kernel(Geom gc, int nc,
             return;
         }
         const float2* As = reinterpret_cast<const float2*>(buf);
-        const float2* Xs = reinterpret_cast<const float2*>(buf + ablk) + (size_t)q * kBulkG * nc;
+        const float2* Xs = reinterpret_cast<const float2*>(buf + coarse_bulk_xoff(nc, q * kBulkG));
         if (active) {
             if (d == 0) {
 #pragma unroll
                 for (int k = 0; k < kBulkG; ++k) xself[k] = Xs[(size_t)k * nc + r];
             }
-#pragma unroll 4
-            for (int col = 0; col < nc; ++col) {
-                const float2 a = As[(size_t)col * nc + r];
+            // two columns per step: one 16-byte broadcast load per right-hand side
+#pragma unroll 2
+            for (int col = 0; col < nc; col += 2) {
+                const float2 a0 = As[(size_t)col * nc + r], a1 = As[(size_t)(col + 1) * nc + r];
 #pragma unroll
                 for (int k = 0; k < kBulkG; ++k) {
-                    const float2 xv = Xs[(size_t)k * nc + col];
-                    acc[k].x = fmaf(a.x, xv.x, fmaf(-a.y, xv.y, acc[k].x));
-                    acc[k].y = fmaf(a.x, xv.y, fmaf(a.y, xv.x, acc[k].y));
+                    const float4 xv = *reinterpret_cast<const float4*>(Xs + (size_t)k * nc + col);
+                    acc[k].x = fmaf(a0.x, xv.x, fmaf(-a0.y, xv.y, acc[k].x));
+                    acc[k].y = fmaf(a0.x, xv.y, fmaf(a0.y, xv.x, acc[k].y));
+                    acc[k].x = fmaf(a1.x, xv.z, fmaf(-a1.y, xv.w, acc[k].x));
+                    acc[k].y = fmaf(a1.x, xv.w, fmaf(a1.y, xv.z, acc[k].y));
                 }
             }
         }

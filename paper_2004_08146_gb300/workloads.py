@@ -17,19 +17,22 @@ WORKLOADS = {
                       use_mg=1, agg=(2, 2, 2, 2), nv=8, sap=(2, 2, 2, 2), target=1e-2),
     # 32 x 16^3, two-level MG with 4^4 aggregates, Nv = 20, 100 pairs with 16
     # shifted systems (targets) per outer iteration, m_min 30 and m_max 50
-    # (Table 2), P rebuilt every 20 locks; m0 from the dense-proxy tuning.
+    # (Table 2), P rebuilt every 20 locks; SAP block solves in FP32 with the
+    # block Krylov basis stored in FP16; m0 from the dense-proxy tuning.
     "c3_32x16c3": dict(dims=(32, 16, 16, 16), eps=0.6, csw=1.7, m0=-1.1, seed=1003, k=100,
                        use_mg=1, agg=(4, 4, 4, 4), nv=20, sap=(2, 2, 2, 2), target=5e-3,
-                       block=16, m_min=30, m_max=50, update_every=20),
+                       block=16, m_min=30, m_max=50, update_every=20, sap_half=1),
     # 64 x 32^3 (2.1 M sites, 25 M unknowns), three-level MG: 4^4 aggregates
     # (Nv = 24) on the fine lattice, 2^4 aggregates (nv2 = 24) on the coarse
-    # one; 100 pairs with 16 targets per outer iteration, m_min 30, m_max 50.
+    # one; 100 pairs with 16 targets per outer iteration, m_min 30, m_max 50;
+    # FP16-stored SAP block basis (12 block solves per SM instead of 8).
     # m0 from tests/golden/tune_m0_dense.py (dense oracle spectra of 4^4 and
     # 8 x 4^3 proxies with the same eps and c_sw), limited to -1.0: at -1.2
     # the three-level correction solves stalled and no pair locked.
     "c4_64x32c3": dict(dims=(64, 32, 32, 32), eps=0.6, csw=1.9, m0=-1.0, seed=1004, k=100,
                        use_mg=1, agg=(4, 4, 4, 4), nv=24, sap=(2, 2, 2, 2), target=1e-3,
-                       block=16, m_min=30, m_max=50, update_every=20, levels=3, agg2=(2, 2, 2, 2), nv2=24),
+                       block=16, m_min=30, m_max=50, update_every=20, levels=3, agg2=(2, 2, 2, 2), nv2=24,
+                       sap_half=1),
 }
 
 
