@@ -35,7 +35,9 @@ extern "C" {
 #define QCD_ENOMEM    2   /* device allocation failed */
 #define QCD_ENOTSETUP 3   /* gauge field or multigrid hierarchy missing */
 #define QCD_ENOCONV   4   /* iteration cap reached; outputs hold the best iterate */
-#define QCD_ETIMEOUT  5   /* a device-side wait hit its iteration limit */
+#define QCD_ETIMEOUT  5   /* a bounded device-side wait gave up (reported by
+                             qcd_mg_setup, the shifted solves and qcd_eigs,
+                             which synchronise anyway; outputs unreliable) */
 #define QCD_ECUDA     6   /* a CUDA runtime call failed */
 
 /* Operators for qcd_apply */
@@ -383,6 +385,13 @@ int qcd_stats_sap_work(double* site_steps, double* site_steps_tri);
  * up after about half a second, skips its output and counts itself here; 0
  * in every correct run).  ECUDA if the read fails, EINVAL on NULL. */
 int qcd_stats_wait_timeouts(unsigned long long* n);
+
+/* Self-test of the bounded device-side waits: launches on the context's
+ * stream a one-warp kernel that waits on an mbarrier nothing arrives at; the
+ * wait gives up after 2^21 clocks (about 1 ms), counts itself, and the call
+ * returns QCD_ETIMEOUT with the context still usable (a later call that
+ * reports timeouts sees only newer ones).  Faults nothing, hangs nothing. */
+int qcd_selftest_wait_limit(qcd_ctx* ctx);
 
 /* Measured fused multiply-add throughput of the current device in TFLOP/s
  * (2 flops per FMA) for prec QCD_FP32 or QCD_FP64 (FMA units), or prec 2 for

@@ -1359,6 +1359,21 @@ void check_align(const void* p, const char* what) {
     if (((uintptr_t)p) & 15) throw QcdError(QCD_EINVAL, std::string(what) + " must be 16-byte aligned");
 }
 
+// Bounded device-side waits that gave up since the last check: the calls
+// that end with their results on the host (setup, solves, eigs) read the
+// library-wide counter after synchronising and report QCD_ETIMEOUT when it
+// grew (their outputs are then unreliable).
+std::atomic<unsigned long long> g_timeouts_seen{0};
+void check_wait_timeouts(qcd_ctx* ctx) {
+    CK(cudaStreamSynchronize(ctx->st));
+    const unsigned long long n = wait_timeouts_read();
+    unsigned long long seen = g_timeouts_seen.load();
+    if (n > seen) {
+        g_timeouts_seen.store(n);
+        throw QcdError(QCD_ETIMEOUT, "a device-side wait gave up (" + std::to_string(n - seen) + ")");
+    }
+}
+
 template <typename F>
 int guarded(qcd_ctx* ctx, F&& fn) {
     if (!ctx) return QCD_EINVAL;
@@ -1540,6 +1555,7 @@ int qcd_mg_setup(qcd_ctx* ctx, int Nv, const int block[4]) {
         if (!block) throw QcdError(QCD_EINVAL, "null block");
         if (Nv < 1 || Nv > 32) throw QcdError(QCD_EINVAL, "need 1 <= Nv <= 32");
         mg_setup_impl(ctx, Nv, block);
+        check_wait_timeouts(ctx);
         return QCD_OK;
     });
 }
@@ -1878,7 +1894,7 @@ int qcd_shifted_solve_batched(qcd_ctx* ctx, int nrhs, const void* const* b, void
         double res = shifted_solve_impl(ctx, nrhs, bb, xx, tau, tol, info);
         for (int j = 0; j < nrhs; ++j)
             CK(cudaMemcpyAsync(x[j], xx + (size_t)j * n, n * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
-        CK(cudaStreamSynchronize(ctx->st));
+        check_wait_timeouts(ctx);
         if (info) info->seconds = now_s() - t0;
         return res <= tol ? QCD_OK : QCD_ENOCONV;
     });
@@ -1890,11 +1906,21 @@ int qcd_shifted_solve(qcd_ctx* ctx, const void* b, void* x, double tau, double t
     return qcd_shifted_solve_batched(ctx, 1, bs, xs, &tau, tol, info);
 }
 
+int qcd_selftest_wait_limit(qcd_ctx* ctx) {
+    return guarded(ctx, [&]() {
+        wait_probe(ctx->st);
+        check_launch("wait probe");
+        check_wait_timeouts(ctx);
+        return QCD_OK;
+    });
+}
+
 int qcd_eigs(qcd_ctx* ctx, int k, double tol, double* lambda, void* V, qcd_eig_info* info) {
     return guarded(ctx, [&]() {
         if (k < 1 || !lambda || !(tol > 0)) throw QcdError(QCD_EINVAL, "bad arguments");
         double t0 = now_s();
         int rc = eigs_impl(ctx, k, tol, lambda, (double2*)V, info);
+        check_wait_timeouts(ctx);
         if (info) info->seconds = now_s() - t0;
         if (rc == QCD_ENOCONV) ctx->err = "qcd_eigs: outer iteration cap reached";
         return rc;

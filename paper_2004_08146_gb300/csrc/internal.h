@@ -201,6 +201,8 @@ void sap_work_reset();
 void sap_work_read(double out[2]);
 // bounded shared-memory waits that gave up (since the library was loaded)
 unsigned long long wait_timeouts_read();
+// one-warp kernel whose bounded wait on an mbarrier nobody arrives at gives up
+void wait_probe(cudaStream_t st);
 // FP32 / FP64 fused multiply-add throughput of the current device (TFLOP/s)
 double fma_peak_tflops(int prec, cudaStream_t st);
 size_t sap_scratch_bytes(const SapPlan& sp, int prec, int nrhs, int iters);

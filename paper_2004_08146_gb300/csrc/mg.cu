@@ -494,12 +494,13 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// wait for phase `parity` of the barrier, giving up after ~0.5 s of clock
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// wait for phase `parity` of the barrier, giving up after `limit` clocks
+// (default 2^30, ~0.5 s)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = 1ll << 30) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
-        if (clock64() - t0 > (1ll << 30)) {
+        if (clock64() - t0 > limit) {
             atomicAdd(&g_wait_timeouts, 1ull);
             return false;
         }
@@ -507,6 +508,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     return true;
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Self-test of the bounded wait: one warp waits on an mbarrier that nothing
+// arrives at, gives up after `limit` clocks, counts itself and returns.
+__global__ void wait_probe_kernel(long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0, limit);
+}
 
 // FP32 coarse stencil on up to kBulkR right-hand sides per CTA, one coarse
 // site per CTA.  The 9 stencil blocks A_d (nc x nc complex, contiguous) and
@@ -1622,6 +1635,11 @@ void sap_work_reset() {
     static const unsigned long long zero[2][64] = {};
     cudaMemcpyToSymbol(g_sap_work, zero, sizeof(zero));
 }
+void wait_probe(cudaStream_t st) {
+    KTimer kt("wait_probe", 0.0, 0.0, st);
+    wait_probe_kernel<<<1, 32, 0, st>>>(1ll << 21);
+}
+
 unsigned long long wait_timeouts_read() {
     unsigned long long h = 0;
     cudaMemcpyFromSymbol(&h, g_wait_timeouts, sizeof(h));

@@ -124,6 +124,7 @@ _SIGS = {
     "qcd_stats_read": (_I, [ctypes.POINTER(qcd_kernel_stat), _I, _IP]),
     "qcd_stats_sap_work": (_I, [_DP, _DP]),
     "qcd_stats_wait_timeouts": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "qcd_selftest_wait_limit": (_I, [_P]),
     "qcd_fma_peak": (_I, [_I, _DP]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -310,6 +311,10 @@ class Context:
 
     def qcd_mg_prolong(self, prec, nrhs, xc, x):
         return self._check(_lib.qcd_mg_prolong(self.h, prec, nrhs, _ptr(xc), _ptr(x)))
+
+    def qcd_selftest_wait_limit(self):
+        """Raw status of the bounded-wait self-test (QCD_ETIMEOUT expected)."""
+        return _lib.qcd_selftest_wait_limit(self.h)
 
     def qcd_coarse_apply(self, op, prec, nrhs, x, y, tau):
         t, tp = _dbl(tau)

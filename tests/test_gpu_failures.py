@@ -7,7 +7,10 @@ fault is provoked):
   oracle operator);
 * qcd_eigs stopped by its outer-iteration cap returns ENOCONV with the pairs
   it has locked (each within the tolerance, checked with the oracle
-  operator) and NaN for the rest."""
+  operator) and NaN for the rest;
+* a bounded device-side wait that runs out (an mbarrier nothing arrives at,
+  ~1 ms limit) is counted and reported as ETIMEOUT, and the context keeps
+  working."""
 import numpy as np
 import pytest
 
@@ -81,3 +84,25 @@ def test_eigs_enoconv_returns_locked_pairs():
         v = Vh[j].reshape(DIMS + (4, 3))
         assert np.linalg.norm(op.Q(v) - lam[j] * v) <= 1e-8
     ctx.close()
+
+
+def test_bounded_wait_runs_out_and_context_stays_usable():
+    from paper_2004_08146_gb300 import qcd
+    torch = torch_cuda()
+    U = synth.gauge_field(DIMS, 0.3, 93)
+    op = WilsonClover(U, -0.2, 1.0)
+    ctx = make_ctx(U, DIMS, -0.2, 1.0)
+    n0 = qcd.qcd_stats_wait_timeouts()
+    assert ctx.qcd_selftest_wait_limit() == qcd.QCD_ETIMEOUT
+    assert qcd.qcd_stats_wait_timeouts() == n0 + 1
+    # the context still works, and later calls do not report the old timeout
+    psi = synth.spinor(DIMS, 94)
+    x = dev(psi)
+    y = torch.zeros_like(x)
+    ctx.qcd_apply_Q(x, y, 0.1)
+    assert np.linalg.norm(host(y) - op.Q_shift(psi, 0.1)) <= 1e-13 * np.linalg.norm(op.Q_shift(psi, 0.1))
+    ctx.qcd_mg_setup(8, (2, 2, 2, 2))
+    xs = torch.zeros_like(x)
+    rc, info = ctx.qcd_shifted_solve(x, xs, 0.05, 1e-8)
+    assert rc == qcd.QCD_OK
+    assert qcd.qcd_stats_wait_timeouts() == n0 + 1
