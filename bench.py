@@ -57,10 +57,10 @@ def parse():
                     help="lc(v) of all 3072 eigenvectors of the 4^4 Q for the 128 interpolation sets "
                          "of 24 consecutive eigenpairs (block averages), then exit")
     ap.add_argument("--large", action="store_true",
-                    help="study: 100 pairs of the 32x16^3 workload (4^4 aggregates, Nv 20, 8 targets per "
+                    help="study: 100 pairs of the 32x16^3 workload (4^4 aggregates, Nv 20, 16 targets per "
                          "iteration), mixed precision")
     ap.add_argument("--large-blocks", default="",
-                    help="comma-separated targets per outer iteration for --large (default: the workload's 8)")
+                    help="comma-separated targets per outer iteration for --large (default: the workload's 16)")
     ap.add_argument("--gradient", action="store_true",
                     help="eigenvalue derivatives of the 20 smallest |lambda| on a 16^4 field along 16 su(3) "
                          "directions, checked by central differences of Rayleigh quotients; then exit")
@@ -669,13 +669,13 @@ def gradient_study(qcd, synth, torch, devn, stream):
 
 
 def large_study(qcd, synth, torch, devn, stream, block=None):
-    """The 32x16^3 workload (1,572,864 unknowns; eps 0.6, csw 1.7, m0 -0.85 not
-    tuned): 100 eigenpairs to residual 1e-8, mixed precision, two-level MG with
-    4^4 aggregates and Nv = 20, SAP on 2^4 blocks, 8 targets per outer
-    iteration (m_min 30, m_max 48; ``block`` overrides the 8), P rebuilt every
-    20 locks.  Reported: setup
-    and eigensolver times, iteration counts, residuals, and the largest
-    deviation of V^H V from the identity."""
+    """The 32x16^3 workload (1,572,864 unknowns; eps 0.6, csw 1.7, m0 from the
+    dense-proxy tuning): 100 eigenpairs to residual 1e-8, mixed precision,
+    two-level MG with 4^4 aggregates and Nv = 20, SAP on 2^4 blocks with an
+    FP16-stored block basis, 16 targets per outer iteration (m_min 30,
+    m_max 50; ``block`` overrides the 16), P rebuilt every 20 locks.
+    Reported: setup and eigensolver times, iteration counts, residuals, and
+    the largest deviation of V^H V from the identity."""
     from paper_2004_08146_gb300 import workloads
     w = workloads.get("c3_32x16c3")
     dims = tuple(w["dims"])
@@ -683,8 +683,7 @@ def large_study(qcd, synth, torch, devn, stream, block=None):
     n = 12 * int(np.prod(dims))
     k = w["k"]
     block = w["block"] if block is None else block
-    p = qcd.default_params(use_mg=1, sap_block=w["sap"], block=block, m_min=w["m_min"], m_max=w["m_max"],
-                           update_every=w["update_every"], max_outer=4000)
+    p = workload_params(qcd, w, block=block, max_outer=4000)
     ctx = qcd.Context(params=p, stream=stream.cuda_stream)
     ctx.qcd_set_gauge(U, dims, w["m0"], w["csw"])
     V = torch.zeros(k * n, dtype=torch.complex128, device=devn)
@@ -700,7 +699,7 @@ def large_study(qcd, synth, torch, devn, stream, block=None):
     orth = float((Vm.conj() @ Vm.T - torch.eye(k, dtype=V.dtype, device=devn)).abs().max().item())
     ctx.close()
     return {"workload": "c3_32x16c3", "lattice": "32x16^3", "unknowns": n, "k": k, "block": block,
-            "nv": w["nv"], "aggregates": list(w["agg"]), "m0": w["m0"], "m0_tuned": False,
+            "nv": w["nv"], "aggregates": list(w["agg"]), "m0": w["m0"], "sap_half": w.get("sap_half", 0),
             "setup_s": t_setup, "setup_plus_eigs_s": t_eigs, "converged": bool(info.converged),
             "locked": info.locked, "outer": info.outer, "inner": info.inner, "updates": info.updates,
             "coarse_iterations": info.coarse_iterations, "max_residual": info.max_residual,

@@ -1020,6 +1020,33 @@ __host__ __device__ inline SapSmemLayout sap_layout(int BS, int iters, size_t ba
     return L;
 }
 
+// Shared memory of the chirality-split kernel with rw right-hand sides per
+// CTA: the block's links and clover once, then per warp its Krylov basis and
+// GMRES scalars.
+struct ChiLayout {
+    size_t links, clover, shared, basis, H, g, sn, y, cs, flag, perwarp, total;
+};
+template <typename R>
+__host__ __device__ inline ChiLayout chi_layout(int iters, size_t basis_elem, int rw) {
+    auto up = [](size_t v) { return (v + 15) & ~size_t(15); };
+    ChiLayout L;
+    size_t o = 0;
+    L.links = o;  o = up(o + (size_t)16 * 36 * sizeof(cplx<R>));
+    L.clover = o; o = up(o + (size_t)16 * 72 * sizeof(R));
+    L.shared = o;
+    size_t w = 0;
+    L.basis = w;  w = up(w + (size_t)(iters + 1) * 16 * 12 * basis_elem);
+    L.H = w;      w = up(w + (size_t)(iters + 1) * iters * sizeof(cplx<R>));
+    L.g = w;      w = up(w + (size_t)(iters + 1) * sizeof(cplx<R>));
+    L.sn = w;     w = up(w + (size_t)iters * sizeof(cplx<R>));
+    L.y = w;      w = up(w + (size_t)iters * sizeof(cplx<R>));
+    L.cs = w;     w = up(w + (size_t)iters * sizeof(R));
+    L.flag = w;   w = up(w + 4 * sizeof(int));
+    L.perwarp = w;
+    L.total = L.shared + (size_t)rw * w;
+    return L;
+}
+
 template <int BS, typename T>
 __device__ __forceinline__ T seg_sum(T v) {
 #pragma unroll
@@ -1260,34 +1287,31 @@ __device__ __forceinline__ void stage16(void* __restrict__ dst, const void* __re
 // the partner lane (lane ^ 16) before it reconstructs its own half.  Same
 // GMRES as sap_warp_kernel (modified Gram-Schmidt, Givens by lane 0).
 template <typename R, typename BT>
-__global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const cplx<R>* __restrict__ U,
-                                                     const R* __restrict__ A, const int* __restrict__ blocks, int ncol,
-                                                     int op, Shifts tau, const cplx<R>* __restrict__ r,
-                                                     cplx<R>* __restrict__ x, int iters, double tol,
-                                                     const int* __restrict__ act) {
+__global__ void __launch_bounds__(128) sap_chi_kernel(Geom g, Blocking B, const cplx<R>* __restrict__ U,
+                                                      const R* __restrict__ A, const int* __restrict__ blocks,
+                                                      int ncol, int op, Shifts tau, const cplx<R>* __restrict__ r,
+                                                      cplx<R>* __restrict__ x, int iters, double tol,
+                                                      const int* __restrict__ act, int nrhs) {
     constexpr int BS = 16;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, rw = blockDim.x >> 5;
     const int chi = lane >> 4, l = lane & 15;
-    const SapSmemLayout LY = sap_layout<R>(BS, iters, sizeof(BT));
-    unsigned char* base = smraw;
-    BT* basis = reinterpret_cast<BT*>(base + LY.basis);
-    cplx<R>* slink = reinterpret_cast<cplx<R>*>(base + LY.links);
-    R* sclov = reinterpret_cast<R*>(base + LY.clover);
-    cplx<R>* H = reinterpret_cast<cplx<R>*>(base + LY.H);
-    cplx<R>* gv = reinterpret_cast<cplx<R>*>(base + LY.g);
-    cplx<R>* sn = reinterpret_cast<cplx<R>*>(base + LY.sn);
-    cplx<R>* yv = reinterpret_cast<cplx<R>*>(base + LY.y);
-    R* cs = reinterpret_cast<R*>(base + LY.cs);
-    int* flag = reinterpret_cast<int*>(base + LY.flag);
+    const ChiLayout LY = chi_layout<R>(iters, sizeof(BT), rw);
+    unsigned char* wbase = smraw + LY.shared + (size_t)wid * LY.perwarp;
+    BT* basis = reinterpret_cast<BT*>(wbase + LY.basis);
+    cplx<R>* slink = reinterpret_cast<cplx<R>*>(smraw + LY.links);
+    R* sclov = reinterpret_cast<R*>(smraw + LY.clover);
+    cplx<R>* H = reinterpret_cast<cplx<R>*>(wbase + LY.H);
+    cplx<R>* gv = reinterpret_cast<cplx<R>*>(wbase + LY.g);
+    cplx<R>* sn = reinterpret_cast<cplx<R>*>(wbase + LY.sn);
+    cplx<R>* yv = reinterpret_cast<cplx<R>*>(wbase + LY.y);
+    R* cs = reinterpret_cast<R*>(wbase + LY.cs);
+    int* flag = reinterpret_cast<int*>(wbase + LY.flag);
 
-    const int j = blockIdx.y;
-    if (act != nullptr && !act[j]) return;
+    // warp w of the CTA solves the block for right-hand side blockIdx.y * rw + w;
+    // the block's links and clover are staged once for all of them
+    const int j = blockIdx.y * rw + wid;
     const int blk = blocks[blockIdx.x];
-    const size_t fstride = (size_t)g.V * 12;
-    r += j * fstride;
-    x += j * fstride;
-    const R t = (R)tau.t[j];
     int o[4];
     {
         int tt = l;
@@ -1296,15 +1320,26 @@ __global__ void __launch_bounds__(32) sap_chi_kernel(Geom g, Blocking B, const c
         o[1] = tt % B.b[1]; o[0] = tt / B.b[1];
     }
     const int y = block_fine_site(g, B, blk, l);
-    // stage links and clover of the 16 sites: lane chi copies half of its
-    // site's links and its own chirality block of the clover term (16-byte
-    // words, every load in flight at once)
+    // stage links and clover of the 16 sites (warp 0): lane chi copies half
+    // of its site's links and its own chirality block of the clover term
+    // (16-byte words, every load in flight at once)
     constexpr int kHalf = 18 * (int)sizeof(cplx<R>) / 16;   // 16-byte words in 18 complex / 36 reals
-    stage16<kHalf>(slink + l * 36 + 18 * chi, U + (size_t)y * 36 + 18 * chi);
-    stage16<kHalf>(sclov + l * 72 + 36 * chi, A + (size_t)y * 72 + 36 * chi);
+    if (wid == 0) {
+        stage16<kHalf>(slink + l * 36 + 18 * chi, U + (size_t)y * 36 + 18 * chi);
+        stage16<kHalf>(sclov + l * 72 + 36 * chi, A + (size_t)y * 72 + 36 * chi);
+    }
+    const bool mine = j < nrhs && (act == nullptr || act[j]);
+    const size_t fstride = (size_t)g.V * 12;
     cplx<R> w[6];
+    if (mine) {
+        r += j * fstride;
+        x += j * fstride;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) w[k] = __ldg(r + (size_t)y * 12 + 6 * chi + k);
+        for (int k = 0; k < 6; ++k) w[k] = __ldg(r + (size_t)y * 12 + 6 * chi + k);
+    }
+    __syncthreads();
+    if (!mine) return;
+    const R t = (R)tau.t[j];
     R nn = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) nn += w[k].x * w[k].x + w[k].y * w[k].y;
@@ -1674,22 +1709,35 @@ void sap_blocks(const FineOp& f, const SapPlan& sp, int colour, int prec, int op
               rs * sites * (nrhs * 72.0 + 144.0),
               1824.0 * sites * nrhs * iters, st);
     if (bs == 16) {
-        dim3 grid(sp.ncol[colour], nrhs);
+        // one warp per block solve; with four or more right-hand sides four
+        // of them share a CTA (and one staged copy of the block's links and
+        // clover), so more block solves fit in shared memory per SM
+        const int rw = nrhs >= 4 ? 4 : 1;
+        dim3 grid(sp.ncol[colour], (nrhs + rw - 1) / rw);
         if (prec == QCD_FP64) {
-            const size_t sm = sap_layout<double>(16, iters).total;
-            if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            sap_chi_kernel<double, double2><<<grid, 32, sm, st>>>(f.g, sp.B, f.U64, f.A64, sp.blocks_of_colour[colour],
-                sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol, act);
+            const size_t sm = chi_layout<double>(iters, sizeof(double2), rw).total;
+            if (sm + 1024 > 48 * 1024)
+                cudaFuncSetAttribute(sap_chi_kernel<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm);
+            sap_chi_kernel<double, double2><<<grid, 32 * rw, sm, st>>>(f.g, sp.B, f.U64, f.A64,
+                sp.blocks_of_colour[colour], sp.ncol[colour], op, sh, (const double2*)r, (double2*)x, iters, tol,
+                act, nrhs);
         } else if (half) {
-            const size_t sm = sap_layout<float>(16, iters, sizeof(__half2)).total;
-            if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            sap_chi_kernel<float, __half2><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
-                sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
+            const size_t sm = chi_layout<float>(iters, sizeof(__half2), rw).total;
+            if (sm + 1024 > 48 * 1024)
+                cudaFuncSetAttribute(sap_chi_kernel<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm);
+            sap_chi_kernel<float, __half2><<<grid, 32 * rw, sm, st>>>(f.g, sp.B, f.U32, f.A32,
+                sp.blocks_of_colour[colour], sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol,
+                act, nrhs);
         } else {
-            const size_t sm = sap_layout<float>(16, iters).total;
-            if (sm + 1024 > 48 * 1024) cudaFuncSetAttribute(sap_chi_kernel<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            sap_chi_kernel<float, float2><<<grid, 32, sm, st>>>(f.g, sp.B, f.U32, f.A32, sp.blocks_of_colour[colour],
-                sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol, act);
+            const size_t sm = chi_layout<float>(iters, sizeof(float2), rw).total;
+            if (sm + 1024 > 48 * 1024)
+                cudaFuncSetAttribute(sap_chi_kernel<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm);
+            sap_chi_kernel<float, float2><<<grid, 32 * rw, sm, st>>>(f.g, sp.B, f.U32, f.A32,
+                sp.blocks_of_colour[colour], sp.ncol[colour], op, sh, (const float2*)r, (float2*)x, iters, tol,
+                act, nrhs);
         }
         return;
     }

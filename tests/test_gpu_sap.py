@@ -76,3 +76,32 @@ def test_sap_fp16_basis_matches_oracle():
     names = {r["name"]: r["launches"] for r in qcd.qcd_stats_read()}
     assert names.get("sap_block_f32h", 0) == 8 and "sap_block_f32" not in names
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,half,tol", [(0, 0, 1e-10), (1, 0, 1e-4), (1, 1, 5e-3)])
+def test_sap_16site_blocks_many_rhs(prec, half, tol):
+    """Six right-hand sides on 16-site blocks: four block solves share a CTA
+    (one staged copy of the block's links and clover) and the last CTA holds
+    two; every right-hand side follows the oracle's sweeps at fixed
+    block-GMRES steps, both forms."""
+    from paper_2004_08146_gb300 import qcd
+    torch_cuda()
+    dims, block, nrhs = (8, 4, 4, 4), (2, 2, 2, 2), 6
+    U = synth.gauge_field(dims, 0.5, 75)
+    m0, csw = -0.3, 1.3
+    op = WilsonClover(U, m0, csw)
+    ctx = make_ctx(U, dims, m0, csw, sap_block=block, sap_block_iters=ITERS, sap_half=half)
+    dt = np.complex128 if prec == 0 else np.complex64
+    b = synth.spinor(dims, 76, nvec=nrhs)
+    x0 = synth.spinor(dims, 77, nvec=nrhs)
+    taus = [0.05 * j - 0.12 for j in range(nrhs)]
+    sap = mg.SAP(dims, block, block_iters=ITERS, block_tol=0.0)
+    for opc, form in ((qcd.QCD_OP_D, 'g5'), (qcd.QCD_OP_Q, 'Q')):
+        xd = dev(x0, dt)
+        ctx.qcd_sap(opc, prec, nrhs, dev(b, dt), xd, taus, 2, -1.0)
+        got = host(xd).reshape((nrhs,) + dims + (4, 3))
+        for j in range(nrhs):
+            A = lambda v, t=taus[j]: mg.fine_apply(op, v, t, form)
+            ref = sap.smooth(A, b[j], x0[j], 2)
+            assert relerr(got[j], ref) < tol, (form, j)
+    ctx.close()
