@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--coarse-stencil", action="store_true",
                     help="run and print only the coarse-stencil comparison (tensor cores vs FMA units)")
     ap.add_argument("--no-coarse-stencil", action="store_true")
+    ap.add_argument("--sap-bench", action="store_true",
+                    help="run and print only the SAP block-solve measurement (32x16^3, 2 and 16 right-hand "
+                         "sides, FP32 and FP16 block basis)")
     ap.add_argument("--no-large-workload", action="store_true",
                     help="skip the 64 x 32^3 three-level measurement")
     ap.add_argument("--large-workload", default="c4_64x32c3")
@@ -340,6 +343,9 @@ def main():
         return
     if args.coarse_stencil:
         print(json.dumps({"coarse_stencil": coarse_stencil_bench(qcd, synth, torch, devn, stream)}), flush=True)
+        return
+    if args.sap_bench:
+        print(json.dumps({"sap": sap_bench(qcd, synth, torch, devn, stream)}), flush=True)
         return
     if args.only_large:
         print(json.dumps({"large_workload": large_workload(qcd, synth, torch, devn, stream, workloads,
@@ -857,6 +863,48 @@ def coarse_stencil_bench(qcd, synth, torch, devn, stream, reps=20):
         out["tensor" if tensor else "fma"] = {"us_per_apply": t * 1e6, "tflops": flops / t / 1e12,
                                                "gbs": nbytes / t / 1e9}
         ctx.close()
+    return out
+
+
+def sap_bench(qcd, synth, torch, devn, stream, reps=5):
+    """SAP smoothing (Eq. 2.10, 2^4 blocks, block GMRES to 1e-1 or 10 steps,
+    D - tau Gamma5 form) on the 32 x 16^3 field (eps 0.6, c_sw 1.7, m0 -1.1;
+    inputs larger than L2) with 2 and 16 right-hand sides, FP32 with the
+    block basis in FP32 and in FP16: per launch of the block-solve kernel
+    (one colour) its CUDA-event time, the block solves and GMRES steps it ran,
+    and the counted block-solve arithmetic against the measured FP32 FMA
+    peak."""
+    dims = (32, 16, 16, 16)
+    U = synth.gauge_field(dims, 0.6, 1003)
+    V = int(np.prod(dims))
+    peak = qcd.qcd_fma_peak(qcd.QCD_FP32)
+    out = {"lattice": "32x16^3", "block": [2, 2, 2, 2], "fp32_fma_peak_tflops": peak}
+    for nrhs in (2, 16):
+        b = torch.randn(nrhs * V * 12, dtype=torch.complex64, device=devn)
+        taus = [0.01 * j for j in range(nrhs)]
+        for half in (0, 1):
+            ctx = qcd.Context(params=qcd.default_params(sap_half=half), stream=stream.cuda_stream)
+            ctx.qcd_set_gauge(U, dims, -1.1, 1.7)
+            x = torch.zeros_like(b)
+            ctx.qcd_sap(qcd.QCD_OP_D, qcd.QCD_FP32, nrhs, b, x, taus, 1, 0.1)     # warm-up
+            torch.cuda.synchronize()
+            qcd.qcd_stats_reset(1)
+            for _ in range(reps):
+                x.zero_()
+                ctx.qcd_sap(qcd.QCD_OP_D, qcd.QCD_FP32, nrhs, b, x, taus, 1, 0.1)
+            torch.cuda.synchronize()
+            st = {r["name"]: r for r in qcd.qcd_stats_read()}
+            work = qcd.qcd_stats_sap_work()
+            name = "sap_block_f32h" if half else "sap_block_f32"
+            r = st[name]
+            fl = sap_flops(*work)
+            out[f"nrhs{nrhs}_{'fp16' if half else 'fp32'}_basis"] = {
+                "us_per_launch": r["total_ms"] * 1e3 / max(1, r["launches"]), "launches": r["launches"],
+                "block_solves_per_launch": V // 16 // 2 * nrhs,
+                "gmres_steps_per_solve": work[0] / (r["launches"] * (V // 2) * nrhs),
+                "tflops": fl / (r["total_ms"] * 1e-3) / 1e12, "frac_fp32_fma": fl / (r["total_ms"] * 1e-3) / 1e12 / peak}
+            ctx.close()
+    qcd.qcd_stats_reset(0)
     return out
 
 
