@@ -4,7 +4,8 @@
 Metric: seconds to the k smallest-|lambda| eigenpairs of Q = Gamma5 D at
 eigen-residual 1e-8 (mixed precision: FP32 inner solves, FP64 outer).  The
 timed step is the 16 x 8^3 workload (k = 50, two-level MG, 2^4 aggregates,
-Nv = 8, SAP 2^4): multigrid setup + eigensolve from the resident gauge field.
+Nv = 8, SAP 2^4, 4 targets per outer iteration): multigrid setup +
+eigensolve from the resident gauge field.
 Also reported: the same step in plain FP64; the end-to-end time through the
 C ABI from host buffers; the fine-stencil bandwidth on a 64 x 32^3 lattice;
 the live roofline of the dominant kernel (HBM and, for the SAP block solves,
@@ -109,10 +110,8 @@ def max_over_ranks(value, device=None):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of each kernel as it stands now, for the roofline's
 # "traffic"; a kernel that changes is taken out of this table until it is
-# captured again (the field is then null).  sap_block_f32: two launches of
-# sap_chi_kernel<float, float2> in the 16 x 8^3 step (k = 4), 4.7834 and
-# 4.7839 MB read, 0 written (profiles/sap_chi_f32_c2_16x8c3.md).
-NCU_TRAFFIC = {"sap_block_f32": 4.7836e6}
+# captured again (the field is then null).
+NCU_TRAFFIC = {}
 
 # Work model of the SAP block solves for the FP32-ALU roofline, per block
 # site and GMRES step j (0-based) of a block solve of k steps: the Dirichlet
@@ -191,7 +190,7 @@ class ClockSampler:
 # summed over targets, outer iterations; from the GPU bench line), used to
 # scale the oracle's per-operation times to one eigensolve when no GPU run
 # of the same process provides them (the reference arm).
-REF_COUNTS = {"c2_16x8c3": dict(inner=3129, outer=316, block=2)}
+REF_COUNTS = {"c2_16x8c3": dict(inner=3267, outer=166, block=4)}
 
 
 def oracle_ops(w):
@@ -486,7 +485,7 @@ def main():
         w["name"] = args.workload
         ops = oracle_sample_subprocess(args.workload)
         cpu = cpu_baseline_line(w, ops, int(np.mean([i.inner for i in infos])), int(np.mean([i.outer for i in infos])),
-                                qcd.default_params().block, "this run's GPU steps")
+                                w.get("block", qcd.default_params().block), "this run's GPU steps")
 
     if rank == 0:
         info = infos[-1]
@@ -496,6 +495,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": args.workload, "lattice": "x".join(map(str, dims)), "k": w["k"],
                        "mg": f"2-level, {w['agg']} aggregates, Nv={w['nv']}, SAP {w['sap']}",
+                       "targets_per_iteration": w.get("block", 2),
                        "precision": "FP32 inner / FP64 outer", "tol": 1e-8, "m0": w["m0"], "csw": w["csw"],
                        "eps": w["eps"], "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{ws}"},
