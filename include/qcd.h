@@ -125,6 +125,9 @@ typedef struct qcd_params {
                                 that bound) must leave none below it before the call
                                 returns; a value below it resets the count.  0 returns
                                 at the first such check (default 2, <= 64) */
+    int    coarse_ctas;      /* CTAs of the one-launch coarse GMRES: 0 (default) one per
+                                SM; n > 0 at most n (fewer CTAs make its grid-wide
+                                barriers cheaper on small coarse lattices) */
 } qcd_params;
 
 typedef struct qcd_solve_info {

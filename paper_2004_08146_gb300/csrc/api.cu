@@ -196,6 +196,7 @@ void validate_params(const qcd_params& p) {
     if (p.coarse_tensor != 0 && p.coarse_tensor != 1) throw QcdError(QCD_EINVAL, "coarse_tensor must be 0 or 1");
     if (p.sap_half != 0 && p.sap_half != 1) throw QcdError(QCD_EINVAL, "sap_half must be 0 or 1");
     if (p.confirm < 0 || p.confirm > 64) throw QcdError(QCD_EINVAL, "confirm must be in [0, 64]");
+    if (p.coarse_ctas < 0) throw QcdError(QCD_EINVAL, "coarse_ctas must be >= 0");
 }
 
 // ------------------------------------------------------------------ linear operators
@@ -681,6 +682,7 @@ void build_level2(qcd_ctx* ctx, const double2* V, int nvec) {
         c2.B = B2;
         c2.nv = nv2;
         c2.nc = 2 * nv2;
+        c2.ctas = ctx->p.coarse_ctas;
         for (int mu = 0; mu < 4; ++mu) c2.gc.L[mu] = B2.cd[mu];
         c2.gc.V = B2.nb;
         c2.gc.antiperiodic = 0;
@@ -718,6 +720,7 @@ void build_from_vectors(qcd_ctx* ctx, const double2* V, int nvec, const int bloc
         c.B = B;
         c.nv = nvec;
         c.nc = 2 * nvec;
+        c.ctas = ctx->p.coarse_ctas;
         for (int mu = 0; mu < 4; ++mu) c.gc.L[mu] = B.cd[mu];
         c.gc.V = B.nb;
         c.gc.antiperiodic = 0;
@@ -1431,6 +1434,7 @@ void qcd_default_params(qcd_params* p) {
     p->coarse_tensor = 0;
     p->sap_half = 0;
     p->confirm = 2;
+    p->coarse_ctas = 0;
 }
 
 int qcd_create(qcd_ctx** out, const qcd_params* p, void* stream) {
@@ -1445,6 +1449,7 @@ int qcd_create(qcd_ctx** out, const qcd_params* p, void* stream) {
         return e.code;
     }
     ctx->p = *p;
+    ctx->c.ctas = ctx->c2.ctas = p->coarse_ctas;
     ctx->st = (cudaStream_t)stream;
     *out = ctx;
     return QCD_OK;
@@ -1468,6 +1473,7 @@ int qcd_set_params(qcd_ctx* ctx, const qcd_params* p) {
         const bool l2_changed = p->levels != ctx->p.levels || p->nv2 != ctx->p.nv2 ||
                                 memcmp(p->agg2, ctx->p.agg2, sizeof(p->agg2)) != 0;
         ctx->p = *p;
+        ctx->c.ctas = ctx->c2.ctas = p->coarse_ctas;
         if (l2_changed) {
             ctx->c2.ready = false;
             if (p->levels == 3 && ctx->c.ready && ctx->test_vectors) build_level2(ctx, ctx->test_vectors, ctx->n_test);

@@ -86,6 +86,7 @@ struct Coarse {
     float2* A32 = nullptr;
     bool a64_stale = false;   // A32 was built in FP32 and A64 is out of date
     bool ready = false;
+    int ctas = 0;             // CTAs of the one-launch coarse GMRES (0: one per SM)
 };
 
 // ------------------------------------------------------------------ kernels (dirac.cu)

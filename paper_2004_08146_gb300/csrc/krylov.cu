@@ -12,6 +12,7 @@
 //     grid-wide barriers of the cooperative launch.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include "internal.h"
 
 namespace cg = cooperative_groups;
@@ -577,7 +578,7 @@ int coarse_gmres_grid() {
 
 // Site-based partition: each CTA owns `sps` consecutive coarse sites.
 static void coarse_partition(const Coarse& c, int& sps, int& nblk) {
-    const int nct = coarse_gmres_grid();
+    const int nct = c.ctas > 0 ? std::min(c.ctas, coarse_gmres_grid()) : coarse_gmres_grid();
     sps = (c.gc.V + nct - 1) / nct;
     nblk = (c.gc.V + sps - 1) / sps;
 }

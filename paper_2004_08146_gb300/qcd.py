@@ -61,6 +61,7 @@ class qcd_params(ctypes.Structure):
         ("coarse_tensor", ctypes.c_int),
         ("sap_half", ctypes.c_int),
         ("confirm", ctypes.c_int),
+        ("coarse_ctas", ctypes.c_int),
     ]
 
 
