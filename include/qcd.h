@@ -120,11 +120,12 @@ typedef struct qcd_params {
                                 solves resident; default 0) */
     int    confirm;          /* completion check of qcd_eigs: once k pairs are locked
                                 and no harmonic Ritz value lies below the k-th
-                                smallest locked |lambda|, this many further outer
-                                iterations (corrections for the smallest values above
-                                that bound) must leave none below it before the call
-                                returns; a value below it resets the count.  0 returns
-                                at the first such check (default 2, <= 64) */
+                                smallest locked |lambda|, the search continues until
+                                this many correction equations (for the smallest values
+                                above that bound) have left none below it; a value
+                                below it resets the count.  0 returns at the first such
+                                check (default 32: two outer iterations at 16 targets,
+                                eight at 4; <= 1024) */
     int    coarse_ctas;      /* CTAs of the one-launch coarse GMRES: 0 (default) one per
                                 SM; n > 0 at most n (fewer CTAs make its grid-wide
                                 barriers cheaper on small coarse lattices) */

@@ -151,9 +151,9 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
     confirm      : completion check (the paper states no stopping rule beyond
                    the number of pairs): once n pairs are locked and no
                    harmonic Ritz value lies below the n-th smallest locked
-                   |lambda|, this many further outer iterations correct the
-                   smallest values above that bound; a value below it resets
-                   the count, and the run ends when the count is reached
+                   |lambda|, the run continues until this many correction
+                   equations (for the smallest values above that bound) have
+                   left none below it; a value below it resets the count
     """
     extract = harmonic_ritz if extraction == 'harmonic' else rayleigh_ritz
     n_want = n
@@ -252,7 +252,7 @@ def gd_lambda_amg(Q, n, V0, t0, correction, m_min=30, m_max=50, eps=1e-8,
             T[:, j] = t
             inner += int(it)
         if confirming:
-            confirm_done += 1
+            confirm_done += len(pairs)
         if V.shape[1] + T.shape[1] > m_max:
             theta, S = extract(V, W)
             Qs, _ = np.linalg.qr(S[:, :m_min])

@@ -195,7 +195,7 @@ void validate_params(const qcd_params& p) {
     if (p.coarse_layout < 0 || p.coarse_layout > 3) throw QcdError(QCD_EINVAL, "coarse_layout must be in [0, 3]");
     if (p.coarse_tensor != 0 && p.coarse_tensor != 1) throw QcdError(QCD_EINVAL, "coarse_tensor must be 0 or 1");
     if (p.sap_half != 0 && p.sap_half != 1) throw QcdError(QCD_EINVAL, "sap_half must be 0 or 1");
-    if (p.confirm < 0 || p.confirm > 64) throw QcdError(QCD_EINVAL, "confirm must be in [0, 64]");
+    if (p.confirm < 0 || p.confirm > 1024) throw QcdError(QCD_EINVAL, "confirm must be in [0, 1024]");
     if (p.coarse_ctas < 0) throw QcdError(QCD_EINVAL, "coarse_ctas must be >= 0");
 }
 
@@ -1163,9 +1163,10 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
     int outer = 0, inner = 0, updates = 0, locks_since_update = 0;
     bool finished = false;
     // completion: once k pairs are locked and no harmonic Ritz value lies
-    // below the k-th smallest locked |lambda|, P.confirm further outer
-    // iterations expand the space towards the smallest values above that
-    // bound; a value that falls below it restarts the count
+    // below the k-th smallest locked |lambda|, the search goes on until
+    // P.confirm correction equations (aimed at the smallest values above that
+    // bound) have expanded the space; a value that falls below it restarts
+    // the count
     int confirm_done = 0;
     bool confirming = false;
     // interpolation updates stage their vectors in the test-vector buffer
@@ -1308,7 +1309,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
         for (int v : g.iters) inner += v;
         blas_convert(prec, tl, QCD_FP64, gd.T, (size_t)nb * n, st);
         nT = nb;
-        if (confirming) ++confirm_done;
+        if (confirming) confirm_done += nb;
         // thick restart
         if (gd.m + nT > P.m_max) {
             std::vector<double> th;
@@ -1433,7 +1434,7 @@ void qcd_default_params(qcd_params* p) {
     p->coarse_layout = 0;
     p->coarse_tensor = 0;
     p->sap_half = 0;
-    p->confirm = 2;
+    p->confirm = 32;
     p->coarse_ctas = 0;
 }
 

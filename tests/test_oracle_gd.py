@@ -128,10 +128,10 @@ def test_gd_three_level_corrections_c1():
 def test_completion_confirm_passes():
     """The completion check: with confirm = 0 the run ends at the first check
     that finds no harmonic Ritz value below the k-th locked |lambda|; with
-    confirm = 2 the same (deterministic) run reaches that check at the same
-    outer iteration and then takes at least two more.  Both return the k
-    smallest |lambda| of a dense Hermitian indefinite matrix with a cluster at
-    the k-th value."""
+    confirm = 8 corrections (two outer iterations of 4 targets) the same
+    (deterministic) run reaches that check at the same outer iteration and
+    then takes at least two more.  Both return the k smallest |lambda| of a
+    dense Hermitian indefinite matrix with a cluster at the k-th value."""
     n, k = 120, 10
     w = np.concatenate([np.linspace(0.05, 1.0, n // 2), -np.linspace(0.06, 1.1, n // 2)])
     w[:6] = 0.2 + 1e-3 * np.arange(6)          # a cluster around the boundary
@@ -144,10 +144,10 @@ def test_completion_confirm_passes():
         x, it = mg.gmres(lambda v: (A @ v[0] - theta * v[0])[None], r[None], 1e-1, 8)
         return x[0], it[0]
     out = {}
-    for c in (0, 2):
+    for c in (0, 8):
         out[c] = gd.gd_lambda_amg(lambda v: A @ v, k, synth.complex_gaussian((n, 6), 7),
                                   synth.complex_gaussian((n, 4), 8), corr, m_min=16, m_max=32,
                                   eps=1e-9, block=4, confirm=c)
         assert out[c].converged
         assert np.max(np.abs(out[c].lam - ev[:k]) / np.abs(ev[:k])) < 1e-10
-    assert out[2].outer >= out[0].outer + 2
+    assert out[8].outer >= out[0].outer + 2
