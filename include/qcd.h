@@ -129,6 +129,10 @@ typedef struct qcd_params {
     int    coarse_ctas;      /* CTAs of the one-launch coarse GMRES: 0 (default) one per
                                 SM; n > 0 at most n (fewer CTAs make its grid-wide
                                 barriers cheaper on small coarse lattices) */
+    int    guard;            /* qcd_eigs locks k + guard pairs before its completion check
+                                and returns the k smallest |lambda| (an interior eigensolver
+                                can skip an eigenvalue near the end of its run; the extra
+                                pairs keep the search there longer).  Default 0, <= 256 */
 } qcd_params;
 
 typedef struct qcd_solve_info {

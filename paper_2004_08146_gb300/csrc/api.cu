@@ -197,6 +197,7 @@ void validate_params(const qcd_params& p) {
     if (p.sap_half != 0 && p.sap_half != 1) throw QcdError(QCD_EINVAL, "sap_half must be 0 or 1");
     if (p.confirm < 0 || p.confirm > 1024) throw QcdError(QCD_EINVAL, "confirm must be in [0, 1024]");
     if (p.coarse_ctas < 0) throw QcdError(QCD_EINVAL, "coarse_ctas must be >= 0");
+    if (p.guard < 0 || p.guard > 256) throw QcdError(QCD_EINVAL, "guard must be in [0, 256]");
 }
 
 // ------------------------------------------------------------------ linear operators
@@ -1149,7 +1150,7 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
     // locked-pair slots: k plus room for the pairs locked while the last
     // targets finish; when they are full, a new lock replaces the locked
     // pair of largest |lambda| (or is dropped if it is larger still)
-    gd.alloc(P.m_max + block, k + 2 * block + 8, block);
+    gd.alloc(P.m_max + block, k + P.guard + 2 * block + 8, block);
     CK(cudaMemsetAsync(ctx->counters(), 0, 2 * sizeof(unsigned long long), st));
     double2* t0 = gd.tmp;
     // start basis: setup test vectors (or random vectors without MG)
@@ -1189,11 +1190,13 @@ int eigs_impl(qcd_ctx* ctx, int k, double tol, double* lambda, double2* Vout, qc
         while (true) {
             gd.harmonic(theta, col);
             std::vector<char> allowed(theta.size(), 1);
-            if (gd.nlock >= k) {
+            // the completion check runs on k + guard pairs (the k smallest are returned)
+            const int kk = k + P.guard;
+            if (gd.nlock >= kk) {
                 std::vector<double> al(gd.lam.size());
                 for (size_t i = 0; i < al.size(); ++i) al[i] = std::fabs(gd.lam[i]);
-                std::nth_element(al.begin(), al.begin() + (k - 1), al.end());
-                double lim = al[k - 1];
+                std::nth_element(al.begin(), al.begin() + (kk - 1), al.end());
+                double lim = al[kk - 1];
                 int cnt = 0;
                 for (size_t i = 0; i < theta.size(); ++i) { allowed[i] = std::fabs(theta[i]) < lim; cnt += allowed[i]; }
                 confirming = cnt == 0;
@@ -1436,6 +1439,7 @@ void qcd_default_params(qcd_params* p) {
     p->sap_half = 0;
     p->confirm = 32;
     p->coarse_ctas = 0;
+    p->guard = 0;
 }
 
 int qcd_create(qcd_ctx** out, const qcd_params* p, void* stream) {

@@ -62,6 +62,7 @@ class qcd_params(ctypes.Structure):
         ("sap_half", ctypes.c_int),
         ("confirm", ctypes.c_int),
         ("coarse_ctas", ctypes.c_int),
+        ("guard", ctypes.c_int),
     ]
 
 

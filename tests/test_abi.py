@@ -82,7 +82,7 @@ def test_calls_without_gauge_fail_cleanly():
                                  dict(levels=4), dict(levels=1), dict(nv2=0), dict(nv2=33),
                                  dict(agg2=(2, 0, 2, 2)), dict(nu2=-1), dict(coarse_layout=4),
                                  dict(coarse_layout=-1), dict(coarse_tensor=2), dict(sap_half=-1),
-                                 dict(confirm=-1), dict(confirm=1025), dict(coarse_ctas=-1)])
+                                 dict(confirm=-1), dict(confirm=1025), dict(coarse_ctas=-1), dict(guard=-1)])
 def test_create_rejects_each_bad_field(bad):
     """Parameter validation happens in qcd_create, on the host, before any GPU work."""
     from paper_2004_08146_gb300 import qcd
