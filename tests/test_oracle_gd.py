@@ -151,3 +151,29 @@ def test_completion_confirm_passes():
         assert out[c].converged
         assert np.max(np.abs(out[c].lam - ev[:k]) / np.abs(ev[:k])) < 1e-10
     assert out[8].outer >= out[0].outer + 2
+
+
+def test_guard_pairs_return_the_k_smallest():
+    """Guard pairs: the completion check runs on k + g locked pairs and the k
+    smallest |lambda| are returned -- still exactly the k smallest of a dense
+    Hermitian indefinite matrix, after at least as many outer iterations as
+    without guard pairs (the same deterministic run up to the first check)."""
+    n, k = 120, 10
+    w = np.concatenate([np.linspace(0.05, 1.0, n // 2), -np.linspace(0.06, 1.1, n // 2)])
+    w[:6] = 0.2 + 1e-3 * np.arange(6)
+    Y, _ = np.linalg.qr(synth.complex_gaussian((n, n), 6))
+    A = (Y * w) @ Y.conj().T
+    A = 0.5 * (A + A.conj().T)
+    ev = w[np.lexsort((w, np.abs(w)))]
+
+    def corr(theta, r):
+        x, it = mg.gmres(lambda v: (A @ v[0] - theta * v[0])[None], r[None], 1e-1, 8)
+        return x[0], it[0]
+    out = {}
+    for g in (0, 4):
+        out[g] = gd.gd_lambda_amg(lambda v: A @ v, k, synth.complex_gaussian((n, 6), 7),
+                                  synth.complex_gaussian((n, 4), 8), corr, m_min=16, m_max=32,
+                                  eps=1e-9, block=4, n_guard=g)
+        assert out[g].converged and out[g].lam.size == k
+        assert np.max(np.abs(out[g].lam - ev[:k]) / np.abs(ev[:k])) < 1e-10
+    assert out[4].outer >= out[0].outer
