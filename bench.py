@@ -110,8 +110,11 @@ def max_over_ranks(value, device=None):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of each kernel as it stands now, for the roofline's
 # "traffic"; a kernel that changes is taken out of this table until it is
-# captured again (the field is then null).
-NCU_TRAFFIC = {}
+# captured again (the field is then null).  coarse_gmres_f32: two launches of
+# coarse_gmres_kernel<float2, float> in the 16 x 8^3 step (k = 4, 4 targets),
+# dram__bytes.sum.per_second x gpu__time_duration.sum = 9.808 and 9.820 MB
+# (profiles/coarse_gmres_f32_c2_16x8c3.md).
+NCU_TRAFFIC = {"coarse_gmres_f32": 9.814e6}
 
 # Work model of the SAP block solves for the FP32-ALU roofline, per block
 # site and GMRES step j (0-based) of a block solve of k steps: the Dirichlet
