@@ -605,25 +605,27 @@ def large_workload(qcd, synth, torch, devn, stream, workloads, name, k):
 
 
 def gradient_study(qcd, synth, torch, devn, stream):
-    """Differentiation workload: 16^4 field (eps 0.5, csw 1.5; m0 = -0.85 as in
-    the 16x8^3 workload, not retuned), the 20 smallest-|lambda| eigenpairs from
-    the GPU eigensolver (two-level MG, 4^4 aggregates, Nv = 8), then d lambda_k / d eps along 16 random su(3)
+    """Differentiation workload: 16^4 field (eps 0.5, csw 1.5, m0 of the
+    workload table), the 20 smallest-|lambda| eigenpairs from the GPU
+    eigensolver (two-level MG, 4^4 aggregates, Nv = 8), then d lambda_k / d eps along 16 random su(3)
     directions X (U -> exp(i eps X) U).  Each derivative is checked against
     the central difference (h = 1e-6) of the Rayleigh quotient v_k^H Q(U(+-h)) v_k,
     whose derivative at eps = 0 is the same Hellmann-Feynman expression.  The
     per-link forces of all 20 eigenvalues are timed once and contracted with
     every direction against the directional derivatives."""
-    dims = (16, 16, 16, 16)
-    k, ndir, h = 20, 16, 1e-6
-    U = synth.gauge_field(dims, 0.5, 1007)
+    from paper_2004_08146_gb300 import workloads
+    w = workloads.get("c5_16c4")
+    dims, m0, csw = tuple(w["dims"]), w["m0"], w["csw"]
+    k, ndir, h = w["k"], 16, 1e-6
+    U = synth.gauge_field(dims, w["eps"], w["seed"])
     n = 12 * int(np.prod(dims))
-    p = qcd.default_params(sap_block=(2, 2, 2, 2))
+    p = qcd.default_params(sap_block=w["sap"])
     ctx = qcd.Context(params=p, stream=stream.cuda_stream)
-    ctx.qcd_set_gauge(U, dims, -0.85, 1.5)
+    ctx.qcd_set_gauge(U, dims, m0, csw)
     V = torch.zeros(k * n, dtype=torch.complex128, device=devn)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx.qcd_mg_setup(8, (4, 4, 4, 4))        # 4^4 aggregates: a 4^4 coarse lattice
+    ctx.qcd_mg_setup(w["nv"], w["agg"])      # 4^4 aggregates: a 4^4 coarse lattice
     rc, lam, info = ctx.qcd_eigs(k, 1e-8, V)
     torch.cuda.synchronize()
     t_eigs = time.perf_counter() - t0
@@ -638,7 +640,7 @@ def gradient_study(qcd, synth, torch, devn, stream):
         return np.einsum('...ab,...bc->...ac', E, U)
 
     def rayleigh(Um):
-        ctx_fd.qcd_set_gauge(Um, dims, -0.85, 1.5)
+        ctx_fd.qcd_set_gauge(Um, dims, m0, csw)
         for j in range(k):
             ctx_fd.qcd_apply_Q(Vm[j], QV[j], 0.0)
         torch.cuda.synchronize()      # the library's stream is not torch's
@@ -670,7 +672,7 @@ def gradient_study(qcd, synth, torch, devn, stream):
         worst_force = max(worst_force, float(np.max(np.abs(con - der) / np.maximum(np.abs(der), 1e-3))))
     ctx.close()
     ctx_fd.close()
-    return {"lattice": "16^4", "k": k, "directions": ndir, "eigs_s": t_eigs, "converged": bool(info.converged),
+    return {"lattice": "16^4", "m0": m0, "k": k, "directions": ndir, "eigs_s": t_eigs, "converged": bool(info.converged),
             "min_abs_lambda": float(np.min(np.abs(lam))), "derivative_s_per_direction": t_der / ndir,
             "max_rel_dev_from_central_difference": worst, "h": h,
             "force_s_per_eigenvector": t_force / k,

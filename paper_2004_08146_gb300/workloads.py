@@ -36,6 +36,12 @@ WORKLOADS = {
                        use_mg=1, agg=(4, 4, 4, 4), nv=24, sap=(2, 2, 2, 2), target=1e-3,
                        block=16, m_min=30, m_max=50, update_every=20, levels=3, agg2=(2, 2, 2, 2), nv2=24,
                        sap_half=1),
+    # 16^4 differentiation workload (FP64 derivatives of the 20 smallest
+    # |lambda|); m0 from tests/golden/tune_m0_dense.py: at eps 0.5 the proxies'
+    # min |lambda| bottoms out at 0.066 around m0 = -0.9 and rises on both
+    # sides, so the 1e-2 target is out of reach and the minimum is taken.
+    "c5_16c4": dict(dims=(16, 16, 16, 16), eps=0.5, csw=1.5, m0=-0.9, seed=1007, k=20,
+                    use_mg=1, agg=(4, 4, 4, 4), nv=8, sap=(2, 2, 2, 2), target=1e-2),
 }
 
 

@@ -40,6 +40,7 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workloads.json")
 SPECS = {
     "c3_32x16c3": dict(dims=(32, 16, 16, 16), eps=0.6, csw=1.7, seed=1003, target=5e-3, most_negative_m0=-1.2),
     "c4_64x32c3": dict(dims=(64, 32, 32, 32), eps=0.6, csw=1.9, seed=1004, target=1e-3, most_negative_m0=-1.0),
+    "c5_16c4": dict(dims=(16, 16, 16, 16), eps=0.5, csw=1.5, seed=1007, target=1e-2, most_negative_m0=-1.2),
 }
 PROXIES = [(4, 4, 4, 4), (8, 4, 4, 4)]
 GRID = [-0.80, -0.90, -1.00, -1.10, -1.20]

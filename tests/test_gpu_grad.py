@@ -151,8 +151,10 @@ def test_autograd_links_central_differences_16c4():
     to 1e-6 relative; the spinor gradient is (Q - tau) g."""
     torch = torch_cuda()
     from paper_2004_08146_gb300 import autograd
-    dims, tau, m0, csw = (16, 16, 16, 16), 0.05, -0.85, 1.5
-    U = synth.gauge_field(dims, 0.5, 1007)
+    from paper_2004_08146_gb300 import workloads
+    w = workloads.get("c5_16c4")
+    dims, tau, m0, csw = tuple(w["dims"]), 0.05, w["m0"], w["csw"]
+    U = synth.gauge_field(dims, w["eps"], w["seed"])
     ctx = make_ctx(U, dims, m0, csw)
     nrhs = 8
     g = dev(synth.spinor(dims, 181, nvec=nrhs))
