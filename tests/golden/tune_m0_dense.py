@@ -1,5 +1,6 @@
-"""Choose m0 for the two large synthetic workloads (32 x 16^3 and 64 x 32^3)
-so that min |lambda(Q)| comes as close as the field allows to its target (the
+"""Choose m0 for the synthetic workloads whose volume the oracle cannot
+diagonalise (32 x 16^3, 64 x 32^3 and the 16^4 differentiation field) so that
+min |lambda(Q)| comes as close as the field allows to its target (the
 stand-in for the paper's "comparable conditioning", Sec. 4).  Calls only the
 oracle and the seeded input generator; adds entries to
 tests/golden/workloads.json.
@@ -11,10 +12,9 @@ unknowns), two seeds each, by dense Hermitian eigendecomposition.  The m0 grid
 runs across the region where the smallest |lambda| is smallest; the chosen m0
 is the grid point (no nearer criticality than the workload allows) whose
 larger proxy (8 x 4^3, mean over the seeds) is closest to the target in log
-distance.  What min |lambda| the chosen m0 gives on the
-full lattice is measured by the GPU runs and reported with them: a larger
-volume has more low modes, so it is at most the proxy's value when the
-spectrum near zero has no gap.
+distance.  What min |lambda| the chosen m0 gives on the full lattice is
+measured by the GPU runs and reported with them; the proxies do not predict
+it reliably (the full lattices came out both above and below their proxies).
 
 usage: python tests/golden/tune_m0_dense.py <name> [<name> ...]
 """
