@@ -193,7 +193,7 @@ class ClockSampler:
 # summed over targets, outer iterations; from the GPU bench line), used to
 # scale the oracle's per-operation times to one eigensolve when no GPU run
 # of the same process provides them (the reference arm).
-REF_COUNTS = {"c2_16x8c3": dict(inner=3387, outer=172, block=4)}
+REF_COUNTS = {"c2_16x8c3": dict(inner=3303, outer=168, block=4)}
 
 
 def oracle_ops(w):
@@ -535,7 +535,7 @@ def workload_params(qcd, w, **kw):
     """Library parameters of a workload: Table 2 defaults plus the workload's
     MG and outer-iteration shape."""
     p = dict(use_mg=w["use_mg"], sap_block=w["sap"])
-    for key in ("block", "m_min", "m_max", "update_every", "levels", "nv2", "agg2", "sap_half"):
+    for key in ("block", "m_min", "m_max", "update_every", "levels", "nv2", "agg2", "sap_half", "coarse_maxiter"):
         if key in w:
             p[key] = w[key]
     p.update(kw)

@@ -33,7 +33,7 @@ def _run(c2, precision, seed, block=None):
     torch = torch_cuda()
     w, dims, U, op = c2
     ctx = make_ctx(U, dims, w["m0"], w["csw"], precision=precision, seed=seed, sap_block=w["sap"],
-                   block=w["block"] if block is None else block)
+                   block=w["block"] if block is None else block, coarse_maxiter=w["coarse_maxiter"])
     ctx.qcd_mg_setup(w["nv"], w["agg"])
     V = torch.zeros(K * op.n, dtype=torch.complex128, device="cuda")
     rc, lam, info = ctx.qcd_eigs(K, 1e-8, V)

@@ -32,6 +32,6 @@ def test_bench_parameters_follow_the_workload_table():
     p3 = bench.workload_params(qcd, w3)
     assert (p3.levels, p3.block, p3.m_min, p3.m_max, p3.sap_half) == (2, 16, 30, 50, 1)
     p2 = bench.workload_params(qcd, workloads.get("c2_16x8c3"))
-    assert (p2.block, p2.levels, p2.guard) == (4, 2, 0)
+    assert (p2.block, p2.levels, p2.guard, p2.coarse_maxiter) == (4, 2, 0, 12)
     # Table 2 defaults stay in place
     assert (p2.nu, p2.inner_maxiter, p2.inner_tol, p2.coarse_tol, p2.setup_iters) == (4, 5, 0.1, 0.5, 6)
