@@ -113,8 +113,10 @@ def max_over_ranks(value, device=None):
 # captured again (the field is then null).  coarse_gmres_f32: two launches of
 # coarse_gmres_kernel<float2, float> in the 16 x 8^3 step (k = 4, 4 targets),
 # dram__bytes.sum.per_second x gpu__time_duration.sum = 9.808 and 9.820 MB
-# (profiles/coarse_gmres_f32_c2_16x8c3.md).
-NCU_TRAFFIC = {"coarse_gmres_f32": 9.814e6}
+# (profiles/coarse_gmres_f32_c2_16x8c3.md).  sap_block_f32: two launches of
+# sap_chi_kernel<float, float2> in the same step (four block solves per CTA),
+# 6.8831 and 6.8836 MB read, 0 written (profiles/sap_chi_f32_c2_16x8c3.md).
+NCU_TRAFFIC = {"coarse_gmres_f32": 9.814e6, "sap_block_f32": 6.8833e6}
 
 # Work model of the SAP block solves for the FP32-ALU roofline, per block
 # site and GMRES step j (0-based) of a block solve of k steps: the Dirichlet
